@@ -1,0 +1,167 @@
+"""Python access to the FP64 oracle (fe_oracle.c) through ctypes.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()`` and by
+the CPU-baseline leg of ``bench.py``. The library's GPU path never imports it.
+
+``build()`` compiles fe_oracle.c with the host C compiler into ``oracle/_build``.
+Every function here only converts arguments; the arithmetic is in fe_oracle.c.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fe_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+MASS, WMASS, STIFF, ELAS = 0, 1, 2, 3
+COEF_NONE, COEF_SCALAR, COEF_P0, COEF_P1 = 0, 1, 2, 3
+ERRORS = {1: "argument", 2: "index", 3: "degenerate", 4: "out of memory"}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, -O2, no vectorisation flags) if it is missing or stale."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        lib.orc_magic.argtypes = [I32, P, D]
+        lib.orc_magic.restype = D
+        lib.orc_simplex.argtypes = [I32, P, P, P, P]
+        lib.orc_element.argtypes = [I32, I32, P, P, P, P, P]
+        lib.orc_assemble.argtypes = [I32, I32, I64, I64, P, P, I32, P, I32, P,
+                                     P, P, P, P, P, P, P]
+        lib.orc_stiff_loss.argtypes = [I32, I64, I64, P, P, P, P, P, P, P, P, P]
+        lib.orc_free.argtypes = [P]
+        _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, bad_id=-1):
+        super().__init__(f"oracle error {code} ({ERRORS.get(code, '?')}), id {bad_id}")
+        self.code, self.bad_id = code, bad_id
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def magic(d: int, n, vol: float) -> float:
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    return _load().orc_magic(d, _ptr(n), vol)
+
+
+def simplex(X: np.ndarray):
+    """(det B, |K|, G) for one simplex; X is (d+1, d); G is (d+1, d), row a = grad lambda_a."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    d = X.shape[1]
+    det, vol = C.c_double(), C.c_double()
+    G = np.zeros((d + 1, d))
+    rc = _load().orc_simplex(d, _ptr(X), C.byref(det), C.byref(vol), _ptr(G))
+    if rc:
+        raise OracleError(rc)
+    return det.value, vol.value, G
+
+
+def element(kind: int, X: np.ndarray, cv1=None, cv2=None):
+    """Local matrix (nl, nl) with E[i, j] = local entry (i, j), and its condition scale."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    d = X.shape[1]
+    nl = (d + 1) * (d if kind == ELAS else 1)
+    E = np.zeros(nl * nl)
+    S = np.zeros(nl * nl)
+    c1 = None if cv1 is None else np.ascontiguousarray(np.broadcast_to(cv1, (d + 1,)), dtype=np.float64)
+    c2 = None if cv2 is None else np.ascontiguousarray(np.broadcast_to(cv2, (d + 1,)), dtype=np.float64)
+    rc = _load().orc_element(kind, d, _ptr(X), _ptr(c1), _ptr(c2), _ptr(E), _ptr(S))
+    if rc:
+        raise OracleError(rc)
+    # storage is column-wise: E[j*nl + i] holds local entry (i, j)
+    return E.reshape(nl, nl).T.copy(), S.reshape(nl, nl).T.copy()
+
+
+def _coef(c):
+    """(kind, array) for a coefficient given as None, a number, or a per-element/vertex array."""
+    if c is None:
+        return COEF_NONE, None
+    if np.isscalar(c):
+        return COEF_SCALAR, np.array([float(c)])
+    kind, arr = c
+    return kind, np.ascontiguousarray(arr, dtype=np.float64)
+
+
+def assemble(kind: int, q: np.ndarray, me: np.ndarray, c1=None, c2=None) -> dict:
+    """Assemble the global matrix. c1/c2: None, a number, or (COEF_P0|COEF_P1, array).
+
+    Returns dict(n, nnz, row_ptr int64, col_idx int32, val float64, scale float64).
+    """
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    me = np.ascontiguousarray(me, dtype=np.int32)
+    d, nq = q.shape
+    nme = me.shape[1]
+    k1, a1 = _coef(c1)
+    k2, a2 = _coef(c2)
+    n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
+    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    lib = _load()
+    rc = lib.orc_assemble(kind, d, nq, nme, _ptr(q), _ptr(me), k1, _ptr(a1), k2, _ptr(a2),
+                          C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
+                          C.byref(sc), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+
+    def take(p, ctype, count, dtype):
+        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
+        out = np.array(arr, dtype=dtype)
+        lib.orc_free(p)
+        return out
+
+    N, NNZ = n.value, nnz.value
+    return dict(n=N, nnz=NNZ,
+                row_ptr=take(rp, C.c_int64, N + 1, np.int64),
+                col_idx=take(ci, C.c_int32, NNZ, np.int32),
+                val=take(va, C.c_double, NNZ, np.float64),
+                scale=take(sc, C.c_double, NNZ, np.float64))
+
+
+def stiff_loss(q, me, w, u, v, grads: bool = True):
+    """(L, dL/dw, dL/dq) for L = u^T K(w) v, K the stiffness matrix; w per element or None."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    me = np.ascontiguousarray(me, dtype=np.int32)
+    d, nq = q.shape
+    nme = me.shape[1]
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    L, bad = C.c_double(), C.c_int64()
+    dw = np.zeros(nme) if grads else None
+    dq = np.zeros((d, nq)) if grads else None
+    rc = _load().orc_stiff_loss(d, nq, nme, _ptr(q), _ptr(me), _ptr(w), _ptr(u), _ptr(v),
+                                C.byref(L), _ptr(dw), _ptr(dq), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+    return L.value, dw, dq
+
+
+def to_dense(res: dict) -> np.ndarray:
+    """Dense copy of an oracle CSR result (small cases only)."""
+    n = res["n"]
+    A = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(res["row_ptr"]))
+    A[rows, res["col_idx"]] = res["val"]
+    return A

@@ -1,0 +1,396 @@
+/*
+ * fe_oracle.c -- plain FP64 reference ("oracle") for P1 finite element assembly.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file. The library's GPU path never
+ * calls, links or includes it, and it shares no code with that path.
+ *
+ * What it computes, step by step, in the order of the paper
+ * (Cuvelier, Japhet, Scarella, "An efficient way to assemble finite element
+ * matrices in vector languages"):
+ *   1. per element k: B_k with i-th column q^i - q^0 (App. C.1), the barycentric
+ *      gradients G_k as the solution of B_k^T G_k = G^ (Eq. gradient:SystemeMat),
+ *      solved here by Gaussian elimination with partial pivoting; det B_k from the
+ *      pivots and |K| = |det B_k| / d!;
+ *   2. the local matrix E(T_k) from its definition:
+ *        mass / weighted mass: integrals of products of barycentric coordinates
+ *          by the magic formula (Eq. MagicFormula), with w replaced by its P1
+ *          interpolant (Section 4.1);
+ *        stiffness: |K| <grad lambda_b, grad lambda_a> (Eq. stiffelemmat), times
+ *          an optional per-element coefficient;
+ *        elasticity: int eps(phi_j)^T C eps(phi_i) (Eq. StiffElasElem) with the
+ *          strain vector order and Hooke matrix C of Section 5.1 and the Lame
+ *          coefficients replaced by their P1 interpolants;
+ *   3. the (Ig, Jg, Kg) triplets of all elements (Algorithm 2, column-wise local
+ *      order), sorted by (row, column, element, local slot) and summed, which is
+ *      the `sparse` constructor of Section 3. Entries whose sum is zero are kept.
+ * Every step is a plain loop over elements; nothing is blocked or fused.
+ *
+ * Indices are 0-based; vector unknowns use the alternate numbering
+ * dof = m * vertex + component (Section 5).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_INDEX 2
+#define ORC_ERR_DEGENERATE 3
+#define ORC_ERR_NOMEM 4
+
+#define ORC_MASS 0
+#define ORC_WMASS 1
+#define ORC_STIFF 2
+#define ORC_ELAS 3
+
+/* coefficient kinds */
+#define ORC_COEF_NONE 0   /* identically 1 */
+#define ORC_COEF_SCALAR 1 /* one value */
+#define ORC_COEF_P0 2     /* one value per element */
+#define ORC_COEF_P1 3     /* one value per vertex, P1-interpolated */
+
+static double factorial(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= (double)i;
+  return f;
+}
+
+/* Eq. MagicFormula: int_K prod_i lambda_i^{n_i} = d! |K| prod_i n_i! / (d + sum_i n_i)! */
+double orc_magic(int d, const int* n, double vol) {
+  double num = 1.0;
+  int s = 0;
+  for (int i = 0; i < d + 1; ++i) {
+    num *= factorial(n[i]);
+    s += n[i];
+  }
+  return factorial(d) * vol * num / factorial(d + s);
+}
+
+/*
+ * Geometry of one d-simplex (App. C.1). X holds the d+1 vertices, X[a*d + c] is
+ * coordinate c of local vertex a. Output: det = det B, vol = |det B| / d!,
+ * G[a*d + i] = d lambda_a / d x_i, found by solving B^T G = G^ with
+ * G^ = [-1, I_d] by Gaussian elimination with partial pivoting.
+ */
+int orc_simplex(int d, const double* X, double* det, double* vol, double* G) {
+  if (d < 1 || d > 3) return ORC_ERR_ARG;
+  double A[3][3], R[3][4];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) A[i][j] = X[(i + 1) * d + j] - X[j]; /* A = B^T: A[i][j] = B[j][i] */
+  for (int i = 0; i < d; ++i) {
+    R[i][0] = -1.0;
+    for (int a = 1; a <= d; ++a) R[i][a] = (a - 1 == i) ? 1.0 : 0.0;
+  }
+  double dt = 1.0;
+  for (int c = 0; c < d; ++c) {
+    int p = c;
+    for (int r = c + 1; r < d; ++r)
+      if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
+    if (A[p][c] == 0.0) {
+      *det = 0.0;
+      *vol = 0.0;
+      return ORC_ERR_DEGENERATE;
+    }
+    if (p != c) {
+      for (int j = 0; j < d; ++j) { double t = A[c][j]; A[c][j] = A[p][j]; A[p][j] = t; }
+      for (int a = 0; a <= d; ++a) { double t = R[c][a]; R[c][a] = R[p][a]; R[p][a] = t; }
+      dt = -dt;
+    }
+    dt *= A[c][c];
+    for (int r = c + 1; r < d; ++r) {
+      double f = A[r][c] / A[c][c];
+      for (int j = c; j < d; ++j) A[r][j] -= f * A[c][j];
+      for (int a = 0; a <= d; ++a) R[r][a] -= f * R[c][a];
+    }
+  }
+  for (int a = 0; a <= d; ++a) {
+    double x[3];
+    for (int i = d - 1; i >= 0; --i) {
+      double s = R[i][a];
+      for (int j = i + 1; j < d; ++j) s -= A[i][j] * x[j];
+      x[i] = s / A[i][i];
+    }
+    for (int i = 0; i < d; ++i) G[a * d + i] = x[i];
+  }
+  *det = dt;
+  *vol = fabs(dt) / factorial(d);
+  if (!isfinite(dt) || !isfinite(*vol)) return ORC_ERR_DEGENERATE;
+  return ORC_OK;
+}
+
+/* integral over K of the P1 interpolant of a field with vertex values f[0..d] */
+static double p1_integral(int d, const double* f, double vol) {
+  double s = 0.0;
+  int n[4];
+  for (int g = 0; g <= d; ++g) {
+    for (int i = 0; i <= d; ++i) n[i] = (i == g);
+    s += f[g] * orc_magic(d, n, vol);
+  }
+  return s;
+}
+
+/* strain vector of phi = lambda_a e_l, in the order of Section 5.1:
+ * 2D (e11, e22, 2 e12), 3D (e11, e22, e33, 2 e12, 2 e23, 2 e13). */
+static void strain_vector(int d, const double* ga, int l, double* eps) {
+  double e[3][3];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) e[i][j] = 0.5 * ((i == l) * ga[j] + (j == l) * ga[i]);
+  if (d == 2) {
+    eps[0] = e[0][0]; eps[1] = e[1][1]; eps[2] = 2.0 * e[0][1];
+  } else {
+    eps[0] = e[0][0]; eps[1] = e[1][1]; eps[2] = e[2][2];
+    eps[3] = 2.0 * e[0][1]; eps[4] = 2.0 * e[1][2]; eps[5] = 2.0 * e[0][2];
+  }
+}
+
+/* Hooke matrix of Section 5.1 with lambda, mu replaced by their integrals */
+static void hooke(int d, double lam, double mu, double C[6][6]) {
+  int ns = (d == 2) ? 3 : 6;
+  for (int i = 0; i < ns; ++i)
+    for (int j = 0; j < ns; ++j) C[i][j] = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) C[i][j] = lam + ((i == j) ? 2.0 * mu : 0.0);
+  for (int i = d; i < ns; ++i) C[i][i] = mu;
+}
+
+/*
+ * Local matrix of one element, column-wise: E[j*nl + i], nl = m (d+1), local
+ * index i = a m + l for vertex a, component l. S receives the "condition scale"
+ * of every entry: the same expression with every product replaced by its absolute
+ * value (used by the tests to normalise errors of cancelling sums).
+ * cv1 / cv2 are the vertex values of the coefficient(s) (P1 interpolation; a
+ * scalar or P0 coefficient is passed as d+1 equal values).
+ */
+int orc_element(int kind, int d, const double* X, const double* cv1, const double* cv2,
+                double* E, double* S) {
+  double det, vol, G[4 * 3];
+  int rc = orc_simplex(d, X, &det, &vol, G);
+  if (rc) return rc;
+  int nv = d + 1;
+  if (kind == ORC_MASS || kind == ORC_WMASS) {
+    for (int b = 0; b < nv; ++b)
+      for (int a = 0; a < nv; ++a) {
+        double s = 0.0, sa = 0.0;
+        int n[4];
+        if (kind == ORC_MASS) {
+          for (int i = 0; i < nv; ++i) n[i] = (i == a) + (i == b);
+          s = orc_magic(d, n, vol);
+          sa = s;
+        } else {
+          for (int g = 0; g < nv; ++g) {
+            for (int i = 0; i < nv; ++i) n[i] = (i == a) + (i == b) + (i == g);
+            double t = cv1[g] * orc_magic(d, n, vol);
+            s += t;
+            sa += fabs(t);
+          }
+        }
+        E[b * nv + a] = s;
+        S[b * nv + a] = sa;
+      }
+    return ORC_OK;
+  }
+  if (kind == ORC_STIFF) {
+    double w = cv1 ? cv1[0] : 1.0;
+    for (int b = 0; b < nv; ++b)
+      for (int a = 0; a < nv; ++a) {
+        double s = 0.0, sa = 0.0;
+        for (int i = 0; i < d; ++i) {
+          s += G[b * d + i] * G[a * d + i];
+          sa += fabs(G[b * d + i] * G[a * d + i]);
+        }
+        E[b * nv + a] = w * vol * s;
+        S[b * nv + a] = fabs(w) * vol * sa;
+      }
+    return ORC_OK;
+  }
+  if (kind == ORC_ELAS) {
+    int m = d, nl = m * nv, ns = (d == 2) ? 3 : 6;
+    double lam = p1_integral(d, cv1, vol), mu = p1_integral(d, cv2, vol);
+    double C[6][6], Ca[6][6];
+    hooke(d, lam, mu, C);
+    hooke(d, fabs(lam), fabs(mu), Ca);
+    for (int b = 0; b < nv; ++b)
+      for (int n = 0; n < m; ++n) {
+        double eb[6];
+        strain_vector(d, &G[b * d], n, eb);
+        int j = b * m + n;
+        for (int a = 0; a < nv; ++a)
+          for (int l = 0; l < m; ++l) {
+            double ea[6];
+            strain_vector(d, &G[a * d], l, ea);
+            int i = a * m + l;
+            double s = 0.0, sa = 0.0;
+            for (int r = 0; r < ns; ++r)
+              for (int c = 0; c < ns; ++c) {
+                s += eb[r] * C[r][c] * ea[c];
+                sa += fabs(eb[r] * Ca[r][c] * ea[c]);
+              }
+            E[j * nl + i] = s;
+            S[j * nl + i] = sa;
+          }
+      }
+    return ORC_OK;
+  }
+  return ORC_ERR_ARG;
+}
+
+/* vertex values of a coefficient on element k */
+static void coef_values(int kind, const double* c, int d, int64_t nme, const int32_t* me, int64_t k,
+                        double* out) {
+  for (int a = 0; a <= d; ++a) {
+    switch (kind) {
+      case ORC_COEF_NONE: out[a] = 1.0; break;
+      case ORC_COEF_SCALAR: out[a] = c[0]; break;
+      case ORC_COEF_P0: out[a] = c[k]; break;
+      default: out[a] = c[me[(int64_t)a * nme + k]]; break;
+    }
+  }
+}
+
+typedef struct {
+  int64_t row, col, k;
+  int32_t slot;
+  double v, s;
+} triplet;
+
+static int cmp_triplet(const void* pa, const void* pb) {
+  const triplet* a = (const triplet*)pa;
+  const triplet* b = (const triplet*)pb;
+  if (a->row != b->row) return a->row < b->row ? -1 : 1;
+  if (a->col != b->col) return a->col < b->col ? -1 : 1;
+  if (a->k != b->k) return a->k < b->k ? -1 : 1;
+  if (a->slot != b->slot) return a->slot < b->slot ? -1 : 1;
+  return 0;
+}
+
+/*
+ * Full assembly (Algorithm 2 followed by `sparse`). q is d x nq (q[c*nq + v]),
+ * me is (d+1) x nme (me[a*nme + k]). The result is a CSR matrix of order
+ * n = m nq with sorted column indices, returned in malloc'ed arrays that the
+ * caller frees with orc_free. scale receives, per entry, the sum over its
+ * contributions of their condition scale (see orc_element). On error *bad_id is
+ * the offending element (or vertex index for ORC_ERR_INDEX).
+ */
+int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                 int c1_kind, const double* c1, int c2_kind, const double* c2,
+                 int64_t* n_out, int64_t* nnz_out, int64_t** row_ptr, int32_t** col_idx,
+                 double** val, double** scale, int64_t* bad_id) {
+  *bad_id = -1;
+  if (d < 1 || d > 3 || nq < 0 || nme < 0) return ORC_ERR_ARG;
+  int m = (kind == ORC_ELAS) ? d : 1;
+  int nv = d + 1, nl = m * nv, ns = nl * nl;
+  int64_t n = (int64_t)m * nq;
+  int64_t nt = nme * ns;
+  triplet* t = (triplet*)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(triplet));
+  if (!t) return ORC_ERR_NOMEM;
+  double X[12], cv1[4], cv2[4], E[144], S[144];
+  int rc = ORC_OK;
+  for (int64_t k = 0; k < nme && rc == ORC_OK; ++k) {
+    for (int a = 0; a < nv; ++a) {
+      int32_t v = me[(int64_t)a * nme + k];
+      if (v < 0 || v >= nq) { *bad_id = k; rc = ORC_ERR_INDEX; break; }
+      for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
+    }
+    if (rc) break;
+    coef_values(c1_kind, c1, d, nme, me, k, cv1);
+    coef_values(c2_kind, c2, d, nme, me, k, cv2);
+    rc = orc_element(kind, d, X, cv1, cv2, E, S);
+    if (rc) { *bad_id = k; break; }
+    for (int j = 0; j < nl; ++j)
+      for (int i = 0; i < nl; ++i) {
+        triplet* p = &t[k * ns + j * nl + i];
+        int a = i / m, l = i % m, b = j / m, c = j % m;
+        p->row = (int64_t)m * me[(int64_t)a * nme + k] + l;
+        p->col = (int64_t)m * me[(int64_t)b * nme + k] + c;
+        p->k = k;
+        p->slot = j * nl + i;
+        p->v = E[j * nl + i];
+        p->s = S[j * nl + i];
+      }
+  }
+  if (rc) { free(t); return rc; }
+  qsort(t, (size_t)nt, sizeof(triplet), cmp_triplet);
+  int64_t nnz = 0;
+  for (int64_t i = 0; i < nt; ++i)
+    if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) ++nnz;
+  *row_ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  *col_idx = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+  *val = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+  *scale = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+  if (!*row_ptr || !*col_idx || !*val || !*scale) { free(t); return ORC_ERR_NOMEM; }
+  int64_t j = -1;
+  for (int64_t i = 0; i < nt; ++i) {
+    if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) {
+      ++j;
+      (*col_idx)[j] = (int32_t)t[i].col;
+      (*val)[j] = 0.0;
+      (*scale)[j] = 0.0;
+      (*row_ptr)[t[i].row + 1] += 1;
+    }
+    (*val)[j] += t[i].v;
+    (*scale)[j] += t[i].s;
+  }
+  for (int64_t r = 0; r < n; ++r) (*row_ptr)[r + 1] += (*row_ptr)[r];
+  free(t);
+  *n_out = n;
+  *nnz_out = nnz;
+  return ORC_OK;
+}
+
+void orc_free(void* p) { free(p); }
+
+/*
+ * Loss L = u^T K(w) v for the stiffness matrix with per-element coefficient w
+ * (NULL: w = 1), and its gradients. Per element, with ubar = sum_a u_a grad
+ * lambda_a and vbar likewise, the element part is L_e = w_e |K| ubar . vbar, so
+ *   dL/dw_e = |K| ubar . vbar,
+ *   dL/dq^c = sum over elements containing vertex c of
+ *             w_e |K| [ (ubar . vbar) g_c - ubar (g_c . vbar) - vbar (g_c . ubar) ],
+ * where g_c is the gradient of the barycentric coordinate of that vertex. The
+ * last formula is the derivative of |det B| / d! and of B^{-T} with respect to
+ * the columns of B = [q^1 - q^0, ...] (App. C.1); the paper itself has no
+ * derivatives. dLdq is d x nq like q and is accumulated in element order.
+ */
+int orc_stiff_loss(int d, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                   const double* w, const double* u, const double* v, double* L, double* dLdw,
+                   double* dLdq, int64_t* bad_id) {
+  *bad_id = -1;
+  int nv = d + 1;
+  double X[12], G[12], det, vol;
+  double total = 0.0;
+  if (dLdq) memset(dLdq, 0, sizeof(double) * (size_t)(d * nq));
+  for (int64_t k = 0; k < nme; ++k) {
+    int32_t vid[4];
+    for (int a = 0; a < nv; ++a) {
+      vid[a] = me[(int64_t)a * nme + k];
+      if (vid[a] < 0 || vid[a] >= nq) { *bad_id = k; return ORC_ERR_INDEX; }
+      for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + vid[a]];
+    }
+    int rc = orc_simplex(d, X, &det, &vol, G);
+    if (rc) { *bad_id = k; return rc; }
+    double ub[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+    for (int a = 0; a < nv; ++a)
+      for (int i = 0; i < d; ++i) {
+        ub[i] += u[vid[a]] * G[a * d + i];
+        vb[i] += v[vid[a]] * G[a * d + i];
+      }
+    double uv = 0.0;
+    for (int i = 0; i < d; ++i) uv += ub[i] * vb[i];
+    double we = w ? w[k] : 1.0;
+    total += we * vol * uv;
+    if (dLdw) dLdw[k] = vol * uv;
+    if (dLdq) {
+      for (int c = 0; c < nv; ++c) {
+        const double* g = &G[c * d];
+        double gu = 0.0, gv = 0.0;
+        for (int i = 0; i < d; ++i) { gu += g[i] * ub[i]; gv += g[i] * vb[i]; }
+        for (int i = 0; i < d; ++i)
+          dLdq[(int64_t)i * nq + vid[c]] += we * vol * (uv * g[i] - ub[i] * gv - vb[i] * gu);
+      }
+    }
+  }
+  *L = total;
+  return ORC_OK;
+}

@@ -1,0 +1,339 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+No GPU. Each check is chosen so that a plausible slip in the oracle (a dropped
+term, a sign, a transposed index, a wrong factorial) fails at least one of them.
+"""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_3301_gb300 import meshgen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+def duffy_rule(d, n=8):
+    """Collapsed-coordinate Gauss-Legendre rule on the reference simplex (independent quadrature)."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    x, w = 0.5 * (x + 1.0), 0.5 * w
+    pts, wts = [], []
+    if d == 2:
+        for (u, wu), (v, wv) in itertools.product(zip(x, w), zip(x, w)):
+            pts.append((u, v * (1 - u)))
+            wts.append(wu * wv * (1 - u))
+    else:
+        for (u, wu), (v, wv), (t, wt) in itertools.product(zip(x, w), zip(x, w), zip(x, w)):
+            pts.append((u, v * (1 - u), t * (1 - u) * (1 - v)))
+            wts.append(wu * wv * wt * (1 - u) ** 2 * (1 - v))
+    return np.array(pts), np.array(wts)
+
+
+def bary_ref(pts):
+    """Barycentric coordinates on the reference simplex: lambda_0 = 1 - sum x, lambda_i = x_i."""
+    return np.column_stack([1.0 - pts.sum(axis=1), pts])
+
+
+def random_simplex(rng, d):
+    while True:
+        X = rng.normal(size=(d + 1, d))
+        if abs(np.linalg.det((X[1:] - X[0]).T)) > 0.2:
+            return X
+
+
+def read_golden(name):
+    verts, elems, entries = [], [], {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if not line:
+                continue
+            if line[0] == "vertex":
+                verts.append([float(t) for t in line[2:]])
+            elif line[0] == "element":
+                elems.append([int(t) for t in line[1:]])
+            else:
+                val = sum(Fraction(t) for t in line[3].split("+"))
+                entries.setdefault(line[0], {})[(int(line[1]), int(line[2]))] = float(val)
+    q = np.array(verts).T.copy()
+    me = np.array(elems, dtype=np.int32).T.copy()
+    return q, me, entries
+
+
+def csr_entries(res):
+    rows = np.repeat(np.arange(res["n"]), np.diff(res["row_ptr"]))
+    return {(int(r), int(c)): v for r, c, v in zip(rows, res["col_idx"], res["val"])}
+
+
+# ---------------------------------------------------------------- magic formula and geometry
+@pytest.mark.parametrize("d", [2, 3])
+def test_magic_formula_against_quadrature(d):
+    rng = np.random.default_rng(1)
+    X = random_simplex(rng, d)
+    det, vol, _ = oracle.simplex(X)
+    pts, wts = duffy_rule(d)
+    lam = bary_ref(pts)
+    for n in itertools.product(range(3), repeat=d + 1):
+        if sum(n) > 4:
+            continue
+        quad = abs(det) * np.sum(wts * np.prod(lam ** np.array(n), axis=1))
+        assert oracle.magic(d, n, vol) == pytest.approx(quad, rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_simplex_gradients_are_barycentric(d):
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        X = random_simplex(rng, d)
+        det, vol, G = oracle.simplex(X)
+        B = (X[1:] - X[0]).T
+        assert det == pytest.approx(np.linalg.det(B), rel=1e-12)
+        assert vol == pytest.approx(abs(np.linalg.det(B)) / (2 if d == 2 else 6), rel=1e-12)
+        # lambda_a is affine with lambda_a(X_b) = delta_ab, so G_a . (X_b - X_c) = delta_ab - delta_ac
+        for a, b, c in itertools.product(range(d + 1), repeat=3):
+            lhs = G[a] @ (X[b] - X[c])
+            assert lhs == pytest.approx(float(a == b) - float(a == c), abs=1e-11)
+        assert np.abs(G.sum(axis=0)).max() < 1e-11
+
+
+def test_unit_right_simplices_stiffness():
+    # textbook element matrices of the reference triangle / tetrahedron
+    Et, _ = oracle.element(oracle.STIFF, np.array([[0, 0], [1, 0], [0, 1]], float))
+    np.testing.assert_allclose(Et, 0.5 * np.array([[2, -1, -1], [-1, 1, 0], [-1, 0, 1]]), atol=1e-15)
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    Ek, _ = oracle.element(oracle.STIFF, X)
+    ref = np.array([[3, -1, -1, -1], [-1, 1, 0, 0], [-1, 0, 1, 0], [-1, 0, 0, 1]]) / 6.0
+    np.testing.assert_allclose(Ek, ref, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_mass_closed_form(d):
+    # Section 4.1 with w = 1: |K| d!/(d+2)! (1 + delta), i.e. |K|/12 (2D), |K|/20 (3D)
+    rng = np.random.default_rng(3)
+    X = random_simplex(rng, d)
+    _, vol, _ = oracle.simplex(X)
+    E, _ = oracle.element(oracle.MASS, X)
+    c = 12.0 if d == 2 else 20.0
+    np.testing.assert_allclose(E, vol / c * (1 + np.eye(d + 1)), rtol=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_weighted_mass_closed_form_and_quadrature(d):
+    rng = np.random.default_rng(4)
+    X = random_simplex(rng, d)
+    det, vol, _ = oracle.simplex(X)
+    w = rng.uniform(0.5, 2.0, size=d + 1)
+    E, _ = oracle.element(oracle.WMASS, X, cv1=w)
+    # Eq. MatElemMassWP1: d!/(d+3)! |K| (1 + delta_ab)(w^s + w_a + w_b)
+    fac = (2.0 if d == 2 else 6.0) / (120.0 if d == 2 else 720.0)
+    closed = fac * vol * (1 + np.eye(d + 1)) * (w.sum() + w[:, None] + w[None, :])
+    np.testing.assert_allclose(E, closed, rtol=1e-13)
+    # independent: quadrature of (sum_g w_g lambda_g) lambda_a lambda_b (cubic -> exact)
+    pts, wts = duffy_rule(d)
+    lam = bary_ref(pts)
+    wh = lam @ w
+    quad = abs(det) * np.einsum("p,p,pa,pb->ab", wts, wh, lam, lam)
+    np.testing.assert_allclose(E, quad, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- golden two-element meshes
+@pytest.mark.parametrize("name", ["two_triangles.txt", "two_tets.txt"])
+def test_two_element_golden(name):
+    q, me, gold = read_golden(name)
+    for kind, key in ((oracle.STIFF, "stiff"), (oracle.MASS, "mass")):
+        res = oracle.assemble(kind, q, me)
+        got = csr_entries(res)
+        assert set(got) == set(gold[key]), key  # pattern, including the structural zeros
+        for ij, v in gold[key].items():
+            assert got[ij] == pytest.approx(v, abs=1e-15), (key, ij)
+
+
+# ---------------------------------------------------------------- global invariants
+def test_global_mass_and_stiffness_invariants_2d():
+    m = meshgen.square_mesh(12, seed=5)
+    x, y = m.q
+    M = oracle.to_dense(oracle.assemble(oracle.MASS, m.q, m.me))
+    S = oracle.to_dense(oracle.assemble(oracle.STIFF, m.q, m.me))
+    one = np.ones(m.nq)
+    assert one @ M @ one == pytest.approx(1.0, rel=1e-13)       # |Omega|
+    assert x @ M @ x == pytest.approx(1.0 / 3.0, rel=1e-13)     # int x^2 (P1 exact)
+    assert x @ M @ y == pytest.approx(1.0 / 4.0, rel=1e-13)     # int x y
+    assert np.abs(S @ one).max() < 1e-13
+    a, c = np.array([0.7, -1.3]), 0.4
+    u = a @ m.q + c
+    assert u @ S @ u == pytest.approx(a @ a, rel=1e-12)          # |a|^2 |Omega|
+    np.testing.assert_allclose(S, S.T, atol=1e-14)
+    assert np.linalg.eigvalsh(S).min() > -1e-12
+
+
+def test_global_invariants_3d_and_weighted_mass():
+    m = meshgen.kuhn_cube_mesh(4, seed=6)
+    one = np.ones(m.nq)
+    M = oracle.to_dense(oracle.assemble(oracle.MASS, m.q, m.me))
+    assert one @ M @ one == pytest.approx(1.0, rel=1e-13)
+    x, y, z = m.q
+    assert z @ M @ z == pytest.approx(1.0 / 3.0, rel=1e-12)
+    S = oracle.to_dense(oracle.assemble(oracle.STIFF, m.q, m.me))
+    assert np.abs(S @ one).max() < 1e-13
+    a = np.array([0.3, -0.8, 1.1])
+    u = a @ m.q
+    assert u @ S @ u == pytest.approx(a @ a, rel=1e-12)
+    # P1 weight w = 2 + x - y + 3z: the P1 rule is exact, 1^T M_w 1 = int w = 2 + 0.5 - 0.5 + 1.5
+    w = 2 + x - y + 3 * z
+    Mw = oracle.to_dense(oracle.assemble(oracle.WMASS, m.q, m.me, c1=(oracle.COEF_P1, w)))
+    assert one @ Mw @ one == pytest.approx(3.5, rel=1e-13)
+    # int w x = int (2x + x^2 - xy + 3xz) = 1 + 1/3 - 1/4 + 3/4
+    assert one @ Mw @ x == pytest.approx(1 + 1 / 3 - 1 / 4 + 3 / 4, rel=1e-12)
+    # P0 weight: 1^T M 1 = sum_K w_K |K|
+    wk = meshgen.element_weights(6, m.nme)
+    M0 = oracle.assemble(oracle.WMASS, m.q, m.me, c1=(oracle.COEF_P0, wk))
+    vols = np.array([oracle.simplex(m.q[:, m.me[:, k]].T)[1] for k in range(m.nme)])
+    assert M0["val"].sum() == pytest.approx((wk * vols).sum(), rel=1e-13)
+
+
+# ---------------------------------------------------------------- elasticity
+def paper_QS(d):
+    """Q^{n,l} = B_n^T C0 B_l and S^{n,l} = B_n^T C1 B_l with B_l, C0, C1 as printed in App. B."""
+    def Bl(l):
+        dl = [float(l == i) for i in range(d)]
+        if d == 2:
+            return np.array([[dl[0], 0], [0, dl[1]], [dl[1], dl[0]]])
+        return np.array([[dl[0], 0, 0], [0, dl[1], 0], [0, 0, dl[2]],
+                         [dl[1], dl[0], 0], [0, dl[2], dl[1]], [dl[2], 0, dl[0]]])
+    ns = 3 * (d - 1)
+    C0 = np.zeros((ns, ns))
+    C0[:d, :d] = 1.0
+    C1 = np.diag([2.0] * d + [1.0] * (ns - d))
+    Q = {(n, l): Bl(n).T @ C0 @ Bl(l) for n in range(d) for l in range(d)}
+    S = {(n, l): Bl(n).T @ C1 @ Bl(l) for n in range(d) for l in range(d)}
+    return Q, S
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_elasticity_element_matches_lemma(d):
+    # Lemma (Section 5.1): eps(phi_{n,b})^T C eps(phi_{l,a}) = lam <g_b, Q^{n,l} g_a> + mu <g_b, S^{n,l} g_a>
+    rng = np.random.default_rng(7)
+    X = random_simplex(rng, d)
+    _, vol, G = oracle.simplex(X)
+    lam_v, mu_v = rng.uniform(0.5, 2, d + 1), rng.uniform(0.5, 2, d + 1)
+    E, _ = oracle.element(oracle.ELAS, X, cv1=lam_v, cv2=mu_v)
+    Q, S = paper_QS(d)
+    lam_s, mu_s = vol / (d + 1) * lam_v.sum(), vol / (d + 1) * mu_v.sum()
+    for a, l, b, n in itertools.product(range(d + 1), range(d), range(d + 1), range(d)):
+        ref = lam_s * G[b] @ Q[(n, l)] @ G[a] + mu_s * G[b] @ S[(n, l)] @ G[a]
+        assert E[a * d + l, b * d + n] == pytest.approx(ref, rel=1e-12, abs=1e-14)
+    # and the closed forms Q^{n,l} = e_n e_l^T, S^{n,l} = delta_nl I + e_l e_n^T
+    I = np.eye(d)
+    for n, l in itertools.product(range(d), range(d)):
+        np.testing.assert_array_equal(Q[(n, l)], np.outer(I[n], I[l]))
+        np.testing.assert_array_equal(S[(n, l)], (n == l) * I + np.outer(I[l], I[n]))
+
+
+def rigid_modes(q):
+    d = q.shape[0]
+    modes = []
+    for c in range(d):
+        u = np.zeros((q.shape[1], d))
+        u[:, c] = 1.0
+        modes.append(u.ravel())
+    if d == 2:
+        modes.append(np.column_stack([-q[1], q[0]]).ravel())
+    else:
+        for axis in range(3):
+            w = np.zeros(3)
+            w[axis] = 1.0
+            modes.append(np.cross(w, q.T).ravel())
+    return modes
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_elasticity_rigid_modes_and_patch(d):
+    m = meshgen.square_mesh(6, seed=8) if d == 2 else meshgen.kuhn_cube_mesh(3, seed=8)
+    lam, mu = meshgen.lame_from_young(1.0, 0.3)
+    K = oracle.to_dense(oracle.assemble(oracle.ELAS, m.q, m.me, c1=lam, c2=mu))
+    np.testing.assert_allclose(K, K.T, atol=1e-13)
+    for u in rigid_modes(m.q):
+        assert np.abs(K @ u).max() < 1e-12
+    assert np.linalg.eigvalsh(K).min() > -1e-11
+    # patch test with a non-symmetric A of nonzero trace: u = A x has constant strain sym(A)
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(d, d))
+    u = (A @ m.q).T.ravel()  # alternate numbering: dof = d * vertex + component
+    epsA = 0.5 * (A + A.T)
+    energy = lam * np.trace(A) ** 2 + 2 * mu * np.sum(epsA * epsA)  # times |Omega| = 1
+    assert u @ K @ u == pytest.approx(energy, rel=1e-11)
+
+
+# ---------------------------------------------------------------- pattern
+@pytest.mark.parametrize("d", [2, 3])
+def test_pattern_brute_force(d):
+    m = meshgen.square_mesh(5, seed=10) if d == 2 else meshgen.kuhn_cube_mesh(2, seed=10)
+    res = oracle.assemble(oracle.STIFF, m.q, m.me)
+    adj = np.zeros((m.nq, m.nq), bool)
+    for k in range(m.nme):
+        for a in m.me[:, k]:
+            for b in m.me[:, k]:
+                adj[a, b] = True
+    r, c = np.nonzero(adj)  # row-major, sorted columns
+    assert res["nnz"] == len(r)
+    np.testing.assert_array_equal(np.repeat(np.arange(m.nq), np.diff(res["row_ptr"])), r)
+    np.testing.assert_array_equal(res["col_idx"], c)
+    edges = {tuple(sorted((int(a), int(b)))) for k in range(m.nme)
+             for a, b in itertools.combinations(m.me[:, k], 2)}
+    assert res["nnz"] == m.nq + 2 * len(edges)
+    # vector case: 3x3 / 2x2 blocks in the alternate numbering
+    lam, mu = meshgen.lame_from_young(1.0, 0.3)
+    re = oracle.assemble(oracle.ELAS, m.q, m.me, c1=lam, c2=mu)
+    assert re["nnz"] == d * d * res["nnz"]
+
+
+# ---------------------------------------------------------------- derivatives
+@pytest.mark.parametrize("d", [2, 3])
+def test_stiffness_loss_gradients(d):
+    m = meshgen.square_mesh(5, seed=11) if d == 2 else meshgen.kuhn_cube_mesh(2, seed=11)
+    w = meshgen.element_weights(11, m.nme)
+    u, v = meshgen.random_vectors(11, m.nq)
+    L, dw, dq = oracle.stiff_loss(m.q, m.me, w, u, v)
+    # L equals u^T K(w) v with the assembled matrix
+    K = oracle.to_dense(oracle.assemble(oracle.STIFF, m.q, m.me, c1=(oracle.COEF_P0, w)))
+    assert L == pytest.approx(u @ K @ v, rel=1e-12)
+    # L is linear in w: dL/dw_e times w_e sums to L
+    assert np.dot(dw, w) == pytest.approx(L, rel=1e-12)
+    # central differences in q and w
+    rng = np.random.default_rng(12)
+    h = 1e-6
+    for _ in range(12):
+        c, vtx = rng.integers(d), rng.integers(m.nq)
+        qp, qm = m.q.copy(), m.q.copy()
+        qp[c, vtx] += h
+        qm[c, vtx] -= h
+        fd = (oracle.stiff_loss(qp, m.me, w, u, v, False)[0] - oracle.stiff_loss(qm, m.me, w, u, v, False)[0]) / (2 * h)
+        assert dq[c, vtx] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(dq).max())
+    # invariances: translation (sum of dL/dq = 0) and rotation (sum q x dL/dq = 0)
+    assert np.abs(dq.sum(axis=1)).max() < 1e-11 * np.abs(dq).max() * m.nq
+    if d == 2:
+        torque = np.sum(m.q[0] * dq[1] - m.q[1] * dq[0])
+        assert abs(torque) < 1e-11 * np.abs(dq).max() * m.nq
+    else:
+        torque = np.cross(m.q.T, dq.T).sum(axis=0)
+        assert np.abs(torque).max() < 1e-11 * np.abs(dq).max() * m.nq
+
+
+# ---------------------------------------------------------------- errors
+def test_oracle_reports_bad_input():
+    m = meshgen.square_mesh(3, seed=0)
+    me = m.me.copy()
+    me[1, 5] = m.nq
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.assemble(oracle.STIFF, m.q, me)
+    assert e.value.code == 2 and e.value.bad_id == 5
+    q = m.q.copy()
+    a, b, c = m.me[:, 7]
+    q[:, c] = 0.5 * (q[:, a] + q[:, b])  # collapse element 7 (and maybe neighbours)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.assemble(oracle.STIFF, q, m.me)
+    assert e.value.code == 3
