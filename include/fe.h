@@ -1,0 +1,220 @@
+/*
+ * fe.h -- C ABI of the GB300 P1 finite element assembly library (libfe_gb300.so).
+ *
+ * The library computes the P1 Lagrange finite element matrices of a simplicial
+ * mesh (Cuvelier, Japhet, Scarella, "An efficient way to assemble finite element
+ * matrices in vector languages"): mass, weighted mass, stiffness and linear
+ * elasticity, and assembles them into CSR form with duplicate contributions
+ * summed, which is the `sparse(Ig, Jg, Kg, m, n)` constructor of Section 3.
+ *
+ * Conventions shared by every call
+ *   - Mesh (Section 2, Table 1): q is d x nq (coordinate c of vertex v at
+ *     q[c*nq + v], FP64), me is (d+1) x nme (vertex of local corner a of element k
+ *     at me[a*nme + k], int32, 0-BASED; the paper's arrays are 1-based).
+ *   - Vector problems use the alternate numbering of Section 5:
+ *     dof = m * vertex + component (0-based).
+ *   - Every pointer argument is a DEVICE pointer unless stated otherwise. The
+ *     caller owns q, me, coefficients and output arrays; the library owns the
+ *     arrays of a pattern handle until fe_pattern_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are stream-ordered and asynchronous except where stated.
+ *   - Every call returns an fe status code. Argument errors are detected on the
+ *     host before any launch. Data errors found by a kernel (a vertex index out
+ *     of range, a degenerate element) are recorded in the handle's device status
+ *     word; read it with fe_status(), which synchronises the stream.
+ *   - Results are bit-identical from run to run for the deterministic
+ *     reassembly strategies (FE_REASM_CHUNKED, FE_REASM_GATHER).
+ */
+#ifndef FE_GB300_H
+#define FE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes */
+#define FE_OK 0
+#define FE_ERR_ARG 1        /* invalid argument (host-side check) */
+#define FE_ERR_INDEX 2      /* me holds a vertex index outside [0, nq) */
+#define FE_ERR_DEGENERATE 3 /* an element has det B = 0 or a non-finite det B */
+#define FE_ERR_OVERFLOW 4   /* a size does not fit the library's 32-bit indices */
+#define FE_ERR_CUDA 5       /* a CUDA runtime call failed */
+#define FE_ERR_TIMEOUT 6    /* reserved: a bounded device-side wait gave up */
+#define FE_ERR_NOMEM 7      /* device allocation failed */
+
+/* ---- precision forms of the element and value kernels */
+#define FE_F64 0 /* FP64 arithmetic, FP64 values */
+#define FE_F32 1 /* FP32 values; det B and |K| from FP64-accurate coordinates
+                    differences in double-float arithmetic; compensated sums */
+
+/* ---- coefficient kinds (coefficient arrays use the precision of the form:
+ *      double for FE_F64, float for FE_F32) */
+#define FE_COEF_NONE 0        /* identically 1; pointer ignored */
+#define FE_COEF_SCALAR 1      /* one value, device pointer to it */
+#define FE_COEF_P0 2          /* one value per element, input element order */
+#define FE_COEF_P1 3          /* one value per vertex, P1-interpolated */
+#define FE_COEF_P0_INTERNAL 4 /* one value per element, in the pattern's internal
+                                 order (see fe_pattern_element_order) */
+
+/* ---- reassembly strategies */
+#define FE_REASM_CHUNKED 0 /* default: fused element + fixed-order on-chip sums over
+                              element chunks, then a fixed-order sum of the chunk
+                              partials of shared rows. Deterministic, no atomics. */
+#define FE_REASM_GATHER 1  /* two passes: element values to scratch, then each
+                              nonzero sums its slots in ascending slot order.
+                              Deterministic, no atomics. */
+#define FE_REASM_ATOMIC 2  /* fused element + atomicAdd scatter. NOT reproducible. */
+
+/* ---- pattern flags */
+#define FE_PATTERN_KEEP_ORDER 1 /* do not reorder elements internally (default:
+                                   Morton order of element centroids) */
+
+typedef struct fe_mesh {
+  int32_t d;          /* 2 or 3 */
+  int64_t nq;         /* number of vertices */
+  int64_t nme;        /* number of elements */
+  const double* q;    /* device, d x nq, FP64 */
+  const int32_t* me;  /* device, (d+1) x nme, 0-based */
+} fe_mesh;
+
+typedef struct fe_pattern_s* fe_pattern_h;
+
+/*
+ * fe_pattern -- build the sparsity pattern of the global matrix once per mesh
+ * topology. Index part of `sparse` (Section 3): the (Ig, Jg) pairs of every
+ * element slot (Algorithm 3: Ig(l,:) = me(a,:), Jg(l,:) = me(b,:); vector case
+ * Algorithm 9: Ig = m me(a,:) + l, Jg = m me(b,:) + n, 0-based) are sorted by
+ * a 64-bit key row * n + col with a device radix sort and run-length encoded.
+ * The matrix has order n = m nq; every (row, col) pair shared by an element is
+ * a structural nonzero, even when its value sums to zero. Column indices are
+ * sorted within each row.
+ *   m       dofs per vertex: 1 (mass, weighted mass, stiffness) or d (elasticity)
+ *   flags   FE_PATTERN_* bits
+ *   out     receives the handle. The pattern keeps a copy of me (internal order)
+ *           and coordinates are passed again to every assembly call, so q may
+ *           change between calls while me may not.
+ * Synchronous: returns after the pattern is complete. Errors: FE_ERR_ARG,
+ * FE_ERR_INDEX (me out of range), FE_ERR_OVERFLOW (more than 2^31-1 element
+ * slots, nonzeros or rows), FE_ERR_NOMEM, FE_ERR_CUDA.
+ */
+int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out);
+
+/* Borrowed CSR arrays (int32, device): row_ptr[n+1], col_idx[nnz]. */
+int fe_pattern_csr(fe_pattern_h h, int64_t* n, int64_t* nnz, const int32_t** row_ptr,
+                   const int32_t** col_idx);
+
+/*
+ * Borrowed slot maps of the SCALAR pattern (device, int32). A slot is one entry
+ * of one element matrix: slot id = e * (d+1)^2 + b (d+1) + a for element e in
+ * the internal order and local entry (a, b) (column-wise, Section 3).
+ *   slot2nnz[slot]         nonzero the slot is added to
+ *   nnz2slot[nnz_slot_ptr[j] .. nnz_slot_ptr[j+1]-1]  slots of nonzero j, ascending
+ */
+int fe_pattern_slot_map(fe_pattern_h h, const int32_t** slot2nnz, const int32_t** nnz_slot_ptr,
+                        const int32_t** nnz2slot);
+
+/* Copies of the CSR arrays into caller-owned device buffers (row_ptr[n+1],
+ * col_idx[nnz]); either pointer may be NULL. Stream-ordered. */
+int fe_pattern_copy_csr(fe_pattern_h h, int32_t* row_ptr, int32_t* col_idx, void* stream);
+
+/* Copies of the scalar slot maps (sizes as in fe_pattern_slot_map) and of the
+ * internal element order (nme) into caller-owned device buffers; any may be NULL. */
+int fe_pattern_copy_slot_map(fe_pattern_h h, int32_t* slot2nnz, int32_t* nnz_slot_ptr,
+                             int32_t* nnz2slot, int32_t* order, void* stream);
+
+/* Dimensions of a pattern: d, m, nq, nme, n = m nq, nnz. Any pointer may be NULL. */
+int fe_pattern_dims(fe_pattern_h h, int32_t* d, int32_t* m, int64_t* nq, int64_t* nme, int64_t* n,
+                    int64_t* nnz);
+
+/* Borrowed internal element order (device int32[nme]): internal element e is
+ * input element order[e]. Identity under FE_PATTERN_KEEP_ORDER. */
+int fe_pattern_element_order(fe_pattern_h h, const int32_t** order);
+
+/* Select the reassembly strategy used by later fe_assemble_* calls. Strategies
+ * that need scratch memory allocate it here (synchronously), never inside an
+ * assembly call. */
+int fe_pattern_set_strategy(fe_pattern_h h, int32_t strategy);
+
+/* Device bytes held by the handle (pattern, plan and scratch). */
+int fe_pattern_memory(fe_pattern_h h, int64_t* bytes);
+
+/* Counts of the element-chunk plan used by FE_REASM_CHUNKED (for roofline
+ * accounting): chunk size, local vertices, local edges, partial sums. */
+int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices,
+                         int64_t* local_edges, int64_t* partials, int64_t* plan_bytes);
+
+int fe_pattern_destroy(fe_pattern_h h);
+
+/*
+ * Read and clear the device status word of h (synchronises `stream`).
+ * *code is an FE_ERR_* (FE_OK if none) and *id the smallest offending element
+ * (input element order) or -1.
+ */
+int fe_status(fe_pattern_h h, void* stream, int32_t* code, int64_t* id);
+
+/*
+ * Assembly into the fixed pattern of h (the value part of `sparse`). `vals`
+ * receives nnz values, double for FE_F64 and float for FE_F32, in CSR order.
+ * The pattern must have been built with m = 1.
+ *
+ * fe_assemble_mass  -- M_ij = int phi_j phi_i: local |K| d!/(d+2)! (1 + delta_ab),
+ *                      i.e. |K|/12 (2D) and |K|/20 (3D) (Section 4.1, w = 1).
+ * fe_assemble_wmass -- weighted mass int w phi_j phi_i (Eq. massw) with w given
+ *                      per vertex and P1-interpolated (Eq. MatElemMassWP1:
+ *                      d!/(d+3)! |K| (1 + delta_ab)(w^s + w_a + w_b)), or per
+ *                      element (P0: w_K times the mass matrix). w_kind is
+ *                      FE_COEF_P1, FE_COEF_P0 or FE_COEF_P0_INTERNAL.
+ * fe_assemble_stiff -- S_ij = int w grad phi_j . grad phi_i with local
+ *                      w_K |K| <grad lambda_b, grad lambda_a> (Eq. stiffelemmat,
+ *                      Algorithm 7); w per element (FE_COEF_P0 or
+ *                      FE_COEF_P0_INTERNAL) or FE_COEF_NONE.
+ * Asynchronous on `stream`. Degenerate elements set FE_ERR_DEGENERATE in the
+ * status word and leave `vals` unspecified.
+ */
+int fe_assemble_mass(fe_pattern_h h, const double* q, int32_t prec, void* vals, void* stream);
+int fe_assemble_wmass(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
+                      int32_t prec, void* vals, void* stream);
+int fe_assemble_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
+                      int32_t prec, void* vals, void* stream);
+
+/*
+ * fe_assemble_elas -- elastic stiffness (Eq. StiffElasMat, Section 5.1) for an
+ * isotropic Hooke law, pattern built with m = d. Local entry
+ *   K_{(a,l),(b,n)} = |K|/(d+1) (lambda^s <g_b, Q^{n,l} g_a> + mu^s <g_b, S^{n,l} g_a>)
+ * with Q^{n,l} = e_n e_l^T and S^{n,l} = delta_nl I + e_l e_n^T (Lemma
+ * lem:VecLocalElas, App. B), lambda^s and mu^s the sums of the vertex values of
+ * the P1 interpolants (a P0 or scalar coefficient counts as d+1 equal values).
+ * lam_kind / mu_kind: FE_COEF_SCALAR, FE_COEF_P0, FE_COEF_P0_INTERNAL or FE_COEF_P1.
+ */
+int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t lam_kind,
+                     const void* mu, int32_t mu_kind, int32_t prec, void* vals, void* stream);
+
+/*
+ * fe_assemble_stiff_backward -- gradients of L = u^T S(w) v, S the stiffness
+ * matrix of fe_assemble_stiff (the paper has no derivatives; these follow from
+ * Eq. stiffelemmat and App. C.1):
+ *   dL/dw_K = |K| ubar . vbar,  ubar = sum_a u(me(a,K)) grad lambda_a (same for v),
+ *   dL/dq^c = sum_K w_K |K| [(ubar . vbar) g_c - ubar (g_c . vbar) - vbar (g_c . ubar)].
+ * u, v: nq values; dL_dw: nme values in the order given by w_kind (input order
+ * for FE_COEF_NONE/FE_COEF_P0, internal for FE_COEF_P0_INTERNAL), may be NULL;
+ * dL_dq: d x nq like q, may be NULL; L: one value (device), may be NULL. All of
+ * u, v, dL_dw, dL_dq, L use the precision of the form. Vertex sums are taken in a
+ * fixed order (bit-identical run to run).
+ */
+int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
+                               const void* u, const void* v, void* L, void* dL_dw, void* dL_dq,
+                               int32_t prec, void* stream);
+
+/* Library version string (host pointer, static). */
+const char* fe_version(void);
+
+/* Text of the last CUDA runtime error seen by the library (host pointer, static;
+ * empty if none). */
+const char* fe_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_GB300_H */

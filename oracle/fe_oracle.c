@@ -157,9 +157,11 @@ static void hooke(int d, double lam, double mu, double C[6][6]) {
 
 /*
  * Local matrix of one element, column-wise: E[j*nl + i], nl = m (d+1), local
- * index i = a m + l for vertex a, component l. S receives the "condition scale"
- * of every entry: the same expression with every product replaced by its absolute
- * value (used by the tests to normalise errors of cancelling sums).
+ * index i = a m + l for vertex a, component l. S receives the normwise scale of
+ * every entry, used by the tests to normalise errors of cancelling sums: the
+ * entry itself for (weighted) mass (|.| of each term), w |K| |grad lambda_a|
+ * |grad lambda_b| for stiffness and (|lambda^| + 2 |mu^|) |grad lambda_a|
+ * |grad lambda_b| for elasticity (lambda^, mu^ the integrals of the Lame fields).
  * cv1 / cv2 are the vertex values of the coefficient(s) (P1 interpolation; a
  * scalar or P0 coefficient is passed as d+1 equal values).
  */
@@ -195,22 +197,27 @@ int orc_element(int kind, int d, const double* X, const double* cv1, const doubl
     double w = cv1 ? cv1[0] : 1.0;
     for (int b = 0; b < nv; ++b)
       for (int a = 0; a < nv; ++a) {
-        double s = 0.0, sa = 0.0;
+        double s = 0.0, na = 0.0, nb = 0.0;
         for (int i = 0; i < d; ++i) {
           s += G[b * d + i] * G[a * d + i];
-          sa += fabs(G[b * d + i] * G[a * d + i]);
+          na += G[a * d + i] * G[a * d + i];
+          nb += G[b * d + i] * G[b * d + i];
         }
         E[b * nv + a] = w * vol * s;
-        S[b * nv + a] = fabs(w) * vol * sa;
+        S[b * nv + a] = fabs(w) * vol * sqrt(na * nb);
       }
     return ORC_OK;
   }
   if (kind == ORC_ELAS) {
     int m = d, nl = m * nv, ns = (d == 2) ? 3 : 6;
     double lam = p1_integral(d, cv1, vol), mu = p1_integral(d, cv2, vol);
-    double C[6][6], Ca[6][6];
+    double C[6][6], ga_norm[4];
     hooke(d, lam, mu, C);
-    hooke(d, fabs(lam), fabs(mu), Ca);
+    for (int a = 0; a < nv; ++a) {
+      double t = 0.0;
+      for (int i = 0; i < d; ++i) t += G[a * d + i] * G[a * d + i];
+      ga_norm[a] = sqrt(t);
+    }
     for (int b = 0; b < nv; ++b)
       for (int n = 0; n < m; ++n) {
         double eb[6];
@@ -221,14 +228,11 @@ int orc_element(int kind, int d, const double* X, const double* cv1, const doubl
             double ea[6];
             strain_vector(d, &G[a * d], l, ea);
             int i = a * m + l;
-            double s = 0.0, sa = 0.0;
+            double s = 0.0;
             for (int r = 0; r < ns; ++r)
-              for (int c = 0; c < ns; ++c) {
-                s += eb[r] * C[r][c] * ea[c];
-                sa += fabs(eb[r] * Ca[r][c] * ea[c]);
-              }
+              for (int c = 0; c < ns; ++c) s += eb[r] * C[r][c] * ea[c];
             E[j * nl + i] = s;
-            S[j * nl + i] = sa;
+            S[j * nl + i] = (fabs(lam) + 2.0 * fabs(mu)) * ga_norm[a] * ga_norm[b];
           }
       }
     return ORC_OK;

@@ -1,0 +1,4 @@
+// Scalar operators, FP64 form.
+#define FE_T double
+#define FE_LAUNCH_SCALAR fe_launch_scalar_f64
+#include "assemble_scalar.inc"

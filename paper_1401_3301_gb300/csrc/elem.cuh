@@ -1,0 +1,237 @@
+// Per-element geometry and local matrices (device functions).
+//
+// Geometry (App. C.1 of the paper): B = [q^1 - q^0, ..., q^d - q^0]; the barycentric
+// gradients are grad lambda_i = B^{-T} e_i (i >= 1) and grad lambda_0 = -sum_i grad
+// lambda_i. Written with the cofactor vectors c_i (rows of adj(B)), grad lambda_i =
+// c_i / det B, so every local matrix is a polynomial in c and 1/det:
+//   stiffness (Eq. stiffelemmat): |K| g_a . g_b = (c_a . c_b) / (d! |det B|)
+//   mass (Section 4.1, w = 1):    |K| d!/(d+2)! (1 + delta) = |det B| (1 + delta) / (d+2)!
+//   P1 weighted mass (Eq. MatElemMassWP1): |det B| (1 + delta)(w^s + w_a + w_b) / (d+3)!
+//   elasticity (Lemma lem:VecLocalElas): entry ((a,l),(b,n)) =
+//       lam' c_a[l] c_b[n] + mu' (delta_ln c_a . c_b + c_b[l] c_a[n]),
+//       lam' = lambda^s / (d! (d+1) |det B|), mu' likewise.
+// FP64 form: everything in double. FP32 form: coordinates arrive split into
+// (hi, lo) float pairs; edge vectors and det B are formed in double-float
+// arithmetic (FP64-class accuracy on the FP32 pipe), cofactors and values in float.
+#pragma once
+
+#include <stdint.h>
+
+namespace fe {
+
+// ---------------------------------------------------------------- double-float helpers
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  const df t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+// Exact-ish split of a double into two floats: hi = x truncated to 24 significant
+// bits, lo = the next 24 bits, so |x - hi - lo| < 2^-47 |x|. Integer operations
+// only (the FP64 and conversion pipes are slow on this part). Inputs with
+// |x| < 2^-100 are flushed to zero; |x| >= 2^128 gives an infinite hi.
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned long long man = b & 0xFFFFFFFFFFFFFull;
+  const int E = ex - 1023;
+  if (ex == 0 || E < -100) { hi = 0.f; lo = 0.f; return; }
+  if (E > 127) { hi = __int_as_float(sign | 0x7F800000u); lo = 0.f; return; }
+  hi = __int_as_float(sign | ((unsigned int)(E + 127) << 23) | (unsigned int)(man >> 29));
+  const unsigned int r = (unsigned int)(man & 0x1FFFFFFFull);
+  if (r == 0u) { lo = 0.f; return; }
+  const int lz = __clz(r);
+  const int eo = (31 - lz) + E - 52 + 127;
+  if (eo <= 0) { lo = 0.f; return; }
+  lo = __int_as_float(sign | ((unsigned int)eo << 23) | ((r << (lz + 1)) >> 9));
+}
+
+// compensated float accumulator (two-sum, Knuth)
+struct csum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const df t = two_sum(s, x);
+    s = t.hi;
+    c = __fadd_rn(c, t.lo);
+  }
+  __device__ __forceinline__ void add2(float xs, float xc) {
+    add(xs);
+    c = __fadd_rn(c, xc);
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
+
+// ---------------------------------------------------------------- geometry
+// Cofactor vectors c[a][i] (a = 0..d; c[0] = -sum) and det B.
+template <int D, class T>
+struct Geo {
+  T c[D + 1][D];
+  T det;  // FP64 form: det B; FP32 form: det B rounded to float
+};
+
+__device__ __forceinline__ void geo_from_edges3(const double e[3][3], Geo<3, double>& g) {
+  // c_1 = e_2 x e_3, c_2 = e_3 x e_1, c_3 = e_1 x e_2 (rows of adj(B), B = [e_1 e_2 e_3])
+  const double* e1 = e[0]; const double* e2 = e[1]; const double* e3 = e[2];
+  g.c[1][0] = e2[1] * e3[2] - e2[2] * e3[1];
+  g.c[1][1] = e2[2] * e3[0] - e2[0] * e3[2];
+  g.c[1][2] = e2[0] * e3[1] - e2[1] * e3[0];
+  g.c[2][0] = e3[1] * e1[2] - e3[2] * e1[1];
+  g.c[2][1] = e3[2] * e1[0] - e3[0] * e1[2];
+  g.c[2][2] = e3[0] * e1[1] - e3[1] * e1[0];
+  g.c[3][0] = e1[1] * e2[2] - e1[2] * e2[1];
+  g.c[3][1] = e1[2] * e2[0] - e1[0] * e2[2];
+  g.c[3][2] = e1[0] * e2[1] - e1[1] * e2[0];
+  g.det = e1[0] * g.c[1][0] + e1[1] * g.c[1][1] + e1[2] * g.c[1][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) g.c[0][i] = -(g.c[1][i] + g.c[2][i] + g.c[3][i]);
+}
+
+__device__ __forceinline__ void geo_from_edges2(const double e[2][2], Geo<2, double>& g) {
+  // B = [e_1 e_2]; adj(B) rows: c_1 = (e_2y, -e_2x), c_2 = (-e_1y, e_1x)
+  g.c[1][0] = e[1][1];
+  g.c[1][1] = -e[1][0];
+  g.c[2][0] = -e[0][1];
+  g.c[2][1] = e[0][0];
+  g.det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+  g.c[0][0] = -(g.c[1][0] + g.c[2][0]);
+  g.c[0][1] = -(g.c[1][1] + g.c[2][1]);
+}
+
+// FP64 geometry from SoA coordinates
+template <int D>
+__device__ __forceinline__ void geo_f64(const double* __restrict__ q, int64_t nq, const int32_t v[D + 1],
+                                        Geo<D, double>& g) {
+  double x[D + 1][D];
+#pragma unroll
+  for (int a = 0; a <= D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[a][c] = __ldg(q + (int64_t)c * nq + v[a]);
+  double e[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) e[i][c] = x[i + 1][c] - x[0][c];
+  if constexpr (D == 3) geo_from_edges3(e, g);
+  else geo_from_edges2(e, g);
+}
+
+// FP32 geometry from split coordinates: qs holds, per vertex, float4 (hi) and float4 (lo)
+// in 3D, or one float4 (xh, yh, xl, yl) in 2D.
+template <int D>
+__device__ __forceinline__ void geo_f32(const float4* __restrict__ qs, const int32_t v[D + 1],
+                                        Geo<D, float>& g) {
+  float xh[D + 1][D], xl[D + 1][D];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    if constexpr (D == 3) {
+      const float4 h = __ldg(qs + 2 * (int64_t)v[a]);
+      const float4 l = __ldg(qs + 2 * (int64_t)v[a] + 1);
+      xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
+      xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
+    } else {
+      const float4 h = __ldg(qs + (int64_t)v[a]);
+      xh[a][0] = h.x; xh[a][1] = h.y;
+      xl[a][0] = h.z; xl[a][1] = h.w;
+    }
+  }
+  // double-float edges e = (xh_i - xh_0) + (xl_i - xl_0)
+  df e[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const df s = two_sum(xh[i + 1][c], -xh[0][c]);
+      e[i][c] = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][c], xl[0][c])));
+    }
+  float eh[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) eh[i][c] = e[i][c].hi;
+  if constexpr (D == 3) {
+    // det B = e_1 . (e_2 x e_3) in double-float
+    const df cx = df_add(df_mul(e[1][1], e[2][2]), df_neg(df_mul(e[1][2], e[2][1])));
+    const df cy = df_add(df_mul(e[1][2], e[2][0]), df_neg(df_mul(e[1][0], e[2][2])));
+    const df cz = df_add(df_mul(e[1][0], e[2][1]), df_neg(df_mul(e[1][1], e[2][0])));
+    const df dt = df_add(df_add(df_mul(e[0][0], cx), df_mul(e[0][1], cy)), df_mul(e[0][2], cz));
+    g.det = __fadd_rn(dt.hi, dt.lo);
+    const float* e1 = eh[0]; const float* e2 = eh[1]; const float* e3 = eh[2];
+    g.c[1][0] = e2[1] * e3[2] - e2[2] * e3[1];
+    g.c[1][1] = e2[2] * e3[0] - e2[0] * e3[2];
+    g.c[1][2] = e2[0] * e3[1] - e2[1] * e3[0];
+    g.c[2][0] = e3[1] * e1[2] - e3[2] * e1[1];
+    g.c[2][1] = e3[2] * e1[0] - e3[0] * e1[2];
+    g.c[2][2] = e3[0] * e1[1] - e3[1] * e1[0];
+    g.c[3][0] = e1[1] * e2[2] - e1[2] * e2[1];
+    g.c[3][1] = e1[2] * e2[0] - e1[0] * e2[2];
+    g.c[3][2] = e1[0] * e2[1] - e1[1] * e2[0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g.c[0][i] = -(g.c[1][i] + g.c[2][i] + g.c[3][i]);
+  } else {
+    const df dt = df_add(df_mul(e[0][0], e[1][1]), df_neg(df_mul(e[0][1], e[1][0])));
+    g.det = __fadd_rn(dt.hi, dt.lo);
+    g.c[1][0] = eh[1][1];
+    g.c[1][1] = -eh[1][0];
+    g.c[2][0] = -eh[0][1];
+    g.c[2][1] = eh[0][0];
+    g.c[0][0] = -(g.c[1][0] + g.c[2][0]);
+    g.c[0][1] = -(g.c[1][1] + g.c[2][1]);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ bool det_ok(T det) {
+  const T a = det < T(0) ? -det : det;
+  return a > T(0) && a <= (sizeof(T) == 8 ? T(1.7976931348623157e308) : T(3.4028234663852886e38));
+}
+
+template <class T>
+__device__ __forceinline__ T recip(T x);
+template <>
+__device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
+template <>
+__device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+
+__host__ __device__ constexpr int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
+
+// local pair numbering p = 0..npair-1 over a < b, lexicographic
+template <int D>
+struct Pairs;
+template <>
+struct Pairs<2> {
+  static constexpr int n = 3;
+  __device__ static constexpr int a(int p) { return p == 2 ? 1 : 0; }
+  __device__ static constexpr int b(int p) { return p == 0 ? 1 : 2; }
+};
+template <>
+struct Pairs<3> {
+  static constexpr int n = 6;
+  __device__ static constexpr int a(int p) { return p < 3 ? 0 : (p < 5 ? 1 : 2); }
+  __device__ static constexpr int b(int p) { return p < 3 ? p + 1 : (p < 5 ? p - 1 : 3); }
+};
+
+}  // namespace fe

@@ -1,0 +1,609 @@
+// Pattern build (once per mesh topology): the index part of the paper's `sparse`
+// constructor (Section 3, Algorithms 2-3 and 9), plus the element-chunk plan used
+// by the fused deterministic reassembly.
+//
+// Steps, all on the device:
+//   1. check me against [0, nq);
+//   2. internal element order: Morton code of each element centroid, radix-sorted
+//      (stable, so equal codes keep input order);
+//   3. one 64-bit key row * nq + col per element slot (scalar pattern), radix-sorted
+//      with the slot id as value, then run-length encoded into CSR (col_idx,
+//      row_ptr), slot2nnz and the slot lists of each nonzero;
+//   4. vector problems (m = d): the scalar pattern expanded into m x m blocks in
+//      the alternate numbering dof = m v + component;
+//   5. element-chunk plan: elements are cut into chunks of C consecutive internal
+//      elements; per chunk, the distinct vertices and edges it touches, the
+//      (element, corner) and (element, edge) incidences of each, in ascending
+//      element order, and where each per-chunk sum goes (the CSR value itself if
+//      the chunk holds every element of that vertex or edge, else a partial-sum
+//      slot that a second pass adds up in chunk order).
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <vector>
+
+#include "fe_internal.cuh"
+
+namespace {
+
+__host__ __device__ __forceinline__ int bitlen(uint64_t x) {
+  int b = 0;
+  while (x) { ++b; x >>= 1; }
+  return b;
+}
+
+__global__ void k_check_me(const int32_t* me, int64_t nme, int nv, int64_t nq, fe_status_word* st) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    for (int a = 0; a < nv; ++a) {
+      const int32_t v = me[(int64_t)a * nme + k];
+      if (v < 0 || v >= nq) { fe_report(st, FE_ERR_INDEX, k); break; }
+    }
+  }
+}
+
+// per-block min/max of each coordinate; out[blk * 2d + c] = min, out[blk * 2d + d + c] = max
+__global__ void k_bbox_partial(const double* q, int64_t nq, int d, double* out) {
+  __shared__ double smin[3][256], smax[3][256];
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nq;
+       v += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < d; ++c) {
+      const double x = q[(int64_t)c * nq + v];
+      lo[c] = fmin(lo[c], x);
+      hi[c] = fmax(hi[c], x);
+    }
+  for (int c = 0; c < d; ++c) { smin[c][threadIdx.x] = lo[c]; smax[c][threadIdx.x] = hi[c]; }
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int c = 0; c < d; ++c) {
+        smin[c][threadIdx.x] = fmin(smin[c][threadIdx.x], smin[c][threadIdx.x + s]);
+        smax[c][threadIdx.x] = fmax(smax[c][threadIdx.x], smax[c][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < d; ++c) {
+      out[blockIdx.x * 2 * d + c] = smin[c][0];
+      out[blockIdx.x * 2 * d + d + c] = smax[c][0];
+    }
+}
+
+__global__ void k_bbox_final(double* part, int nblk, int d) {
+  if (threadIdx.x != 0) return;
+  for (int c = 0; c < d; ++c) {
+    double lo = part[c], hi = part[d + c];
+    for (int b = 1; b < nblk; ++b) {
+      lo = fmin(lo, part[b * 2 * d + c]);
+      hi = fmax(hi, part[b * 2 * d + d + c]);
+    }
+    part[c] = lo;
+    part[d + c] = hi;
+  }
+}
+
+__device__ __forceinline__ uint64_t spread_bits(uint64_t x, int d) {
+  uint64_t r = 0;
+  for (int b = 0; b < 21; ++b) r |= ((x >> b) & 1ull) << (b * d);
+  return r;
+}
+
+__global__ void k_morton_keys(const double* q, int64_t nq, const int32_t* me, int64_t nme, int d,
+                              const double* bbox, int qbits, uint64_t* keys, uint32_t* vals) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nme) return;
+  const double scale = (double)(1u << qbits);
+  uint64_t code = 0;
+  for (int c = 0; c < d; ++c) {
+    double s = 0.0;
+    for (int a = 0; a <= d; ++a) s += q[(int64_t)c * nq + me[(int64_t)a * nme + k]];
+    s /= (double)(d + 1);
+    const double lo = bbox[c], hi = bbox[d + c];
+    double t = (hi > lo) ? (s - lo) / (hi - lo) : 0.0;
+    t = fmin(fmax(t, 0.0), 1.0);
+    uint64_t iq = (uint64_t)(t * scale);
+    if (iq >= (1ull << qbits)) iq = (1ull << qbits) - 1;
+    code |= spread_bits(iq, d) << c;
+  }
+  keys[k] = code;
+  vals[k] = (uint32_t)k;
+}
+
+__global__ void k_iota(uint32_t* v, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_permute_me(const int32_t* me, int64_t nme, int nv, const uint32_t* order,
+                             int32_t* me_int, int32_t* order_out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nme) return;
+  const int64_t k = order[e];
+  for (int a = 0; a < nv; ++a) me_int[(int64_t)a * nme + e] = me[(int64_t)a * nme + k];
+  order_out[e] = (int32_t)k;
+}
+
+// keys of the scalar slots: slot = e * nv^2 + b * nv + a, (row, col) = (me(a,e), me(b,e))
+__global__ void k_slot_keys(const int32_t* me_int, int64_t nme, int nv, int64_t nq, uint64_t* keys,
+                            uint32_t* vals) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int S = nv * nv;
+  if (s >= nme * S) return;
+  const int64_t e = s / S;
+  const int loc = (int)(s - e * S);
+  const int a = loc % nv, b = loc / nv;
+  const uint64_t row = (uint64_t)me_int[(int64_t)a * nme + e];
+  const uint64_t col = (uint64_t)me_int[(int64_t)b * nme + e];
+  keys[s] = row * (uint64_t)nq + col;
+  vals[s] = (uint32_t)s;
+}
+
+__global__ void k_key_change(const uint64_t* keys, int64_t n, uint32_t* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+// flag is overwritten by its exclusive scan in pos; recompute the flag from keys
+__global__ void k_rle_scalar(const uint64_t* keys, const uint32_t* vals, const uint32_t* pos,
+                             int64_t n, int64_t nq, int32_t* col_idx, int32_t* row_ptr,
+                             int32_t* nnz_slot_ptr, int32_t* slot2nnz) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t key = keys[i];
+  const bool head = (i == 0) || key != keys[i - 1];
+  const uint32_t j = pos[i] + (head ? 1u : 0u) - 1u;
+  slot2nnz[vals[i]] = (int32_t)j;
+  if (!head) return;
+  col_idx[j] = (int32_t)(key % (uint64_t)nq);
+  nnz_slot_ptr[j] = (int32_t)i;
+  const int64_t r = (int64_t)(key / (uint64_t)nq);
+  const int64_t rprev = (i == 0) ? -1 : (int64_t)(keys[i - 1] / (uint64_t)nq);
+  for (int64_t rr = rprev + 1; rr <= r; ++rr) row_ptr[rr] = (int32_t)j;
+}
+
+__global__ void k_rle_tail(const uint64_t* keys, int64_t n, int64_t nq, int64_t nnz,
+                           int32_t* row_ptr, int32_t* nnz_slot_ptr) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int64_t rlast = (n > 0) ? (int64_t)(keys[n - 1] / (uint64_t)nq) : -1;
+  for (int64_t rr = rlast + 1; rr <= nq; ++rr) row_ptr[rr] = (int32_t)nnz;
+  nnz_slot_ptr[nnz] = (int32_t)n;
+}
+
+// m x m block expansion of the scalar CSR (alternate numbering dof = m v + l)
+__global__ void k_expand_csr(const int32_t* rp, const int32_t* ci, int64_t nq, int m,
+                             int32_t* rp_e, int32_t* ci_e) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const int32_t r0 = rp[i], len = rp[i + 1] - rp[i];
+  for (int l = 0; l < m; ++l) {
+    const int64_t base = (int64_t)m * m * r0 + (int64_t)l * m * len;
+    rp_e[(int64_t)m * i + l] = (int32_t)base;
+    for (int jj = 0; jj < len; ++jj)
+      for (int n = 0; n < m; ++n) ci_e[base + (int64_t)m * jj + n] = m * ci[r0 + jj] + n;
+  }
+  if (i == nq - 1) rp_e[(int64_t)m * nq] = (int32_t)((int64_t)m * m * rp[nq]);
+}
+
+__device__ __forceinline__ int32_t find_nnz(const int32_t* rp, const int32_t* ci, int32_t r,
+                                            int32_t c) {
+  int32_t lo = rp[r], hi = rp[r + 1] - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (ci[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// vertex incidences: entry i = e * nv + a, key (chunk, vertex), value e_local * nv + a
+__global__ void k_vinc_keys(const int32_t* me_int, int64_t nme, int nv, int chunk, int vbits,
+                            uint64_t* keys, uint32_t* vals) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nme * nv) return;
+  const int64_t e = i / nv;
+  const int a = (int)(i - e * nv);
+  const uint64_t c = (uint64_t)(e / chunk);
+  keys[i] = (c << vbits) | (uint64_t)me_int[(int64_t)a * nme + e];
+  vals[i] = (uint32_t)((e % chunk) * nv + a);
+}
+
+// edge incidences: entry i = e * npair + p, key (chunk, vmin, vmax),
+// value ((e_local * npair + p) << 1) | (me(a) > me(b)) for pair p = (a, b), a < b
+__global__ void k_einc_keys(const int32_t* me_int, int64_t nme, int nv, int npair, int chunk,
+                            int vbits, uint64_t* keys, uint32_t* vals) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nme * npair) return;
+  const int64_t e = i / npair;
+  const int p = (int)(i - e * npair);
+  int a = 0, b = 1, cnt = 0;
+  for (int x = 0; x < nv; ++x)
+    for (int y = x + 1; y < nv; ++y) {
+      if (cnt == p) { a = x; b = y; }
+      ++cnt;
+    }
+  const uint64_t va = (uint64_t)me_int[(int64_t)a * nme + e];
+  const uint64_t vb = (uint64_t)me_int[(int64_t)b * nme + e];
+  const uint64_t lo = va < vb ? va : vb, hi = va < vb ? vb : va;
+  const uint64_t c = (uint64_t)(e / chunk);
+  keys[i] = (c << (2 * vbits)) | (lo << vbits) | hi;
+  vals[i] = (uint32_t)((((e % chunk) * npair + p) << 1) | (va > vb ? 1 : 0));
+}
+
+// Local entities from sorted incidence keys. For a head at sorted position i with
+// entity index u = pos[i]: offset within the chunk's incidences, chunk start, and the
+// global destination(s). Shared entities are flagged for the partial-sum pass.
+__global__ void k_local_entities(const uint64_t* keys, const uint32_t* pos, int64_t n, int per_elem,
+                                 int chunk, int ebits, int vbits, bool edges, const int32_t* rp,
+                                 const int32_t* ci, const int32_t* nnz_slot_ptr, uint16_t* off,
+                                 int32_t* ch_ptr, int32_t* dst, int32_t* vid, uint32_t* shared_flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t key = keys[i];
+  if (i > 0 && keys[i - 1] == key) return;
+  const uint32_t u = pos[i];
+  const uint64_t c = key >> ebits;
+  int64_t end = i + 1;
+  while (end < n && keys[end] == key) ++end;
+  const int32_t local_count = (int32_t)(end - i);
+  off[u] = (uint16_t)(i - (int64_t)c * chunk * per_elem);
+  if (i == 0 || (keys[i - 1] >> ebits) != c) ch_ptr[c] = (int32_t)u;
+  const uint64_t vmask = (1ull << vbits) - 1ull;
+  int32_t global_count;
+  if (!edges) {
+    const int32_t v = (int32_t)(key & vmask);
+    const int32_t dnz = find_nnz(rp, ci, v, v);
+    dst[u] = dnz;
+    vid[u] = v;
+    global_count = nnz_slot_ptr[dnz + 1] - nnz_slot_ptr[dnz];
+  } else {
+    const int32_t hi = (int32_t)(key & vmask), lo = (int32_t)((key >> vbits) & vmask);
+    const int32_t nij = find_nnz(rp, ci, lo, hi), nji = find_nnz(rp, ci, hi, lo);
+    dst[2 * (int64_t)u] = nij;
+    dst[2 * (int64_t)u + 1] = nji;
+    global_count = nnz_slot_ptr[nij + 1] - nnz_slot_ptr[nij];
+  }
+  shared_flag[u] = (local_count < global_count) ? 1u : 0u;
+}
+
+__global__ void k_to_u16(const uint32_t* v, uint16_t* o, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) o[i] = (uint16_t)v[i];
+}
+
+__global__ void k_entity_change(const uint64_t* k, int64_t n, int cb, uint32_t* f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) f[i] = (i == 0 || (k[i] >> cb) != (k[i - 1] >> cb)) ? 1u : 0u;
+}
+
+__global__ void k_set_last(int32_t* p, int64_t idx, int32_t value) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) p[idx] = value;
+}
+
+// keys (global entity nnz, chunk) of the shared local entities, compacted with spos
+__global__ void k_shared_keys(const uint32_t* shared_flag, const uint32_t* spos, int64_t nloc,
+                              const int32_t* dst, int dst_stride, const int32_t* ch_ptr,
+                              int64_t nchunks, int cbits, uint64_t* keys, uint32_t* vals) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= nloc || !shared_flag[u]) return;
+  // chunk of local entity u: last c with ch_ptr[c] <= u
+  int64_t lo = 0, hi = nchunks - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (ch_ptr[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  const uint32_t s = spos[u];
+  keys[s] = ((uint64_t)dst[(int64_t)u * dst_stride] << cbits) | (uint64_t)lo;
+  vals[s] = (uint32_t)u;
+}
+
+// after sorting shared keys: partial index of each shared local entity and the
+// fixup lists (ranges of partials per global entity, destinations)
+__global__ void k_shared_finish(const uint64_t* keys, const uint32_t* vals, const uint32_t* gpos,
+                                int64_t n, int cbits, int64_t part_base, int64_t ent_base,
+                                int32_t* dst, int dst_stride, const int32_t* vid, bool edges,
+                                int32_t* sh_ptr, int32_t* sh_dst, int32_t* lv_dst_or_null) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t u = vals[i];
+  const uint64_t ent = keys[i] >> cbits;
+  const bool head = (i == 0) || (keys[i - 1] >> cbits) != ent;
+  if (head) {
+    const int64_t g = ent_base + gpos[i];
+    sh_ptr[g] = (int32_t)(part_base + i);
+    if (!edges) {
+      sh_dst[2 * g] = dst[(int64_t)u * dst_stride];
+      sh_dst[2 * g + 1] = vid[u];
+    } else {
+      sh_dst[2 * g] = dst[(int64_t)u * dst_stride];
+      sh_dst[2 * g + 1] = dst[(int64_t)u * dst_stride + 1];
+    }
+  }
+  dst[(int64_t)u * dst_stride] = -1 - (int32_t)(part_base + i);
+  (void)lv_dst_or_null;
+}
+
+struct dev_tmp {
+  std::vector<void*> ptrs;
+  ~dev_tmp() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  int get(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (count > 0 ? count : 1) * sizeof(T));
+    if (e != cudaSuccess) return fe_cuda_fail(e);
+    ptrs.push_back(q);
+    *p = (T*)q;
+    return FE_OK;
+  }
+};
+
+template <class T>
+int to_host(T* dst, const T* src, cudaStream_t s) {
+  FE_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T), cudaMemcpyDeviceToHost, s));
+  FE_CUDA_TRY(cudaStreamSynchronize(s));
+  return FE_OK;
+}
+
+int default_chunk(int d, int m) {
+  const char* env = getenv("FE_CHUNK");
+  if (env) {
+    const int c = atoi(env);
+    if (c >= 32 && c <= 4096) return c;
+  }
+  if (m == 1) return d == 3 ? 1024 : 2048;
+  return d == 3 ? 256 : 512;
+}
+
+// Builds the element-chunk plan. sort buffers sized for max(nv, npair) * nme keys.
+int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStream_t s) {
+  const int nv = h->nv, npair = h->npair, C = h->chunk;
+  const int64_t nme = h->nme;
+  h->nchunks = (nme + C - 1) / C;
+  const int cbits = bitlen((uint64_t)(h->nchunks > 1 ? h->nchunks - 1 : 1));
+  const int vbits = bitlen((uint64_t)(h->nq > 1 ? h->nq - 1 : 1));
+  const int T = 256;
+  uint32_t *flag, *pos;
+  const int64_t nmax = nme * (nv > npair ? nv : npair);
+  FE_TRY(tmp.get(&flag, nmax + 1));
+  FE_TRY(tmp.get(&pos, nmax + 1));
+  uint32_t* sflag_v; uint32_t* sflag_e;
+  uint64_t* keys; uint32_t* vals;
+  int64_t nlv = 0, nle = 0;
+
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool edges = pass == 1;
+    const int per = edges ? npair : nv;
+    const int64_t n = nme * per;
+    if (!edges)
+      k_vinc_keys<<<fe_grid(n, T), T, 0, s>>>(h->me_int, nme, nv, C, vbits, sb->k0, sb->v0);
+    else
+      k_einc_keys<<<fe_grid(n, T), T, 0, s>>>(h->me_int, nme, nv, npair, C, vbits, sb->k0, sb->v0);
+    FE_CUDA_TRY(cudaGetLastError());
+    const int ebits = edges ? 2 * vbits : vbits;
+    FE_TRY(fe_radix_sort(n, ebits + cbits, sb, &keys, &vals, s));
+    k_key_change<<<fe_grid(n, T), T, 0, s>>>(keys, n, flag);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_TRY(fe_scan_exclusive(flag, pos, n, sb->scan_tmp, s));
+    uint32_t last_pos = 0, last_flag = 0;
+    FE_TRY(to_host(&last_pos, pos + n - 1, s));
+    FE_TRY(to_host(&last_flag, flag + n - 1, s));
+    const int64_t nloc = (int64_t)last_pos + last_flag;
+    uint16_t* inc; uint16_t* off; int32_t* ch_ptr; int32_t* dst; int32_t* vid = nullptr;
+    uint32_t* sflag;
+    FE_TRY(fe_malloc(h, (void**)&inc, sizeof(uint16_t) * n));
+    FE_TRY(fe_malloc(h, (void**)&off, sizeof(uint16_t) * nloc));
+    FE_TRY(fe_malloc(h, (void**)&ch_ptr, sizeof(int32_t) * (h->nchunks + 1)));
+    FE_TRY(fe_malloc(h, (void**)&dst, sizeof(int32_t) * nloc * (edges ? 2 : 1)));
+    if (!edges) FE_TRY(fe_malloc(h, (void**)&vid, sizeof(int32_t) * nloc));
+    FE_TRY(tmp.get(&sflag, nloc + 1));
+    // inc = sorted values as uint16 (they are < C * per <= 65536)
+    k_to_u16<<<fe_grid(n, T), T, 0, s>>>(vals, inc, n);
+    FE_CUDA_TRY(cudaGetLastError());
+    k_local_entities<<<fe_grid(n, T), T, 0, s>>>(keys, pos, n, per, C, ebits, vbits, edges,
+                                                  h->row_ptr_s, h->col_idx_s, h->nnz_slot_ptr, off,
+                                                  ch_ptr, dst, vid, sflag);
+    FE_CUDA_TRY(cudaGetLastError());
+    k_set_last<<<1, 1, 0, s>>>(ch_ptr, h->nchunks, (int32_t)nloc);
+    FE_CUDA_TRY(cudaGetLastError());
+    if (!edges) {
+      h->inc_v = inc; h->lv_off = off; h->ch_v_ptr = ch_ptr; h->lv_dst = dst; h->lv_vid = vid;
+      sflag_v = sflag; nlv = nloc;
+    } else {
+      h->inc_e = inc; h->le_off = off; h->ch_e_ptr = ch_ptr; h->le_dst = dst;
+      sflag_e = sflag; nle = nloc;
+    }
+  }
+  h->nlv = nlv;
+  h->nle = nle;
+
+  // shared entities: compact, sort by (global entity, chunk), assign partial slots
+  int64_t nsh_ent[2] = {0, 0}, npart[2] = {0, 0};
+  uint32_t* spos[2];
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool edges = pass == 1;
+    const int64_t nloc = edges ? nle : nlv;
+    uint32_t* sflag = edges ? sflag_e : sflag_v;
+    FE_TRY(tmp.get(&spos[pass], nloc + 1));
+    FE_TRY(fe_scan_exclusive(sflag, spos[pass], nloc, sb->scan_tmp, s));
+    uint32_t lp = 0, lf = 0;
+    FE_TRY(to_host(&lp, spos[pass] + nloc - 1, s));
+    FE_TRY(to_host(&lf, sflag + nloc - 1, s));
+    npart[pass] = (int64_t)lp + lf;
+  }
+  // count distinct shared global entities per kind after sorting; allocate fixup arrays
+  // with an upper bound (npart) and trim counts later
+  FE_TRY(fe_malloc(h, (void**)&h->sh_ptr, sizeof(int32_t) * (npart[0] + npart[1] + 1)));
+  FE_TRY(fe_malloc(h, (void**)&h->sh_dst, sizeof(int32_t) * 2 * (npart[0] + npart[1] + 1)));
+  int64_t ent_base = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool edges = pass == 1;
+    const int64_t nloc = edges ? nle : nlv;
+    const int64_t np = npart[pass];
+    if (np == 0) continue;
+    int32_t* dst = edges ? h->le_dst : h->lv_dst;
+    const int stride = edges ? 2 : 1;
+    const int32_t* ch_ptr = edges ? h->ch_e_ptr : h->ch_v_ptr;
+    k_shared_keys<<<fe_grid(nloc, T), T, 0, s>>>(edges ? sflag_e : sflag_v, spos[pass], nloc, dst,
+                                                 stride, ch_ptr, h->nchunks, cbits, sb->k0, sb->v0);
+    FE_CUDA_TRY(cudaGetLastError());
+    const int kbits = bitlen((uint64_t)(h->nnz_s > 1 ? h->nnz_s - 1 : 1)) + cbits;
+    FE_TRY(fe_radix_sort(np, kbits, sb, &keys, &vals, s));
+    // distinct entities
+    k_entity_change<<<fe_grid(np, T), T, 0, s>>>(keys, np, cbits, flag);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_TRY(fe_scan_exclusive(flag, pos, np, sb->scan_tmp, s));
+    uint32_t lp = 0, lf = 0;
+    FE_TRY(to_host(&lp, pos + np - 1, s));
+    FE_TRY(to_host(&lf, flag + np - 1, s));
+    nsh_ent[pass] = (int64_t)lp + lf;
+    const int64_t part_base = edges ? npart[0] : 0;
+    k_shared_finish<<<fe_grid(np, T), T, 0, s>>>(keys, vals, pos, np, cbits, part_base, ent_base,
+                                                  dst, stride, h->lv_vid, edges, h->sh_ptr,
+                                                  h->sh_dst, nullptr);
+    FE_CUDA_TRY(cudaGetLastError());
+    ent_base += nsh_ent[pass];
+  }
+  h->nsh_v = nsh_ent[0];
+  h->nsh_e = nsh_ent[1];
+  h->npart_v = npart[0];
+  h->npart = npart[0] + npart[1];
+  k_set_last<<<1, 1, 0, s>>>(h->sh_ptr, h->nsh_v + h->nsh_e, (int32_t)(npart[0] + npart[1]));
+  FE_CUDA_TRY(cudaGetLastError());
+  h->plan_bytes = (int64_t)sizeof(uint16_t) * nme * (nv + npair) +
+                  (int64_t)(sizeof(uint16_t) + 2 * sizeof(int32_t)) * nlv +
+                  (int64_t)(sizeof(uint16_t) + 2 * sizeof(int32_t)) * nle +
+                  (int64_t)sizeof(int32_t) * 2 * (h->nchunks + 1) +
+                  (int64_t)sizeof(int32_t) * 3 * (h->nsh_v + h->nsh_e + 1);
+  // partial-sum scratch: up to 9 values (elasticity blocks) of 8 bytes per partial
+  const int vals_per_partial = (h->m == 1) ? 1 : h->m * h->m;
+  const size_t pb = (size_t)(npart[0] + npart[1]) * vals_per_partial * 2 * sizeof(float) + 16;
+  FE_TRY(fe_malloc(h, &h->partials, pb));
+  h->partials_bytes = pb;
+  return FE_OK;
+}
+
+}  // namespace
+
+extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
+                          fe_pattern_h* out) {
+  if (!mesh || !out) return FE_ERR_ARG;
+  *out = nullptr;
+  const int d = mesh->d;
+  if (d != 2 && d != 3) return FE_ERR_ARG;
+  if (m != 1 && m != d) return FE_ERR_ARG;
+  if (mesh->nq < 1 || mesh->nme < 1 || !mesh->q || !mesh->me) return FE_ERR_ARG;
+  const int nv = d + 1, S = nv * nv;
+  const int64_t nq = mesh->nq, nme = mesh->nme;
+  if (nq > INT32_MAX / m || nme > INT32_MAX / S) return FE_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  fe_pattern_s* h = new fe_pattern_s();
+  h->d = d; h->m = m; h->nv = nv; h->npair = nv * d / 2; h->flags = flags;
+  h->nq = nq; h->nme = nme; h->n = (int64_t)m * nq;
+  h->chunk = default_chunk(d, m);
+  int rc = FE_OK;
+  dev_tmp tmp;
+  do {
+    const int T = 256;
+    rc = fe_malloc(h, (void**)&h->status, sizeof(fe_status_word));
+    if (rc) break;
+    {
+      fe_status_word init = {0, 0, ~0ull};
+      if (cudaMemcpyAsync(h->status, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        rc = FE_ERR_CUDA; break;
+      }
+    }
+    k_check_me<<<fe_grid(nme, T, 4096), T, 0, s>>>(mesh->me, nme, nv, nq, h->status);
+    fe_status_word st;
+    if (cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+    if (st.code != 0) { rc = st.code; break; }
+
+    const int64_t nslots = nme * S;
+    const int64_t nkeys = nslots > nme * (nv > h->npair ? nv : h->npair) ? nslots : nme * nv;
+    fe_sort_buffers sb;
+    if ((rc = tmp.get(&sb.k0, nkeys)) || (rc = tmp.get(&sb.k1, nkeys)) ||
+        (rc = tmp.get(&sb.v0, nkeys)) || (rc = tmp.get(&sb.v1, nkeys)) ||
+        (rc = tmp.get(&sb.hist, fe_sort_hist_size(nkeys))) ||
+        (rc = tmp.get(&sb.scan_tmp, fe_scan_tmp_size((int64_t)fe_sort_hist_size(nkeys)) +
+                                        fe_scan_tmp_size(nkeys))))
+      break;
+    uint64_t* keys; uint32_t* vals;
+
+    // 2. internal element order
+    if ((rc = fe_malloc(h, (void**)&h->me_int, sizeof(int32_t) * nv * nme))) break;
+    if ((rc = fe_malloc(h, (void**)&h->order, sizeof(int32_t) * nme))) break;
+    if (flags & FE_PATTERN_KEEP_ORDER) {
+      k_iota<<<fe_grid(nme, T), T, 0, s>>>(sb.v0, nme);
+      vals = sb.v0;
+    } else {
+      double* bb;
+      const int nblk = 256;
+      if ((rc = tmp.get(&bb, (size_t)nblk * 2 * d))) break;
+      k_bbox_partial<<<nblk, 256, 0, s>>>(mesh->q, nq, d, bb);
+      k_bbox_final<<<1, 32, 0, s>>>(bb, nblk, d);
+      int qbits = (bitlen((uint64_t)nme) + d - 1) / d + 2;
+      if (qbits > 21) qbits = 21;
+      k_morton_keys<<<fe_grid(nme, T), T, 0, s>>>(mesh->q, nq, mesh->me, nme, d, bb, qbits, sb.k0,
+                                                 sb.v0);
+      if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+      if ((rc = fe_radix_sort(nme, qbits * d, &sb, &keys, &vals, s))) break;
+    }
+    k_permute_me<<<fe_grid(nme, T), T, 0, s>>>(mesh->me, nme, nv, vals, h->me_int, h->order);
+    if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+
+    // 3. scalar pattern
+    k_slot_keys<<<fe_grid(nslots, T), T, 0, s>>>(h->me_int, nme, nv, nq, sb.k0, sb.v0);
+    if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+    const int kbits = bitlen((uint64_t)nq * (uint64_t)nq - 1ull);
+    if ((rc = fe_radix_sort(nslots, kbits, &sb, &keys, &vals, s))) break;
+    uint32_t *flag, *pos;
+    if ((rc = tmp.get(&flag, nslots + 1)) || (rc = tmp.get(&pos, nslots + 1))) break;
+    k_key_change<<<fe_grid(nslots, T), T, 0, s>>>(keys, nslots, flag);
+    if ((rc = fe_scan_exclusive(flag, pos, nslots, sb.scan_tmp, s))) break;
+    uint32_t lp = 0, lf = 0;
+    if ((rc = to_host(&lp, pos + nslots - 1, s)) || (rc = to_host(&lf, flag + nslots - 1, s))) break;
+    const int64_t nnz_s = (int64_t)lp + lf;
+    if ((int64_t)m * m * nnz_s > INT32_MAX) { rc = FE_ERR_OVERFLOW; break; }
+    h->nnz_s = nnz_s;
+    h->nnz = (int64_t)m * m * nnz_s;
+    if ((rc = fe_malloc(h, (void**)&h->row_ptr_s, sizeof(int32_t) * (nq + 1))) ||
+        (rc = fe_malloc(h, (void**)&h->col_idx_s, sizeof(int32_t) * nnz_s)) ||
+        (rc = fe_malloc(h, (void**)&h->slot2nnz, sizeof(int32_t) * nslots)) ||
+        (rc = fe_malloc(h, (void**)&h->nnz_slot_ptr, sizeof(int32_t) * (nnz_s + 1))) ||
+        (rc = fe_malloc(h, (void**)&h->nnz2slot, sizeof(int32_t) * nslots)))
+      break;
+    k_rle_scalar<<<fe_grid(nslots, T), T, 0, s>>>(keys, vals, pos, nslots, nq, h->col_idx_s,
+                                                  h->row_ptr_s, h->nnz_slot_ptr, h->slot2nnz);
+    k_rle_tail<<<1, 1, 0, s>>>(keys, nslots, nq, nnz_s, h->row_ptr_s, h->nnz_slot_ptr);
+    if (cudaMemcpyAsync(h->nnz2slot, vals, sizeof(int32_t) * nslots, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess) { rc = FE_ERR_CUDA; break; }
+    if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+
+    // 4. vector pattern
+    if (m == 1) {
+      h->row_ptr = h->row_ptr_s;
+      h->col_idx = h->col_idx_s;
+    } else {
+      if ((rc = fe_malloc(h, (void**)&h->row_ptr, sizeof(int32_t) * (m * nq + 1))) ||
+          (rc = fe_malloc(h, (void**)&h->col_idx, sizeof(int32_t) * h->nnz)))
+        break;
+      k_expand_csr<<<fe_grid(nq, T), T, 0, s>>>(h->row_ptr_s, h->col_idx_s, nq, m, h->row_ptr,
+                                                h->col_idx);
+      if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+    }
+
+    // 5. chunk plan
+    if ((rc = build_chunk_plan(h, &sb, tmp, s))) break;
+    if ((rc = fe_ensure_scratch(h, h->strategy))) break;
+    if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+  } while (0);
+  if (rc != FE_OK) {
+    cudaStreamSynchronize(s);
+    fe_free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return FE_OK;
+}

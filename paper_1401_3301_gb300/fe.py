@@ -1,0 +1,232 @@
+"""Thin Python binding of the C ABI in include/fe.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls and takes torch CUDA
+tensors; all arithmetic happens in libfe_gb300.so. There is no CPU fallback: if
+the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build_ext
+
+F64, F32 = 0, 1
+COEF_NONE, COEF_SCALAR, COEF_P0, COEF_P1, COEF_P0_INTERNAL = 0, 1, 2, 3, 4
+REASM_CHUNKED, REASM_GATHER, REASM_ATOMIC = 0, 1, 2
+PATTERN_KEEP_ORDER = 1
+ERRORS = {1: "FE_ERR_ARG", 2: "FE_ERR_INDEX", 3: "FE_ERR_DEGENERATE", 4: "FE_ERR_OVERFLOW",
+          5: "FE_ERR_CUDA", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NOMEM"}
+
+_lib = None
+
+
+class FEError(RuntimeError):
+    def __init__(self, code: int, detail: str = ""):
+        super().__init__(f"{ERRORS.get(code, code)}{': ' + detail if detail else ''}")
+        self.code = code
+
+
+def lib() -> C.CDLL:
+    """The loaded libfe_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = build_ext.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libfe_gb300.so is missing ({path}); build it with "
+                               "paper_1401_3301_gb300.build_ext.build()")
+        L = C.CDLL(path)
+        P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+        L.fe_pattern.argtypes = [P, I32, I32, P, P]
+        L.fe_pattern_copy_csr.argtypes = [P, P, P, P]
+        L.fe_pattern_copy_slot_map.argtypes = [P, P, P, P, P, P]
+        L.fe_pattern_dims.argtypes = [P, P, P, P, P, P, P]
+        L.fe_pattern_set_strategy.argtypes = [P, I32]
+        L.fe_pattern_memory.argtypes = [P, P]
+        L.fe_pattern_plan_info.argtypes = [P, P, P, P, P, P]
+        L.fe_pattern_destroy.argtypes = [P]
+        L.fe_status.argtypes = [P, P, P, P]
+        L.fe_assemble_mass.argtypes = [P, P, I32, P, P]
+        L.fe_assemble_wmass.argtypes = [P, P, P, I32, I32, P, P]
+        L.fe_assemble_stiff.argtypes = [P, P, P, I32, I32, P, P]
+        L.fe_assemble_elas.argtypes = [P, P, P, I32, P, I32, I32, P, P]
+        L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
+        L.fe_version.restype = C.c_char_p
+        L.fe_last_cuda_error.restype = C.c_char_p
+        for name in ("fe_pattern", "fe_pattern_copy_csr", "fe_pattern_copy_slot_map", "fe_pattern_dims",
+                     "fe_pattern_set_strategy", "fe_pattern_memory", "fe_pattern_plan_info",
+                     "fe_pattern_destroy", "fe_status", "fe_assemble_mass", "fe_assemble_wmass",
+                     "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise FEError(rc, lib().fe_last_cuda_error().decode() if rc in (5, 7) else "")
+
+
+def _stream(stream) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor | None, dtype=None, name="tensor") -> C.c_void_p | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("d", C.c_int32), ("nq", C.c_int64), ("nme", C.c_int64), ("q", C.c_void_p),
+                ("me", C.c_void_p)]
+
+
+def _vtype(prec: int):
+    return torch.float64 if prec == F64 else torch.float32
+
+
+class Pattern:
+    """Owner of an fe_pattern_h handle."""
+
+    def __init__(self, handle: C.c_void_p):
+        self.handle = handle
+        d, m = C.c_int32(), C.c_int32()
+        nq, nme, n, nnz = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().fe_pattern_dims(handle, C.byref(d), C.byref(m), C.byref(nq), C.byref(nme),
+                                     C.byref(n), C.byref(nnz)))
+        self.d, self.m, self.nq, self.nme, self.n, self.nnz = (d.value, m.value, nq.value, nme.value,
+                                                               n.value, nnz.value)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.handle is not None and _lib is not None:
+            _lib.fe_pattern_destroy(self.handle)
+        self.handle = None
+
+    def csr(self, stream=None):
+        """(row_ptr, col_idx): int32 CUDA tensors (copies)."""
+        rp = torch.empty(self.n + 1, dtype=torch.int32, device="cuda")
+        ci = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
+        _check(lib().fe_pattern_copy_csr(self.handle, _dev(rp), _dev(ci), _stream(stream)))
+        return rp, ci
+
+    def slot_map(self, stream=None):
+        """(slot2nnz, nnz_slot_ptr, nnz2slot, order) of the scalar pattern (copies)."""
+        S = (self.d + 1) ** 2
+        s2n = torch.empty(self.nme * S, dtype=torch.int32, device="cuda")
+        nsp = torch.empty(self.nnz // (self.m * self.m) + 1, dtype=torch.int32, device="cuda")
+        n2s = torch.empty(self.nme * S, dtype=torch.int32, device="cuda")
+        order = torch.empty(self.nme, dtype=torch.int32, device="cuda")
+        _check(lib().fe_pattern_copy_slot_map(self.handle, _dev(s2n), _dev(nsp), _dev(n2s), _dev(order),
+                                              _stream(stream)))
+        return s2n, nsp, n2s, order
+
+    def element_order(self, stream=None) -> torch.Tensor:
+        order = torch.empty(self.nme, dtype=torch.int32, device="cuda")
+        _check(lib().fe_pattern_copy_slot_map(self.handle, None, None, None, _dev(order), _stream(stream)))
+        return order
+
+    def set_strategy(self, strategy: int):
+        _check(lib().fe_pattern_set_strategy(self.handle, strategy))
+
+    def memory(self) -> int:
+        b = C.c_int64()
+        _check(lib().fe_pattern_memory(self.handle, C.byref(b)))
+        return b.value
+
+    def plan_info(self) -> dict:
+        v = [C.c_int64() for _ in range(5)]
+        _check(lib().fe_pattern_plan_info(self.handle, *[C.byref(x) for x in v]))
+        return dict(zip(("chunk", "local_vertices", "local_edges", "partials", "plan_bytes"),
+                        (x.value for x in v)))
+
+    def status(self, stream=None):
+        """(code, element id) from the device status word; clears it."""
+        code, eid = C.c_int32(), C.c_int64()
+        _check(lib().fe_status(self.handle, _stream(stream), C.byref(code), C.byref(eid)))
+        return code.value, eid.value
+
+    def check(self, stream=None):
+        code, eid = self.status(stream)
+        if code:
+            raise FEError(code, f"element {eid}")
+
+
+def fe_pattern(q: torch.Tensor, me: torch.Tensor, m: int = 1, flags: int = 0, stream=None) -> Pattern:
+    d = q.shape[0]
+    mesh = _Mesh(d, q.shape[1], me.shape[1], _dev(q, torch.float64, "q").value,
+                 _dev(me, torch.int32, "me").value)
+    if me.shape[0] != d + 1:
+        raise ValueError("me must be (d+1, nme)")
+    h = C.c_void_p()
+    _check(lib().fe_pattern(C.byref(mesh), m, flags, _stream(stream), C.byref(h)))
+    return Pattern(h)
+
+
+def _out(p: Pattern, vals, prec):
+    if vals is None:
+        vals = torch.empty(p.nnz, dtype=_vtype(prec), device="cuda")
+    return vals
+
+
+def fe_assemble_mass(p: Pattern, q: torch.Tensor, prec: int = F64, vals=None, stream=None):
+    vals = _out(p, vals, prec)
+    _check(lib().fe_assemble_mass(p.handle, _dev(q, torch.float64, "q"), prec,
+                                  _dev(vals, _vtype(prec), "vals"), _stream(stream)))
+    return vals
+
+
+def fe_assemble_wmass(p: Pattern, q: torch.Tensor, w: torch.Tensor, w_kind: int = COEF_P1,
+                      prec: int = F64, vals=None, stream=None):
+    vals = _out(p, vals, prec)
+    _check(lib().fe_assemble_wmass(p.handle, _dev(q, torch.float64, "q"), _dev(w, _vtype(prec), "w"),
+                                   w_kind, prec, _dev(vals, _vtype(prec), "vals"), _stream(stream)))
+    return vals
+
+
+def fe_assemble_stiff(p: Pattern, q: torch.Tensor, w: torch.Tensor | None = None,
+                      w_kind: int | None = None, prec: int = F64, vals=None, stream=None):
+    vals = _out(p, vals, prec)
+    if w_kind is None:
+        w_kind = COEF_NONE if w is None else COEF_P0
+    _check(lib().fe_assemble_stiff(p.handle, _dev(q, torch.float64, "q"), _dev(w, _vtype(prec), "w"),
+                                   w_kind, prec, _dev(vals, _vtype(prec), "vals"), _stream(stream)))
+    return vals
+
+
+def fe_assemble_elas(p: Pattern, q: torch.Tensor, lam: torch.Tensor, lam_kind: int, mu: torch.Tensor,
+                     mu_kind: int, prec: int = F64, vals=None, stream=None):
+    vals = _out(p, vals, prec)
+    _check(lib().fe_assemble_elas(p.handle, _dev(q, torch.float64, "q"), _dev(lam, _vtype(prec), "lam"),
+                                  lam_kind, _dev(mu, _vtype(prec), "mu"), mu_kind, prec,
+                                  _dev(vals, _vtype(prec), "vals"), _stream(stream)))
+    return vals
+
+
+def fe_assemble_stiff_backward(p: Pattern, q: torch.Tensor, w, w_kind: int, u: torch.Tensor,
+                               v: torch.Tensor, L=None, dL_dw=None, dL_dq=None, prec: int = F64,
+                               stream=None):
+    T = _vtype(prec)
+    _check(lib().fe_assemble_stiff_backward(
+        p.handle, _dev(q, torch.float64, "q"), _dev(w, T, "w"), w_kind, _dev(u, T, "u"), _dev(v, T, "v"),
+        _dev(L, T, "L"), _dev(dL_dw, T, "dL_dw"), _dev(dL_dq, T, "dL_dq"), prec, _stream(stream)))
+    return L, dL_dw, dL_dq
+
+
+def fe_version() -> str:
+    return lib().fe_version().decode()
