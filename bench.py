@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: fixed-pattern reassembly of the 3D P1 stiffness matrix on GB300.
+
+Workload: unit cube, N = 100 Kuhn 6-tetrahedron split (6,000,000 tets, 1,030,301
+vertices, 15,210,901 nonzeros), interior vertices jittered by +-0.15 h, elements
+randomly permuted (seeded). The sparsity pattern is built once, outside the timed
+region; one step is one reassembly of the matrix values from the coordinates
+(Algorithm 7 of Cuvelier-Japhet-Scarella followed by the value part of `sparse`).
+Both precision forms are measured in the same run; --prec picks the one reported
+as the headline value (FP64 by default, the precision of the paper).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+With N > 1 the script runs under torchrun, one process per GPU, each assembling
+its own copy of the workload (independent replicas: the method needs no
+exchange between meshes); value = tets of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D P1 stiffness Mtets/s and % HBM roofline, FP32 vs FP64 form, fixed pattern"
+UNIT = "Mtets/s"
+SM_COUNT = 152
+FP64_PIPE_PER_SM_CLK = 2.0      # DFMA/DADD/DMUL issue rate per SM per clock on GB300
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["elem.cuh", "plan.cuh", "tma.cuh", "assemble_impl.cuh", "assemble_scalar.inc",
+                  "assemble_f64.cu", "assemble_f32.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--N", type=int, default=100, help="cells per cube side (default 100: 6M tets)")
+    ap.add_argument("--strategy", default="chunked", choices=["chunked", "gather", "atomic"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_config(N):
+    nq, nme = (N + 1) ** 3, 6 * N ** 3
+    return {"workload": f"3D P1 stiffness, fixed-pattern reassembly, Kuhn cube N={N} "
+                        f"({nme:,} tets, {nq:,} vertices), jitter 0.15h, elements permuted",
+            "mesh": "kuhn_cube", "N": N, "tets": nme, "vertices": nq}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured", float(pk.get("sm_max_mhz", 2070.0))
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback", 2070.0
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(", ") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_baseline(m, sample):
+    import oracle
+    oracle.build()
+    S = min(sample, m.nme)
+    me = np.ascontiguousarray(m.me[:, :S])
+    t0 = time.perf_counter()
+    oracle.assemble(oracle.STIFF, m.q, me)
+    dt = time.perf_counter() - t0
+    return {"value": S / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {S:,} of the {m.nme:,} randomly ordered tets of the same mesh "
+                      f"(element loop + triplet sort-and-sum into CSR, FP64, one thread); {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1401_3301_gb300 import meshgen
+    oracle.build()
+    m = meshgen.kuhn_cube_mesh(args.N, seed=0)
+    # calibrate: choose a per-step sample so the whole run takes about two minutes
+    probe = min(50_000, m.nme)
+    t0 = time.perf_counter()
+    oracle.assemble(oracle.STIFF, m.q, np.ascontiguousarray(m.me[:, :probe]))
+    rate = probe / (time.perf_counter() - t0)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    S = int(min(m.nme, max(10_000, rate * budget)))
+    me = np.ascontiguousarray(m.me[:, :S])
+    for _ in range(args.warmup):
+        oracle.assemble(oracle.STIFF, m.q, me)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.assemble(oracle.STIFF, m.q, me)
+    dt = time.perf_counter() - t0
+    value = S * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {**workload_config(args.N), "strategy": "oracle",
+                                            "parallelism": "host, one thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the first {S:,} of the {m.nme:,} randomly ordered "
+                                       "tets (element loop + triplet sort-and-sum, FP64)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1401_3301_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(form):
+    """DRAM bytes per launch of the chunk kernel from the committed ncu summary, if the
+    kernel sources are unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        ent = t[form]
+        if ent.get("source_hash") != kernel_source_hash():
+            return None
+        return ent["bytes_per_launch"] * ent.get("scale_to_workload", 1.0)
+    except Exception:
+        return None
+
+
+def chunk_algorithmic_bytes(p, prec, info):
+    """Bytes the chunk kernel must move per launch: its plan records (read once), the
+    FP64 coordinates (each vertex once), the owned CSR values and the partial sums it
+    writes; counts are exact, from the plan."""
+    d, nq = p.d, p.nq
+    sT = 8 if prec == 0 else 4
+    lv, le = info["local_vertices"], info["local_edges"]
+    pv, pe = info["partial_vertices"], info["partial_edges"]
+    reads = info["plan_bytes"] + 8 * d * nq
+    writes = (lv - pv) * sT + (le - pe) * 2 * sT + (pv + pe) * 8
+    return reads + writes
+
+
+def fp64_instr_per_tet(info, nme):
+    """FP64-pipe instructions per tet of the FP64 chunk kernel, counted from the source:
+    edges 9 DADD, cofactors 18, det 3, 1/(6|det|) 6, Gram 18 + 6 scalings, row sums 9,
+    plus one DADD per incidence summed (4 vertex + 6 edge incidences per tet)."""
+    return 9 + 18 + 3 + 6 + 24 + 9 + 10
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1401_3301_gb300 import build_ext, fe, meshgen
+    if rank == 0:
+        build_ext.build()
+    if world > 1:
+        torch.distributed.barrier()
+    fe.lib()
+    m = meshgen.kuhn_cube_mesh(args.N, seed=0)
+    q = torch.from_numpy(m.q).cuda()
+    me = torch.from_numpy(m.me).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p = fe.fe_pattern(q, me)
+    pattern_ms = (time.perf_counter() - t0) * 1e3
+    strategy = {"chunked": fe.REASM_CHUNKED, "gather": fe.REASM_GATHER, "atomic": fe.REASM_ATOMIC}[args.strategy]
+    p.set_strategy(strategy)
+    info = p.plan_info()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    hbm_peak, peak_src, sm_max = measured_peaks()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    forms = {}
+    sampler.start()
+    for prec_name, prec in (("f64", fe.F64), ("f32", fe.F32)):
+        T = torch.float64 if prec == fe.F64 else torch.float32
+        vals = torch.empty(p.nnz, dtype=T, device="cuda")
+        for _ in range(args.warmup):
+            fe.fe_assemble_stiff(p, q, prec=prec, vals=vals)
+        p.check()
+        p.profile(True)
+        p.profile_read()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            fe.fe_assemble_stiff(p, q, prec=prec, vals=vals)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_ms = float(sum(step_ms))
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        prof = p.profile_read()
+        p.profile(False)
+        p.check()
+        launches = int(sum(n for _, n in prof.values()))
+        dom = max(prof, key=lambda k: prof[k][0])
+        dom_ms = prof[dom][0] / prof[dom][1]
+        abytes = chunk_algorithmic_bytes(p, prec, info)
+        achieved = abytes / (dom_ms * 1e-3) / 1e9
+        traffic = committed_traffic(prec_name)
+        roof_hbm = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": traffic,
+                    "algorithmic_bytes_per_launch": abytes, "kernel_ms": dom_ms,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                    else "fallback 6.8 TB/s"}
+        tets = p.nme * world
+        value = tets * args.steps / (total_ms * 1e-3) / 1e6
+        forms[prec_name] = {"value": value, "ms_per_step": total_ms / args.steps,
+                            "step_ms_median": statistics.median(step_ms), "kernels": {
+                                k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()},
+                            "roofline_hbm": roof_hbm, "gpu_launches": launches}
+        # path-level effective bandwidth with the per-tet bytes of the method (compulsory + slot map)
+        per_tet = 104.4 if prec == fe.F64 else 94.3
+        forms[prec_name]["path_effective"] = {
+            "bytes_per_tet": per_tet, "GBps": per_tet * p.nme / (forms[prec_name]["ms_per_step"] * 1e-3) / 1e9}
+        forms[prec_name]["path_effective"]["frac"] = forms[prec_name]["path_effective"]["GBps"] / hbm_peak
+        if prec == fe.F64:
+            clock = sm_max
+            instr = fp64_instr_per_tet(info, p.nme) * p.nme
+            peak_ops = FP64_PIPE_PER_SM_CLK * SM_COUNT * clock * 1e6 / 1e9
+            forms[prec_name]["roofline_alu"] = {
+                "bound": "alu", "kernel": dom, "achieved": instr / (dom_ms * 1e-3) / 1e9,
+                "peak": peak_ops, "unit": "G FP64 instr/s",
+                "frac": instr / (dom_ms * 1e-3) / 1e9 / peak_ops,
+                "instr_per_tet": fp64_instr_per_tet(info, p.nme), "counted": "from source",
+                "peak_source": f"{FP64_PIPE_PER_SM_CLK:.0f} FP64 instr/SM/clk x {SM_COUNT} SMs x {clock:.0f} MHz"}
+    clocks = sampler.stop()
+
+    # end-to-end through the public API with host buffers (selected form)
+    prec = fe.F64 if args.prec == "f64" else fe.F32
+    T = torch.float64 if prec == fe.F64 else torch.float32
+    q_host = torch.from_numpy(m.q).pin_memory()
+    vals = torch.empty(p.nnz, dtype=T, device="cuda")
+    vals_host = torch.empty(p.nnz, dtype=T).pin_memory()
+    e2e_steps = max(3, min(args.steps, 30))
+    for _ in range(2):
+        q.copy_(q_host, non_blocking=True)
+        fe.fe_assemble_stiff(p, q, prec=prec, vals=vals)
+        vals_host.copy_(vals, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        q.copy_(q_host, non_blocking=True)
+        fe.fe_assemble_stiff(p, q, prec=prec, vals=vals)
+        vals_host.copy_(vals, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e = {"value": p.nme * world / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(q_host.numel() * 8), "d2h_bytes_per_step": int(vals_host.numel() * vals_host.element_size()),
+           "ms_per_step": e2e_ms, "steps": e2e_steps}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    sel = forms[args.prec]
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(m, args.cpu_sample)
+    roof = sel["roofline_alu"] if args.prec == "f64" else sel["roofline_hbm"]
+    line = {"metric": METRIC, "value": sel["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sel["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {**workload_config(args.N), "strategy": args.strategy, "form": args.prec,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "nnz": p.nnz, "pattern_build_ms": pattern_ms, "plan": info},
+            "roofline": roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": sel["gpu_launches"], "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

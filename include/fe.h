@@ -141,9 +141,13 @@ int fe_pattern_set_strategy(fe_pattern_h h, int32_t strategy);
 int fe_pattern_memory(fe_pattern_h h, int64_t* bytes);
 
 /* Counts of the element-chunk plan used by FE_REASM_CHUNKED (for roofline
- * accounting): chunk size, local vertices, local edges, partial sums. */
+ * accounting): elements per chunk, distinct (chunk, vertex) and (chunk, edge)
+ * pairs, how many of those are partial sums (the vertex or edge also belongs to
+ * another chunk), distinct shared vertices and edges, and the plan's bytes.
+ * Any pointer may be NULL. */
 int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices,
-                         int64_t* local_edges, int64_t* partials, int64_t* plan_bytes);
+                         int64_t* local_edges, int64_t* partial_vertices, int64_t* partial_edges,
+                         int64_t* shared_vertices, int64_t* shared_edges, int64_t* plan_bytes);
 
 int fe_pattern_destroy(fe_pattern_h h);
 
@@ -206,6 +210,18 @@ int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t l
 int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
                                const void* u, const void* v, void* L, void* dL_dw, void* dL_dq,
                                int32_t prec, void* stream);
+
+/*
+ * Per-kernel timing. fe_profile(h, 1) makes every later kernel launch of h be
+ * bracketed by a CUDA event pair on its stream (fe_profile(h, 0) stops and frees
+ * them). fe_profile_read synchronises on the recorded events and returns, per
+ * kernel kind launched since the last read, its name (32-byte slots in `names`),
+ * total milliseconds and launch count; *count receives the number of kinds
+ * (entries beyond max_kernels are dropped). Host pointers.
+ */
+int fe_profile(fe_pattern_h h, int32_t enable);
+int fe_profile_read(fe_pattern_h h, int32_t max_kernels, char* names, double* ms,
+                    int64_t* launches, int32_t* count);
 
 /* Library version string (host pointer, static). */
 const char* fe_version(void);

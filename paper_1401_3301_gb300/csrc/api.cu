@@ -39,7 +39,7 @@ void fe_free_all(fe_pattern_s* h) {
                   h->nnz_slot_ptr, h->nnz2slot, h->ch_v_ptr, h->ch_e_ptr, h->lv_off,
                   h->le_off,  h->inc_v,    h->inc_e,     h->lv_dst,    h->lv_vid,
                   h->le_dst,  h->sh_ptr,   h->sh_dst,    h->partials,  h->kg,
-                  h->qsplit,  h->status};
+                  h->qsplit,  h->status, h->rec, h->rec_off16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->m > 1) {
@@ -47,6 +47,7 @@ void fe_free_all(fe_pattern_s* h) {
     if (h->col_idx) cudaFree(h->col_idx);
   }
   if (h->elas_dst) cudaFree(h->elas_dst);
+  fe_prof_free(h);
 }
 
 int fe_ensure_scratch(fe_pattern_s* h, int strategy) {
@@ -153,12 +154,16 @@ int fe_pattern_memory(fe_pattern_h h, int64_t* bytes) {
 }
 
 int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices,
-                         int64_t* local_edges, int64_t* partials, int64_t* plan_bytes) {
+                         int64_t* local_edges, int64_t* partial_vertices, int64_t* partial_edges,
+                         int64_t* shared_vertices, int64_t* shared_edges, int64_t* plan_bytes) {
   if (!h) return FE_ERR_ARG;
   if (chunk) *chunk = h->chunk;
   if (local_vertices) *local_vertices = h->nlv;
   if (local_edges) *local_edges = h->nle;
-  if (partials) *partials = h->npart;
+  if (partial_vertices) *partial_vertices = h->npart_v;
+  if (partial_edges) *partial_edges = h->npart - h->npart_v;
+  if (shared_vertices) *shared_vertices = h->nsh_v;
+  if (shared_edges) *shared_edges = h->nsh_e;
   if (plan_bytes) *plan_bytes = h->plan_bytes;
   return FE_OK;
 }

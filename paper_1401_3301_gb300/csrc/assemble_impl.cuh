@@ -4,10 +4,88 @@
 
 #include "elem.cuh"
 #include "fe_internal.cuh"
+#include "plan.cuh"
+#include "tma.cuh"
 
 namespace fe {
 
 enum Kind : int { K_MASS = 0, K_WMASS_P1 = 1, K_WMASS_P0 = 2, K_STIFF = 3 };
+
+template <int D, class T>
+struct ScalarVals {
+  T diag[D + 1];
+  T off[Pairs<D>::n];
+};
+
+// per-element coefficient (P0 kinds); 1 when there is none
+template <class T>
+__device__ __forceinline__ T elem_coef(const void* w, int w_kind, const int32_t* order, int64_t e) {
+  const T* wp = (const T*)w;
+  if (w_kind == FE_COEF_P0) return wp[order[e]];
+  if (w_kind == FE_COEF_P0_INTERNAL) return wp[e];
+  if (w_kind == FE_COEF_SCALAR) return wp[0];
+  return T(1);
+}
+
+// Local matrix entries from the geometry. wv: vertex values of the weight (P1 kind).
+template <int D, class T, int KIND>
+__device__ __forceinline__ void values_from_geo(const Geo<D, T>& g, bool has_coef, T coef,
+                                                const T* wv, ScalarVals<D, T>& out) {
+  constexpr int NV = D + 1;
+  const T adet = tabs(g.det);
+  if constexpr (KIND == K_STIFF) {
+    T inv = recip<T>(T(factorial(D)) * adet);
+    if (has_coef) inv *= coef;
+    // scaled Gram matrix of c_1..c_D; the row of vertex 0 follows from sum_a c_a = 0
+    T G[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) {
+        T s = g.c[i + 1][0] * g.c[j + 1][0];
+#pragma unroll
+        for (int k = 1; k < D; ++k) s += g.c[i + 1][k] * g.c[j + 1][k];
+        G[i][j] = s * inv;
+        G[j][i] = G[i][j];
+      }
+    T nr[D];  // nr[i] = S_{0, i+1} = -sum_j G[i][j]
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T s = -G[i][0];
+#pragma unroll
+      for (int j = 1; j < D; ++j) s -= G[i][j];
+      nr[i] = s;
+    }
+    T d0 = -nr[0];
+#pragma unroll
+    for (int i = 1; i < D; ++i) d0 -= nr[i];
+    out.diag[0] = d0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) out.diag[i + 1] = G[i][i];
+#pragma unroll
+    for (int p = 0; p < Pairs<D>::n; ++p) {
+      const int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
+      out.off[p] = (a == 0) ? nr[b - 1] : G[a - 1][b - 1];
+    }
+  } else if constexpr (KIND == K_MASS || KIND == K_WMASS_P0) {
+    T m = adet * T(1.0 / factorial(D + 2));
+    if (has_coef) m *= coef;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) out.diag[a] = T(2) * m;
+#pragma unroll
+    for (int p = 0; p < Pairs<D>::n; ++p) out.off[p] = m;
+  } else {  // K_WMASS_P1
+    T ws = wv[0];
+#pragma unroll
+    for (int a = 1; a < NV; ++a) ws += wv[a];
+    const T base = adet * T(1.0 / factorial(D + 3));
+#pragma unroll
+    for (int a = 0; a < NV; ++a) out.diag[a] = T(2) * base * (ws + T(2) * wv[a]);
+#pragma unroll
+    for (int p = 0; p < Pairs<D>::n; ++p)
+      out.off[p] = base * (ws + wv[Pairs<D>::a(p)] + wv[Pairs<D>::b(p)]);
+  }
+}
 
 struct ElemArgs {
   const int32_t* me;   // internal order, (d+1) x nme
@@ -20,34 +98,7 @@ struct ElemArgs {
   fe_status_word* st;
 };
 
-struct PlanArgs {
-  int chunk;
-  const int32_t* ch_v_ptr;
-  const int32_t* ch_e_ptr;
-  const uint16_t* lv_off;
-  const uint16_t* le_off;
-  const uint16_t* inc_v;
-  const uint16_t* inc_e;
-  const int32_t* lv_dst;
-  const int32_t* le_dst;
-};
-
-template <int D, class T>
-struct ScalarVals {
-  T diag[D + 1];
-  T off[Pairs<D>::n];
-};
-
-template <class T>
-__device__ __forceinline__ T load_coef(const ElemArgs& A, int64_t e) {
-  const T* w = (const T*)A.w;
-  if (A.w_kind == FE_COEF_P0) return w[A.order[e]];
-  if (A.w_kind == FE_COEF_P0_INTERNAL) return w[e];
-  if (A.w_kind == FE_COEF_SCALAR) return w[0];
-  return T(1);
-}
-
-// values of internal element e; returns false (and reports) for a degenerate element
+// values of internal element e, coordinates gathered from global memory
 template <int D, class T, int KIND>
 __device__ __forceinline__ void element_values(const ElemArgs& A, int64_t e, ScalarVals<D, T>& out) {
   constexpr int NV = D + 1;
@@ -55,68 +106,27 @@ __device__ __forceinline__ void element_values(const ElemArgs& A, int64_t e, Sca
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = __ldg(A.me + (int64_t)a * A.nme + e);
   Geo<D, T> g;
-  if constexpr (sizeof(T) == 8) geo_f64<D>(A.q, A.nq, v, g);
-  else geo_f32<D>(A.qs, v, g);
+  if constexpr (sizeof(T) == 8) {
+    double x[NV][D];
+    load_x64<D>(A.q, A.nq, v, x);
+    geo_f64<D>(x, g);
+  } else {
+    float xh[NV][D], xl[NV][D];
+    load_x32<D>(A.qs, v, xh, xl);
+    geo_f32<D>(xh, xl, g);
+  }
   if (!det_ok(g.det)) {
     fe_report(A.st, FE_ERR_DEGENERATE, A.order[e]);
     g.det = T(1);
   }
-  const T adet = g.det < T(0) ? -g.det : g.det;
-  if constexpr (KIND == K_STIFF) {
-    const T inv = load_coef<T>(A, e) * recip<T>(T(factorial(D)) * adet);
-    // Gram matrix of c_1..c_D, scaled; row a = 0 from sum_a c_a = 0
-    T G[D][D];
+  T wv[NV];
+  if constexpr (KIND == K_WMASS_P1) {
 #pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = i; j < D; ++j) {
-        T s = g.c[i + 1][0] * g.c[j + 1][0];
-#pragma unroll
-        for (int k = 1; k < D; ++k) s += g.c[i + 1][k] * g.c[j + 1][k];
-        G[i][j] = s * inv;
-        G[j][i] = G[i][j];
-      }
-    T r[D];
-    T r0 = T(0);
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      T s = G[i][0];
-#pragma unroll
-      for (int j = 1; j < D; ++j) s += G[i][j];
-      r[i] = s;
-      r0 += s;
-    }
-    out.diag[0] = r0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) out.diag[i + 1] = G[i][i];
-#pragma unroll
-    for (int p = 0; p < Pairs<D>::n; ++p) {
-      const int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
-      out.off[p] = (a == 0) ? -r[b - 1] : G[a - 1][b - 1];
-    }
-  } else if constexpr (KIND == K_MASS || KIND == K_WMASS_P0) {
-    T m = adet * T(1.0 / factorial(D + 2));
-    if constexpr (KIND == K_WMASS_P0) m *= load_coef<T>(A, e);
-#pragma unroll
-    for (int a = 0; a < NV; ++a) out.diag[a] = T(2) * m;
-#pragma unroll
-    for (int p = 0; p < Pairs<D>::n; ++p) out.off[p] = m;
-  } else {  // K_WMASS_P1
-    const T* w = (const T*)A.w;
-    T wv[NV];
-    T ws = T(0);
-#pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      wv[a] = w[v[a]];
-      ws += wv[a];
-    }
-    const T base = adet * T(1.0 / factorial(D + 3));
-#pragma unroll
-    for (int a = 0; a < NV; ++a) out.diag[a] = T(2) * base * (ws + T(2) * wv[a]);
-#pragma unroll
-    for (int p = 0; p < Pairs<D>::n; ++p)
-      out.off[p] = base * (ws + wv[Pairs<D>::a(p)] + wv[Pairs<D>::b(p)]);
+    for (int a = 0; a < NV; ++a) wv[a] = ((const T*)A.w)[v[a]];
   }
+  const bool has_coef = A.w_kind != FE_COEF_NONE && KIND != K_WMASS_P1;
+  const T coef = has_coef ? elem_coef<T>(A.w, A.w_kind, A.order, e) : T(1);
+  values_from_geo<D, T, KIND>(g, has_coef, coef, wv, out);
 }
 
 // accumulators: FP64 plain sum, FP32 compensated sum
@@ -124,80 +134,227 @@ template <class T>
 struct Acc;
 template <>
 struct Acc<double> {
-  double s = 0.0;
+  double s;
+  __device__ __forceinline__ explicit Acc(double first) : s(first) {}
   __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ void add_partial(const void* p, int64_t i) { s += ((const double*)p)[i]; }
   __device__ __forceinline__ double value() const { return s; }
   __device__ __forceinline__ void store_partial(void* p, int64_t i) const { ((double*)p)[i] = s; }
+  __device__ __forceinline__ static Acc from_partial(const void* p, int64_t i) {
+    return Acc(((const double*)p)[i]);
+  }
+  __device__ __forceinline__ void add_partial(const void* p, int64_t i) { s += ((const double*)p)[i]; }
 };
 template <>
 struct Acc<float> {
   csum s;
+  __device__ __forceinline__ explicit Acc(float first) { s.s = first; s.c = 0.f; }
   __device__ __forceinline__ void add(float x) { s.add(x); }
-  __device__ __forceinline__ void add_partial(const void* p, int64_t i) {
-    const float2 v = ((const float2*)p)[i];
-    s.add2(v.x, v.y);
-  }
   __device__ __forceinline__ float value() const { return s.value(); }
   __device__ __forceinline__ void store_partial(void* p, int64_t i) const {
     ((float2*)p)[i] = make_float2(s.s, s.c);
   }
+  __device__ __forceinline__ static Acc from_partial(const void* p, int64_t i) {
+    const float2 v = ((const float2*)p)[i];
+    Acc a(v.x);
+    a.s.c = v.y;
+    return a;
+  }
+  __device__ __forceinline__ void add_partial(const void* p, int64_t i) {
+    const float2 v = ((const float2*)p)[i];
+    s.add2(v.x, v.y);
+  }
 };
 
 // ---------------------------------------------------------------- FE_REASM_CHUNKED
-// One block per chunk of internal elements. Phase 1: element values into shared
-// memory (diagonal entries per corner, off-diagonal entries per local edge).
-// Phase 2: each distinct vertex / edge of the chunk sums its incidences in
-// ascending element order and stores the sum in the CSR value (both (i,j) and
-// (j,i) for an edge: the operators are symmetric) or in its partial-sum slot.
+// Shared-memory layout of the staged chunk kernel (byte offsets).
+struct StagedSmem {
+  uint32_t q, w, lvid, kd, ko, total;
+};
+__host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, bool p1_weight,
+                                                           uint32_t rec_max, uint32_t max_lv,
+                                                           uint32_t chunk) {
+  const uint32_t nv = D + 1, np = D * (D + 1) / 2;
+  StagedSmem L;
+  uint32_t o = pad16(rec_max);
+  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
+  L.w = o;    o += p1_weight ? pad16(sizeT * max_lv) : 0u;
+  L.lvid = o; o += pad16(2u * nv * chunk);
+  L.kd = o;   o += pad16(sizeT * nv * chunk);
+  L.ko = o;   o += pad16(sizeT * np * chunk);
+  L.total = o;
+  return L;
+}
+
+struct StagedArgs {
+  int64_t nme, nq;
+  int chunk;
+  uint32_t rec_max, max_lv;
+  const double* q;
+  const void* w;
+  int w_kind;
+  const int32_t* order;
+  const int32_t* ch_v_ptr;
+  const int32_t* ch_e_ptr;
+  const uint8_t* rec;
+  const uint32_t* rec_off16;
+  fe_status_word* st;
+};
+
+constexpr uint32_t kBarrierSpin = 1u << 22;
+
+// One block per chunk of internal elements.
+//  0. one bulk (TMA) copy brings the chunk's plan record into shared memory; the
+//     coordinates of the chunk's distinct vertices are read once from q (split into
+//     hi/lo floats for the FP32 form), and the record's vertex incidence lists give
+//     each element corner its local vertex;
+//  1. element values into shared memory (diagonal per corner, off-diagonal per edge);
+//  2. each distinct vertex / edge sums its incidences in ascending element order and
+//     stores the sum in the CSR value (both (i,j) and (j,i) for an edge: the
+//     operators are symmetric) or in its partial-sum slot.
 template <int D, class T, int KIND, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_chunk_scalar(ElemArgs A, PlanArgs P, T* __restrict__ vals,
+__global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __restrict__ vals,
                                                           void* __restrict__ partials) {
   constexpr int NV = D + 1, NP = Pairs<D>::n;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Kd = reinterpret_cast<T*>(smem_raw);
-  T* Ko = Kd + (int64_t)P.chunk * NV;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
   const int64_t c = blockIdx.x;
-  const int64_t e0 = c * P.chunk;
-  const int ne = (int)min((int64_t)P.chunk, A.nme - e0);
+  const int64_t e0 = c * A.chunk;
+  const int ne = (int)min((int64_t)A.chunk, A.nme - e0);
+  const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
+  const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
+  const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
+  const StagedSmem S = staged_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, R.total);
+    bulk_copy_g2s(smem, A.rec + (int64_t)A.rec_off16[c] * 16, R.total, &bar);
+  }
+  __syncthreads();
+  const bool landed = __syncthreads_and(mbar_wait_bounded(&bar, 0, kBarrierSpin));
+  if (!landed) {
+    if (threadIdx.x == 0) {
+      fe_report(A.st, FE_ERR_TIMEOUT, e0);
+      mbar_wait_bounded(&bar, 0, kBarrierSpin);  // let the copy in flight finish, if it can
+    }
+    return;
+  }
+  const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
+  const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
+  const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
+  const uint16_t* le_off = (const uint16_t*)(smem + R.le_off);
+  const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
+  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  T* Kd = (T*)(smem + S.kd);
+  T* Ko = (T*)(smem + S.ko);
+  T* wl = (T*)(smem + S.w);
+
+  // 0. vertex coordinates of the chunk, and the local vertex of every element corner
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int64_t vid = lv_vid[u];
+    double x[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = __ldg(A.q + k * A.nq + vid);
+    if constexpr (sizeof(T) == 8) {
+      double* xs = (double*)(smem + S.q) + (D == 3 ? 4 : 2) * u;
+      if constexpr (D == 3) {
+        ((double2*)xs)[0] = make_double2(x[0], x[1]);
+        xs[2] = x[2];
+      } else {
+        ((double2*)xs)[0] = make_double2(x[0], x[1]);
+      }
+    } else {
+      float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < D; ++k) split_f64(x[k], h[k], l[k]);
+      float4* xs = (float4*)(smem + S.q) + (D == 3 ? 2 : 1) * u;
+      if constexpr (D == 3) {
+        xs[0] = make_float4(h[0], h[1], h[2], 0.f);
+        xs[1] = make_float4(l[0], l[1], l[2], 0.f);
+      } else {
+        xs[0] = make_float4(h[0], h[1], l[0], l[1]);
+      }
+    }
+    if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
+    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
+  }
+  __syncthreads();
+
+  // 1. element values
+  const bool has_coef = A.w_kind != FE_COEF_NONE && KIND != K_WMASS_P1;
   for (int el = threadIdx.x; el < ne; el += THREADS) {
+    int lv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
+    Geo<D, T> g;
+    if constexpr (sizeof(T) == 8) {
+      double x[NV][D];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const double* xs = (const double*)(smem + S.q) + (D == 3 ? 4 : 2) * lv[a];
+        const double2 xy = ((const double2*)xs)[0];
+        x[a][0] = xy.x;
+        x[a][1] = xy.y;
+        if constexpr (D == 3) x[a][2] = xs[2];
+      }
+      geo_f64<D>(x, g);
+    } else {
+      float xh[NV][D], xl[NV][D];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lv[a];
+        const float4 h = xs[0];
+        if constexpr (D == 3) {
+          const float4 l = xs[1];
+          xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
+          xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
+        } else {
+          xh[a][0] = h.x; xh[a][1] = h.y;
+          xl[a][0] = h.z; xl[a][1] = h.w;
+        }
+      }
+      geo_f32<D>(xh, xl, g);
+    }
+    if (!det_ok(g.det)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+      g.det = T(1);
+    }
+    T wv[NV];
+    if constexpr (KIND == K_WMASS_P1) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) wv[a] = wl[lv[a]];
+    }
+    const T coef = has_coef ? elem_coef<T>(A.w, A.w_kind, A.order, e0 + el) : T(1);
     ScalarVals<D, T> v;
-    element_values<D, T, KIND>(A, e0 + el, v);
+    values_from_geo<D, T, KIND>(g, has_coef, coef, wv, v);
 #pragma unroll
     for (int a = 0; a < NV; ++a) Kd[el * NV + a] = v.diag[a];
 #pragma unroll
     for (int p = 0; p < NP; ++p) Ko[el * NP + p] = v.off[p];
   }
   __syncthreads();
-  {
-    const int32_t ub = P.ch_v_ptr[c], ue = P.ch_v_ptr[c + 1];
-    const uint16_t* inc = P.inc_v + c * (int64_t)P.chunk * NV;
-    for (int32_t u = ub + threadIdx.x; u < ue; u += THREADS) {
-      const int s = P.lv_off[u];
-      const int t = (u + 1 < ue) ? (int)P.lv_off[u + 1] : ne * NV;
-      Acc<T> acc;
-      for (int j = s; j < t; ++j) acc.add(Kd[inc[j]]);
-      const int32_t dst = P.lv_dst[u];
-      if (dst >= 0) vals[dst] = acc.value();
-      else acc.store_partial(partials, -1 - (int64_t)dst);
-    }
+
+  // 2. sums over the incidences of each distinct vertex and edge, in element order
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int s = lv_off[u], t = lv_off[u + 1];
+    Acc<T> acc(Kd[inc_v[s]]);
+    for (int j = s + 1; j < t; ++j) acc.add(Kd[inc_v[j]]);
+    const int32_t dst = lv_dst[u];
+    if (dst >= 0) vals[dst] = acc.value();
+    else acc.store_partial(partials, -1 - (int64_t)dst);
   }
-  {
-    const int32_t ub = P.ch_e_ptr[c], ue = P.ch_e_ptr[c + 1];
-    const uint16_t* inc = P.inc_e + c * (int64_t)P.chunk * NP;
-    for (int32_t u = ub + threadIdx.x; u < ue; u += THREADS) {
-      const int s = P.le_off[u];
-      const int t = (u + 1 < ue) ? (int)P.le_off[u + 1] : ne * NP;
-      Acc<T> acc;
-      for (int j = s; j < t; ++j) acc.add(Ko[inc[j] >> 1]);
-      const int32_t dst = P.le_dst[2 * (int64_t)u];
-      if (dst >= 0) {
-        const T val = acc.value();
-        vals[dst] = val;
-        vals[P.le_dst[2 * (int64_t)u + 1]] = val;
-      } else {
-        acc.store_partial(partials, -1 - (int64_t)dst);
-      }
+  for (int u = threadIdx.x; u < nle; u += THREADS) {
+    const int s = le_off[u], t = le_off[u + 1];
+    Acc<T> acc(Ko[inc_e[s] >> 1]);
+    for (int j = s + 1; j < t; ++j) acc.add(Ko[inc_e[j] >> 1]);
+    const int32_t dst = le_dst[2 * u];
+    if (dst >= 0) {
+      const T val = acc.value();
+      vals[dst] = val;
+      vals[le_dst[2 * u + 1]] = val;
+    } else {
+      acc.store_partial(partials, -1 - (int64_t)dst);
     }
   }
 }
@@ -209,9 +366,9 @@ __global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t
                                T* __restrict__ vals) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nsh) return;
-  Acc<T> acc;
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
-  for (int32_t i = s; i < t; ++i) acc.add_partial(partials, i);
+  Acc<T> acc = Acc<T>::from_partial(partials, s);
+  for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, i);
   const T val = acc.value();
   vals[sh_dst[2 * g]] = val;
   if (g >= nsh_v) vals[sh_dst[2 * g + 1]] = val;
@@ -243,9 +400,9 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t* __restrict__ nsp,
                                                 const T* __restrict__ kg, T* __restrict__ vals) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= nnz) return;
-  Acc<T> acc;
   const int32_t s = nsp[j], t = nsp[j + 1];
-  for (int32_t i = s; i < t; ++i) acc.add(kg[n2s[i]]);
+  Acc<T> acc(kg[n2s[s]]);
+  for (int32_t i = s + 1; i < t; ++i) acc.add(kg[n2s[i]]);
   vals[j] = acc.value();
 }
 
@@ -268,7 +425,8 @@ __global__ void __launch_bounds__(256) k_elem_atomic(ElemArgs A, const int32_t* 
   }
 }
 
-// FP32 form: split FP64 coordinates into (hi, lo) floats, one vertex per thread
+// FP32 form of the two-pass and atomic strategies: split FP64 coordinates into
+// (hi, lo) floats, one vertex per thread
 template <int D>
 __global__ void k_split_q(const double* __restrict__ q, int64_t nq, float4* __restrict__ qs) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

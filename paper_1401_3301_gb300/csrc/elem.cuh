@@ -86,16 +86,18 @@ struct csum {
 };
 
 // ---------------------------------------------------------------- geometry
-// Cofactor vectors c[a][i] (a = 0..d; c[0] = -sum) and det B.
+// Cofactor vectors c[a][i] for a = 1..D (c[0] = -sum_a c[a] is formed only where
+// a kernel needs it) and det B.
 template <int D, class T>
 struct Geo {
   T c[D + 1][D];
-  T det;  // FP64 form: det B; FP32 form: det B rounded to float
+  T det;  // FP64 form: det B; FP32 form: det B (double-float) rounded to float
 };
 
-__device__ __forceinline__ void geo_from_edges3(const double e[3][3], Geo<3, double>& g) {
+template <class T>
+__device__ __forceinline__ void cofactors3(const T e[3][3], Geo<3, T>& g) {
   // c_1 = e_2 x e_3, c_2 = e_3 x e_1, c_3 = e_1 x e_2 (rows of adj(B), B = [e_1 e_2 e_3])
-  const double* e1 = e[0]; const double* e2 = e[1]; const double* e3 = e[2];
+  const T* e1 = e[0]; const T* e2 = e[1]; const T* e3 = e[2];
   g.c[1][0] = e2[1] * e3[2] - e2[2] * e3[1];
   g.c[1][1] = e2[2] * e3[0] - e2[0] * e3[2];
   g.c[1][2] = e2[0] * e3[1] - e2[1] * e3[0];
@@ -105,60 +107,50 @@ __device__ __forceinline__ void geo_from_edges3(const double e[3][3], Geo<3, dou
   g.c[3][0] = e1[1] * e2[2] - e1[2] * e2[1];
   g.c[3][1] = e1[2] * e2[0] - e1[0] * e2[2];
   g.c[3][2] = e1[0] * e2[1] - e1[1] * e2[0];
-  g.det = e1[0] * g.c[1][0] + e1[1] * g.c[1][1] + e1[2] * g.c[1][2];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) g.c[0][i] = -(g.c[1][i] + g.c[2][i] + g.c[3][i]);
 }
 
-__device__ __forceinline__ void geo_from_edges2(const double e[2][2], Geo<2, double>& g) {
+template <class T>
+__device__ __forceinline__ void cofactors2(const T e[2][2], Geo<2, T>& g) {
   // B = [e_1 e_2]; adj(B) rows: c_1 = (e_2y, -e_2x), c_2 = (-e_1y, e_1x)
   g.c[1][0] = e[1][1];
   g.c[1][1] = -e[1][0];
   g.c[2][0] = -e[0][1];
   g.c[2][1] = e[0][0];
-  g.det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
-  g.c[0][0] = -(g.c[1][0] + g.c[2][0]);
-  g.c[0][1] = -(g.c[1][1] + g.c[2][1]);
 }
 
-// FP64 geometry from SoA coordinates
+template <int D, class T>
+__device__ __forceinline__ void form_c0(Geo<D, T>& g) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    T s = -g.c[1][i];
+#pragma unroll
+    for (int a = 2; a <= D; ++a) s -= g.c[a][i];
+    g.c[0][i] = s;
+  }
+}
+
+// FP64 geometry from vertex coordinates x[a][c]
 template <int D>
-__device__ __forceinline__ void geo_f64(const double* __restrict__ q, int64_t nq, const int32_t v[D + 1],
-                                        Geo<D, double>& g) {
-  double x[D + 1][D];
-#pragma unroll
-  for (int a = 0; a <= D; ++a)
-#pragma unroll
-    for (int c = 0; c < D; ++c) x[a][c] = __ldg(q + (int64_t)c * nq + v[a]);
+__device__ __forceinline__ void geo_f64(const double x[D + 1][D], Geo<D, double>& g) {
   double e[D][D];
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int c = 0; c < D; ++c) e[i][c] = x[i + 1][c] - x[0][c];
-  if constexpr (D == 3) geo_from_edges3(e, g);
-  else geo_from_edges2(e, g);
+  if constexpr (D == 3) {
+    cofactors3(e, g);
+    g.det = e[0][0] * g.c[1][0] + e[0][1] * g.c[1][1] + e[0][2] * g.c[1][2];
+  } else {
+    cofactors2(e, g);
+    g.det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+  }
 }
 
-// FP32 geometry from split coordinates: qs holds, per vertex, float4 (hi) and float4 (lo)
-// in 3D, or one float4 (xh, yh, xl, yl) in 2D.
+// FP32 geometry from split coordinates (x = xh + xl): double-float edge vectors and
+// det B, float cofactors from the rounded edges.
 template <int D>
-__device__ __forceinline__ void geo_f32(const float4* __restrict__ qs, const int32_t v[D + 1],
+__device__ __forceinline__ void geo_f32(const float xh[D + 1][D], const float xl[D + 1][D],
                                         Geo<D, float>& g) {
-  float xh[D + 1][D], xl[D + 1][D];
-#pragma unroll
-  for (int a = 0; a <= D; ++a) {
-    if constexpr (D == 3) {
-      const float4 h = __ldg(qs + 2 * (int64_t)v[a]);
-      const float4 l = __ldg(qs + 2 * (int64_t)v[a] + 1);
-      xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
-      xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
-    } else {
-      const float4 h = __ldg(qs + (int64_t)v[a]);
-      xh[a][0] = h.x; xh[a][1] = h.y;
-      xl[a][0] = h.z; xl[a][1] = h.w;
-    }
-  }
-  // double-float edges e = (xh_i - xh_0) + (xl_i - xl_0)
   df e[D][D];
 #pragma unroll
   for (int i = 0; i < D; ++i)
@@ -173,41 +165,60 @@ __device__ __forceinline__ void geo_f32(const float4* __restrict__ qs, const int
 #pragma unroll
     for (int c = 0; c < D; ++c) eh[i][c] = e[i][c].hi;
   if constexpr (D == 3) {
-    // det B = e_1 . (e_2 x e_3) in double-float
     const df cx = df_add(df_mul(e[1][1], e[2][2]), df_neg(df_mul(e[1][2], e[2][1])));
     const df cy = df_add(df_mul(e[1][2], e[2][0]), df_neg(df_mul(e[1][0], e[2][2])));
     const df cz = df_add(df_mul(e[1][0], e[2][1]), df_neg(df_mul(e[1][1], e[2][0])));
     const df dt = df_add(df_add(df_mul(e[0][0], cx), df_mul(e[0][1], cy)), df_mul(e[0][2], cz));
     g.det = __fadd_rn(dt.hi, dt.lo);
-    const float* e1 = eh[0]; const float* e2 = eh[1]; const float* e3 = eh[2];
-    g.c[1][0] = e2[1] * e3[2] - e2[2] * e3[1];
-    g.c[1][1] = e2[2] * e3[0] - e2[0] * e3[2];
-    g.c[1][2] = e2[0] * e3[1] - e2[1] * e3[0];
-    g.c[2][0] = e3[1] * e1[2] - e3[2] * e1[1];
-    g.c[2][1] = e3[2] * e1[0] - e3[0] * e1[2];
-    g.c[2][2] = e3[0] * e1[1] - e3[1] * e1[0];
-    g.c[3][0] = e1[1] * e2[2] - e1[2] * e2[1];
-    g.c[3][1] = e1[2] * e2[0] - e1[0] * e2[2];
-    g.c[3][2] = e1[0] * e2[1] - e1[1] * e2[0];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) g.c[0][i] = -(g.c[1][i] + g.c[2][i] + g.c[3][i]);
+    cofactors3(eh, g);
   } else {
     const df dt = df_add(df_mul(e[0][0], e[1][1]), df_neg(df_mul(e[0][1], e[1][0])));
     g.det = __fadd_rn(dt.hi, dt.lo);
-    g.c[1][0] = eh[1][1];
-    g.c[1][1] = -eh[1][0];
-    g.c[2][0] = -eh[0][1];
-    g.c[2][1] = eh[0][0];
-    g.c[0][0] = -(g.c[1][0] + g.c[2][0]);
-    g.c[0][1] = -(g.c[1][1] + g.c[2][1]);
+    cofactors2(eh, g);
   }
 }
 
-template <class T>
-__device__ __forceinline__ bool det_ok(T det) {
-  const T a = det < T(0) ? -det : det;
-  return a > T(0) && a <= (sizeof(T) == 8 ? T(1.7976931348623157e308) : T(3.4028234663852886e38));
+// coordinates of the d+1 vertices gathered from global memory
+template <int D>
+__device__ __forceinline__ void load_x64(const double* __restrict__ q, int64_t nq, const int32_t v[D + 1],
+                                         double x[D + 1][D]) {
+#pragma unroll
+  for (int a = 0; a <= D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[a][c] = __ldg(q + (int64_t)c * nq + v[a]);
 }
+
+// split coordinates gathered from the per-vertex float4 array of the FP32 form
+template <int D>
+__device__ __forceinline__ void load_x32(const float4* __restrict__ qs, const int32_t v[D + 1],
+                                         float xh[D + 1][D], float xl[D + 1][D]) {
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    if constexpr (D == 3) {
+      const float4 h = __ldg(qs + 2 * (int64_t)v[a]);
+      const float4 l = __ldg(qs + 2 * (int64_t)v[a] + 1);
+      xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
+      xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
+    } else {
+      const float4 h = __ldg(qs + (int64_t)v[a]);
+      xh[a][0] = h.x; xh[a][1] = h.y;
+      xl[a][0] = h.z; xl[a][1] = h.w;
+    }
+  }
+}
+
+// det B usable: nonzero, normal and finite (checked on the exponent bits)
+__device__ __forceinline__ bool det_ok(double det) {
+  const unsigned int ex = ((unsigned int)__double2hiint(det) >> 20) & 0x7FFu;
+  return ex != 0u && ex != 0x7FFu;
+}
+__device__ __forceinline__ bool det_ok(float det) {
+  const unsigned int ex = ((unsigned int)__float_as_uint(det) >> 23) & 0xFFu;
+  return ex != 0u && ex != 0xFFu;
+}
+
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 
 template <class T>
 __device__ __forceinline__ T recip(T x);

@@ -33,6 +33,9 @@ __device__ __forceinline__ void fe_report(fe_status_word* st, int32_t code, long
 }
 
 // ---------------------------------------------------------------- pattern handle
+struct fe_prof_state;
+void fe_prof_free(struct fe_pattern_s* h);
+
 struct fe_pattern_s {
   int d = 0, m = 1, nv = 0, npair = 0, flags = 0, strategy = FE_REASM_CHUNKED;
   int64_t nq = 0, nme = 0, n = 0, nnz_s = 0, nnz = 0;
@@ -62,12 +65,17 @@ struct fe_pattern_s {
   int32_t* sh_ptr = nullptr;        // nsh_v + nsh_e + 1: partial ranges (vertices first)
   int32_t* sh_dst = nullptr;        // 2 per shared entity: vertex (diag nnz, vid), edge (nnz_ij, nnz_ji)
   int64_t plan_bytes = 0;
+  uint8_t* rec = nullptr;           // per-chunk plan records (plan.cuh)
+  uint32_t* rec_off16 = nullptr;    // nchunks: record offset in 16-byte units
+  int64_t rec_bytes = 0, rec_max_bytes = 0;
+  int32_t max_lv = 0;               // most local vertices of any chunk
   // scratch owned by the handle
   void* partials = nullptr; size_t partials_bytes = 0;
   void* kg = nullptr; size_t kg_bytes = 0;
   void* qsplit = nullptr; size_t qsplit_bytes = 0;
   int32_t* elas_dst = nullptr;      // vector problems: expanded destinations (see elas.cu)
   fe_status_word* status = nullptr;
+  fe_prof_state* prof = nullptr;    // per-kernel event timing (fe_profile)
   int64_t bytes = 0;
 };
 

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "fe_internal.cuh"
+#include "plan.cuh"
 
 namespace {
 
@@ -322,6 +323,54 @@ __global__ void k_shared_finish(const uint64_t* keys, const uint32_t* vals, cons
   (void)lv_dst_or_null;
 }
 
+__global__ void k_rec_sizes(int64_t nme, int chunk, int nv, int np, int64_t nchunks,
+                            const int32_t* ch_v_ptr, const int32_t* ch_e_ptr, uint32_t* size16) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nchunks) return;
+  const int64_t ne = min((int64_t)chunk, nme - c * chunk);
+  const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, ch_v_ptr[c + 1] - ch_v_ptr[c],
+                                         ch_e_ptr[c + 1] - ch_e_ptr[c]);
+  size16[c] = L.total / 16u;
+}
+
+// one block per chunk: copy the chunk's slices of the plan arrays into its record
+__global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, const int32_t* ch_v_ptr,
+                           const int32_t* ch_e_ptr, const uint16_t* inc_v, const uint16_t* inc_e,
+                           const uint16_t* lv_off, const uint16_t* le_off, const int32_t* lv_vid,
+                           const int32_t* lv_dst, const int32_t* le_dst, const uint32_t* off16,
+                           uint8_t* rec) {
+  const int64_t c = blockIdx.x;
+  const int64_t ne = min((int64_t)chunk, nme - c * chunk);
+  const int32_t vb = ch_v_ptr[c], nlv = ch_v_ptr[c + 1] - vb;
+  const int32_t eb = ch_e_ptr[c], nle = ch_e_ptr[c + 1] - eb;
+  const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, nlv, nle);
+  uint8_t* r = rec + (int64_t)off16[c] * 16;
+  uint16_t* r_inc_v = (uint16_t*)(r + L.inc_v);
+  uint16_t* r_inc_e = (uint16_t*)(r + L.inc_e);
+  uint16_t* r_lv_off = (uint16_t*)(r + L.lv_off);
+  uint16_t* r_le_off = (uint16_t*)(r + L.le_off);
+  int32_t* r_lv_vid = (int32_t*)(r + L.lv_vid);
+  int32_t* r_lv_dst = (int32_t*)(r + L.lv_dst);
+  int32_t* r_le_dst = (int32_t*)(r + L.le_dst);
+  const int64_t ibv = c * (int64_t)chunk * nv, ibe = c * (int64_t)chunk * np;
+  for (int64_t j = threadIdx.x; j < ne * nv; j += blockDim.x) r_inc_v[j] = inc_v[ibv + j];
+  for (int64_t j = threadIdx.x; j < ne * np; j += blockDim.x) r_inc_e[j] = inc_e[ibe + j];
+  for (int32_t u = threadIdx.x; u < nlv; u += blockDim.x) {
+    r_lv_off[u] = lv_off[vb + u];
+    r_lv_vid[u] = lv_vid[vb + u];
+    r_lv_dst[u] = lv_dst[vb + u];
+  }
+  for (int32_t u = threadIdx.x; u < nle; u += blockDim.x) {
+    r_le_off[u] = le_off[eb + u];
+    r_le_dst[2 * u] = le_dst[2 * (int64_t)(eb + u)];
+    r_le_dst[2 * u + 1] = le_dst[2 * (int64_t)(eb + u) + 1];
+  }
+  if (threadIdx.x == 0) {
+    r_lv_off[nlv] = (uint16_t)(ne * nv);
+    r_le_off[nle] = (uint16_t)(ne * np);
+  }
+}
+
 struct dev_tmp {
   std::vector<void*> ptrs;
   ~dev_tmp() {
@@ -351,7 +400,7 @@ int default_chunk(int d, int m) {
     const int c = atoi(env);
     if (c >= 32 && c <= 4096) return c;
   }
-  if (m == 1) return d == 3 ? 1024 : 2048;
+  if (m == 1) return d == 3 ? 512 : 1024;
   return d == 3 ? 256 : 512;
 }
 
@@ -470,11 +519,44 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
   h->npart = npart[0] + npart[1];
   k_set_last<<<1, 1, 0, s>>>(h->sh_ptr, h->nsh_v + h->nsh_e, (int32_t)(npart[0] + npart[1]));
   FE_CUDA_TRY(cudaGetLastError());
-  h->plan_bytes = (int64_t)sizeof(uint16_t) * nme * (nv + npair) +
-                  (int64_t)(sizeof(uint16_t) + 2 * sizeof(int32_t)) * nlv +
-                  (int64_t)(sizeof(uint16_t) + 2 * sizeof(int32_t)) * nle +
-                  (int64_t)sizeof(int32_t) * 2 * (h->nchunks + 1) +
-                  (int64_t)sizeof(int32_t) * 3 * (h->nsh_v + h->nsh_e + 1);
+  // per-chunk records (contiguous copies of each chunk's slice of the plan)
+  {
+    uint32_t* size16;
+    FE_TRY(tmp.get(&size16, h->nchunks + 1));
+    k_rec_sizes<<<fe_grid(h->nchunks, T), T, 0, s>>>(nme, C, nv, npair, h->nchunks, h->ch_v_ptr,
+                                                     h->ch_e_ptr, size16);
+    FE_CUDA_TRY(cudaGetLastError());
+    std::vector<uint32_t> sz(h->nchunks);
+    FE_CUDA_TRY(cudaMemcpyAsync(sz.data(), size16, sizeof(uint32_t) * h->nchunks,
+                                cudaMemcpyDeviceToHost, s));
+    FE_CUDA_TRY(cudaStreamSynchronize(s));
+    uint64_t total16 = 0;
+    uint32_t max16 = 0;
+    for (uint32_t v : sz) {
+      total16 += v;
+      if (v > max16) max16 = v;
+    }
+    if (total16 > 0xFFFFFFFFull) return FE_ERR_OVERFLOW;
+    FE_TRY(fe_malloc(h, (void**)&h->rec_off16, sizeof(uint32_t) * (h->nchunks + 1)));
+    FE_TRY(fe_scan_exclusive(size16, h->rec_off16, h->nchunks, sb->scan_tmp, s));
+    FE_TRY(fe_malloc(h, (void**)&h->rec, (size_t)total16 * 16));
+    h->rec_bytes = (int64_t)total16 * 16;
+    h->plan_bytes = h->rec_bytes + (int64_t)sizeof(int32_t) * 2 * (h->nchunks + 1);
+    h->rec_max_bytes = (int64_t)max16 * 16;
+    k_rec_fill<<<(unsigned)h->nchunks, 256, 0, s>>>(nme, C, nv, npair, h->ch_v_ptr, h->ch_e_ptr,
+                                                    h->inc_v, h->inc_e, h->lv_off, h->le_off,
+                                                    h->lv_vid, h->lv_dst, h->le_dst, h->rec_off16,
+                                                    h->rec);
+    FE_CUDA_TRY(cudaGetLastError());
+    // max local vertices of a chunk (shared-memory coordinate staging)
+    std::vector<int32_t> vp(h->nchunks + 1);
+    FE_CUDA_TRY(cudaMemcpyAsync(vp.data(), h->ch_v_ptr, sizeof(int32_t) * (h->nchunks + 1),
+                                cudaMemcpyDeviceToHost, s));
+    FE_CUDA_TRY(cudaStreamSynchronize(s));
+    int32_t mlv = 0;
+    for (int64_t c = 0; c < h->nchunks; ++c) mlv = vp[c + 1] - vp[c] > mlv ? vp[c + 1] - vp[c] : mlv;
+    h->max_lv = mlv;
+  }
   // partial-sum scratch: up to 9 values (elasticity blocks) of 8 bytes per partial
   const int vals_per_partial = (h->m == 1) ? 1 : h->m * h->m;
   const size_t pb = (size_t)(npart[0] + npart[1]) * vals_per_partial * 2 * sizeof(float) + 16;

@@ -45,7 +45,7 @@ def lib() -> C.CDLL:
         L.fe_pattern_dims.argtypes = [P, P, P, P, P, P, P]
         L.fe_pattern_set_strategy.argtypes = [P, I32]
         L.fe_pattern_memory.argtypes = [P, P]
-        L.fe_pattern_plan_info.argtypes = [P, P, P, P, P, P]
+        L.fe_pattern_plan_info.argtypes = [P, P, P, P, P, P, P, P, P]
         L.fe_pattern_destroy.argtypes = [P]
         L.fe_status.argtypes = [P, P, P, P]
         L.fe_assemble_mass.argtypes = [P, P, I32, P, P]
@@ -53,12 +53,15 @@ def lib() -> C.CDLL:
         L.fe_assemble_stiff.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_elas.argtypes = [P, P, P, I32, P, I32, I32, P, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
+        L.fe_profile.argtypes = [P, I32]
+        L.fe_profile_read.argtypes = [P, I32, P, P, P, P]
         L.fe_version.restype = C.c_char_p
         L.fe_last_cuda_error.restype = C.c_char_p
         for name in ("fe_pattern", "fe_pattern_copy_csr", "fe_pattern_copy_slot_map", "fe_pattern_dims",
                      "fe_pattern_set_strategy", "fe_pattern_memory", "fe_pattern_plan_info",
                      "fe_pattern_destroy", "fe_status", "fe_assemble_mass", "fe_assemble_wmass",
-                     "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward"):
+                     "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward",
+                     "fe_profile", "fe_profile_read"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -150,10 +153,28 @@ class Pattern:
         return b.value
 
     def plan_info(self) -> dict:
-        v = [C.c_int64() for _ in range(5)]
+        keys = ("chunk", "local_vertices", "local_edges", "partial_vertices", "partial_edges",
+                "shared_vertices", "shared_edges", "plan_bytes")
+        v = [C.c_int64() for _ in keys]
         _check(lib().fe_pattern_plan_info(self.handle, *[C.byref(x) for x in v]))
-        return dict(zip(("chunk", "local_vertices", "local_edges", "partials", "plan_bytes"),
-                        (x.value for x in v)))
+        return dict(zip(keys, (x.value for x in v)))
+
+    def profile(self, enable: bool = True):
+        _check(lib().fe_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read (synchronises)."""
+        n = 16
+        names = C.create_string_buffer(32 * n)
+        ms = (C.c_double * n)()
+        launches = (C.c_int64 * n)()
+        count = C.c_int32()
+        _check(lib().fe_profile_read(self.handle, n, names, ms, launches, C.byref(count)))
+        out = {}
+        for k in range(min(count.value, n)):
+            nm = names.raw[32 * k:32 * k + 32].split(b"\0")[0].decode()
+            out[nm] = (ms[k], launches[k])
+        return out
 
     def status(self, stream=None):
         """(code, element id) from the device status word; clears it."""
