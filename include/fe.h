@@ -43,6 +43,7 @@ extern "C" {
 #define FE_ERR_CUDA 5       /* a CUDA runtime call failed */
 #define FE_ERR_TIMEOUT 6    /* reserved: a bounded device-side wait gave up */
 #define FE_ERR_NOMEM 7      /* device allocation failed */
+#define FE_ERR_SCRATCH_LIMIT 8 /* the mesh needs more scratch than fe_assemble_stiff_noalloc has */
 
 /* ---- precision forms of the element and value kernels */
 #define FE_F64 0 /* FP64 arithmetic, FP64 values */
@@ -222,6 +223,32 @@ int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, i
 int fe_profile(fe_pattern_h h, int32_t enable);
 int fe_profile_read(fe_pattern_h h, int32_t max_kernels, char* names, double* ms,
                     int64_t* launches, int32_t* count);
+
+/*
+ * fe_assemble_stiff_noalloc -- the stiffness assembly of fe_assemble_stiff (same
+ * arguments, same result up to the summation order), computed by the two-pass
+ * scheme of FE_REASM_GATHER, that allocates no device memory. The paper has no
+ * counterpart: this exists for callers that may not call cudaMalloc while they
+ * assemble, such as a plugin inside an application that owns the whole
+ * device-memory budget, or a time-stepping loop that cannot afford the device
+ * synchronisation cudaMalloc may cause. Build the pattern first (fe_pattern
+ * allocates); this call then only reads the handle and writes `vals`.
+ *   - Its element values go to a fixed 16 MiB scratch array that is part of the
+ *     library's device image (every GPU that loads the library holds it until the
+ *     process exits). Meshes that need more, i.e. nme (d+1)^2 times 8 bytes
+ *     (FE_F64) or 4 bytes (FE_F32) above 16 MiB, are rejected with
+ *     FE_ERR_SCRATCH_LIMIT before anything is launched (3D: up to 131,072 tets
+ *     in FP64, 262,144 in FP32).
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress, no allocation) with that device current, and caches
+ *     it; make that first call before any stream capture.
+ *   - Every call, on any handle, shares the one scratch array, which keeps the last
+ *     call's contents: two calls whose kernels overlap on the GPU (different
+ *     streams, no ordering between them) race and give wrong results. Every slot
+ *     the second pass reads is written by the first, so nothing needs clearing.
+ */
+int fe_assemble_stiff_noalloc(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
+                              int32_t prec, void* vals, void* stream);
 
 /* Library version string (host pointer, static). */
 const char* fe_version(void);

@@ -18,7 +18,7 @@ COEF_NONE, COEF_SCALAR, COEF_P0, COEF_P1, COEF_P0_INTERNAL = 0, 1, 2, 3, 4
 REASM_CHUNKED, REASM_GATHER, REASM_ATOMIC = 0, 1, 2
 PATTERN_KEEP_ORDER = 1
 ERRORS = {1: "FE_ERR_ARG", 2: "FE_ERR_INDEX", 3: "FE_ERR_DEGENERATE", 4: "FE_ERR_OVERFLOW",
-          5: "FE_ERR_CUDA", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NOMEM"}
+          5: "FE_ERR_CUDA", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NOMEM", 8: "FE_ERR_SCRATCH_LIMIT"}
 
 _lib = None
 
@@ -53,6 +53,7 @@ def lib() -> C.CDLL:
         L.fe_assemble_stiff.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_elas.argtypes = [P, P, P, I32, P, I32, I32, P, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
+        L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_profile.argtypes = [P, I32]
         L.fe_profile_read.argtypes = [P, I32, P, P, P, P]
         L.fe_version.restype = C.c_char_p
@@ -61,7 +62,7 @@ def lib() -> C.CDLL:
                      "fe_pattern_set_strategy", "fe_pattern_memory", "fe_pattern_plan_info",
                      "fe_pattern_destroy", "fe_status", "fe_assemble_mass", "fe_assemble_wmass",
                      "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward",
-                     "fe_profile", "fe_profile_read"):
+                     "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -247,6 +248,17 @@ def fe_assemble_stiff_backward(p: Pattern, q: torch.Tensor, w, w_kind: int, u: t
         p.handle, _dev(q, torch.float64, "q"), _dev(w, T, "w"), w_kind, _dev(u, T, "u"), _dev(v, T, "v"),
         _dev(L, T, "L"), _dev(dL_dw, T, "dL_dw"), _dev(dL_dq, T, "dL_dq"), prec, _stream(stream)))
     return L, dL_dw, dL_dq
+
+
+def fe_assemble_stiff_noalloc(p: Pattern, q: torch.Tensor, vals: torch.Tensor, w=None,
+                              w_kind: int | None = None, prec: int = F64, stream=None):
+    """Stiffness assembly that allocates no device memory (see include/fe.h): the
+    caller passes the output buffer `vals` (nnz values of the form's precision)."""
+    if w_kind is None:
+        w_kind = COEF_NONE if w is None else COEF_P0
+    _check(lib().fe_assemble_stiff_noalloc(p.handle, _dev(q, torch.float64, "q"), _dev(w, _vtype(prec), "w"),
+                                           w_kind, prec, _dev(vals, _vtype(prec), "vals"), _stream(stream)))
+    return vals
 
 
 def fe_version() -> str:
