@@ -39,7 +39,8 @@ void fe_free_all(fe_pattern_s* h) {
                   h->nnz_slot_ptr, h->nnz2slot, h->ch_v_ptr, h->ch_e_ptr, h->lv_off,
                   h->le_off,  h->inc_v,    h->inc_e,     h->lv_dst,    h->lv_vid,
                   h->le_dst,  h->sh_ptr,   h->sh_dst,    h->partials,  h->kg,
-                  h->qsplit,  h->status, h->rec, h->rec_off16};
+                  h->qsplit,  h->status, h->rec, h->rec_off16,
+                  h->lv_str,  h->le_str,   h->sh_str};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->m > 1) {

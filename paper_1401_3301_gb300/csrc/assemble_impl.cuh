@@ -135,6 +135,7 @@ struct Acc;
 template <>
 struct Acc<double> {
   double s;
+  Acc() = default;
   __device__ __forceinline__ explicit Acc(double first) : s(first) {}
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
@@ -147,6 +148,7 @@ struct Acc<double> {
 template <>
 struct Acc<float> {
   csum s;
+  Acc() = default;
   __device__ __forceinline__ explicit Acc(float first) { s.s = first; s.c = 0.f; }
   __device__ __forceinline__ void add(float x) { s.add(x); }
   __device__ __forceinline__ float value() const { return s.value(); }

@@ -1,6 +1,344 @@
-// Linear elasticity (placeholder until the vector kernels land).
-#include "fe_internal.cuh"
-int fe_launch_elas(fe_pattern_s*, const double*, const void*, int, const void*, int, int, void*,
-                   cudaStream_t) {
-  return FE_ERR_ARG;
+// Linear elasticity (Section 5.1 of the paper): the m = d vector problem with the
+// isotropic Hooke law, reassembled into the m x m block CSR of the pattern.
+//
+// Local matrix (Lemma lem:VecLocalElas, App. B, with the P1 interpolants of the
+// Lame fields): for vertices a, b and components l, n,
+//   K_{(a,l),(b,n)} = |K|/(d+1) (lambda^s g_b[n] g_a[l] + mu^s (delta_ln g_a . g_b + g_b[l] g_a[n]))
+// With g_a = c_a / det B (cofactor vectors) this is
+//   lp c_a[l] c_b[n] + mp (delta_ln c_a . c_b + c_b[l] c_a[n]),
+//   lp = lambda^s / (d! (d+1) |det B|), mp = mu^s / (d! (d+1) |det B|).
+// The kernel keeps, per element, the cofactor vectors and (lp, mp) in shared
+// memory and forms each 3x3 (2x2) block while summing the incidences of a chunk's
+// vertices (diagonal blocks) and edges (off-diagonal blocks, written at (i,j) and,
+// transposed, at (j,i)), in ascending element order.
+#include "assemble_impl.cuh"
+#include "profile.cuh"
+
+namespace fe {
+namespace {
+
+struct ElasArgs {
+  int64_t nme, nq;
+  int chunk;
+  uint32_t rec_max, max_lv;
+  const double* q;
+  const void* lam;
+  int lam_kind;
+  const void* mu;
+  int mu_kind;
+  const int32_t* order;
+  const int32_t* ch_v_ptr;
+  const int32_t* ch_e_ptr;
+  const uint8_t* rec;
+  const uint32_t* rec_off16;
+  fe_status_word* st;
+};
+
+struct ElasSmem {
+  uint32_t q, coef, lvid, cg, lm, total;
+};
+__host__ __device__ __forceinline__ ElasSmem elas_smem(int D, int sizeT, uint32_t rec_max,
+                                                       uint32_t max_lv, uint32_t chunk) {
+  const uint32_t nv = D + 1;
+  ElasSmem L;
+  uint32_t o = pad16(rec_max);
+  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
+  L.coef = o; o += pad16(2u * sizeT * max_lv);
+  L.lvid = o; o += pad16(2u * nv * chunk);
+  L.cg = o;   o += pad16(sizeT * nv * D * chunk);
+  L.lm = o;   o += pad16(2u * sizeT * chunk);
+  L.total = o;
+  return L;
+}
+
+// sum over the element's vertices of a coefficient's P1 values (lambda^s, mu^s)
+template <int D, class T>
+__device__ __forceinline__ T coef_sum(const void* c, int kind, const int32_t* order, int64_t e,
+                                      const T* local_p1, const int lv[D + 1]) {
+  const T* cp = (const T*)c;
+  if (kind == FE_COEF_P1) {
+    T s = local_p1[lv[0]];
+#pragma unroll
+    for (int a = 1; a <= D; ++a) s += local_p1[lv[a]];
+    return s;
+  }
+  T v;
+  if (kind == FE_COEF_SCALAR) v = cp[0];
+  else if (kind == FE_COEF_P0) v = cp[order[e]];
+  else v = cp[e];
+  return T(D + 1) * v;
+}
+
+// block (a, a) of one element from x = c_a: (lp + mp) x x^T + mp |x|^2 I
+template <int D, class T>
+__device__ __forceinline__ void diag_block(const T* x, T lp, T mp, T* blk) {
+  T xx = x[0] * x[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) xx += x[i] * x[i];
+  const T lm = lp + mp, mxx = mp * xx;
+#pragma unroll
+  for (int l = 0; l < D; ++l)
+#pragma unroll
+    for (int n = 0; n < D; ++n) blk[l * D + n] = lm * x[l] * x[n] + (l == n ? mxx : T(0));
+}
+
+// block (a, b) of one element from x = c_a, y = c_b: entry (l, n) =
+// lp x_l y_n + mp (y_l x_n + delta_ln x . y)
+template <int D, class T>
+__device__ __forceinline__ void edge_block(const T* x, const T* y, T lp, T mp, T* blk) {
+  T xy = x[0] * y[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) xy += x[i] * y[i];
+  const T mxy = mp * xy;
+#pragma unroll
+  for (int l = 0; l < D; ++l)
+#pragma unroll
+    for (int n = 0; n < D; ++n) blk[l * D + n] = lp * x[l] * y[n] + mp * y[l] * x[n] + (l == n ? mxy : T(0));
+}
+
+template <int D, class T, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restrict__ vals,
+                                                        void* __restrict__ partials) {
+  constexpr int NV = D + 1, NP = Pairs<D>::n, MM = D * D;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t c = blockIdx.x;
+  const int64_t e0 = c * A.chunk;
+  const int ne = (int)min((int64_t)A.chunk, A.nme - e0);
+  const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
+  const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
+  const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle, true);
+  const ElasSmem S = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, R.total);
+    bulk_copy_g2s(smem, A.rec + (int64_t)A.rec_off16[c] * 16, R.total, &bar);
+  }
+  __syncthreads();
+  const bool landed = __syncthreads_and(mbar_wait_bounded(&bar, 0, kBarrierSpin));
+  if (!landed) {
+    if (threadIdx.x == 0) {
+      fe_report(A.st, FE_ERR_TIMEOUT, e0);
+      mbar_wait_bounded(&bar, 0, kBarrierSpin);
+    }
+    return;
+  }
+  const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
+  const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
+  const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
+  const uint16_t* le_off = (const uint16_t*)(smem + R.le_off);
+  const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
+  const uint16_t* lv_str = (const uint16_t*)(smem + R.lv_str);
+  const uint16_t* le_str = (const uint16_t*)(smem + R.le_str);
+  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  T* lam_l = (T*)(smem + S.coef);
+  T* mu_l = lam_l + A.max_lv;
+  T* Cg = (T*)(smem + S.cg);   // [e][a][i]
+  T* LM = (T*)(smem + S.lm);   // [e][2]
+
+  // 0. coordinates (and P1 Lame values) of the chunk's vertices; local vertex of each corner
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int64_t vid = lv_vid[u];
+    double x[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = __ldg(A.q + k * A.nq + vid);
+    if constexpr (sizeof(T) == 8) {
+      double* xs = (double*)(smem + S.q) + (D == 3 ? 4 : 2) * u;
+      ((double2*)xs)[0] = make_double2(x[0], x[1]);
+      if constexpr (D == 3) xs[2] = x[2];
+    } else {
+      float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < D; ++k) split_f64(x[k], h[k], l[k]);
+      float4* xs = (float4*)(smem + S.q) + (D == 3 ? 2 : 1) * u;
+      if constexpr (D == 3) {
+        xs[0] = make_float4(h[0], h[1], h[2], 0.f);
+        xs[1] = make_float4(l[0], l[1], l[2], 0.f);
+      } else {
+        xs[0] = make_float4(h[0], h[1], l[0], l[1]);
+      }
+    }
+    if (A.lam_kind == FE_COEF_P1) lam_l[u] = ((const T*)A.lam)[vid];
+    if (A.mu_kind == FE_COEF_P1) mu_l[u] = ((const T*)A.mu)[vid];
+    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
+  }
+  __syncthreads();
+
+  // 1. cofactor vectors and scaled Lame sums of every element
+  for (int el = threadIdx.x; el < ne; el += THREADS) {
+    int lv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
+    Geo<D, T> g;
+    if constexpr (sizeof(T) == 8) {
+      double x[NV][D];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const double* xs = (const double*)(smem + S.q) + (D == 3 ? 4 : 2) * lv[a];
+        const double2 xy = ((const double2*)xs)[0];
+        x[a][0] = xy.x;
+        x[a][1] = xy.y;
+        if constexpr (D == 3) x[a][2] = xs[2];
+      }
+      geo_f64<D>(x, g);
+    } else {
+      float xh[NV][D], xl[NV][D];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lv[a];
+        const float4 h = xs[0];
+        if constexpr (D == 3) {
+          const float4 l = xs[1];
+          xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
+          xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
+        } else {
+          xh[a][0] = h.x; xh[a][1] = h.y;
+          xl[a][0] = h.z; xl[a][1] = h.w;
+        }
+      }
+      geo_f32<D>(xh, xl, g);
+    }
+    if (!det_ok(g.det)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+      g.det = T(1);
+    }
+    form_c0<D, T>(g);
+    const T scale = recip<T>(T(factorial(D) * (D + 1)) * tabs(g.det));
+    const T ls = coef_sum<D, T>(A.lam, A.lam_kind, A.order, e0 + el, lam_l, lv);
+    const T ms = coef_sum<D, T>(A.mu, A.mu_kind, A.order, e0 + el, mu_l, lv);
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int i = 0; i < D; ++i) Cg[(el * NV + a) * D + i] = g.c[a][i];
+    LM[2 * el] = ls * scale;
+    LM[2 * el + 1] = ms * scale;
+  }
+  __syncthreads();
+
+  // 2a. diagonal blocks: sum over (element, corner) incidences of each vertex
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int s = lv_off[u], t = lv_off[u + 1];
+    Acc<T> acc[MM];
+    for (int j = s; j < t; ++j) {
+      const int inc = inc_v[j];
+      const int el = inc / NV;
+      T blk[MM];
+      diag_block<D, T>(Cg + inc * D, LM[2 * el], LM[2 * el + 1], blk);
+#pragma unroll
+      for (int k = 0; k < MM; ++k) {
+        if (j == s) acc[k] = Acc<T>(blk[k]);
+        else acc[k].add(blk[k]);
+      }
+    }
+    const int32_t dst = lv_dst[u];
+    if (dst >= 0) {
+      const int str = lv_str[u];
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+#pragma unroll
+        for (int n = 0; n < D; ++n) vals[dst + l * str + n] = acc[l * D + n].value();
+    } else {
+      const int64_t pi = (-1 - (int64_t)dst) * MM;
+#pragma unroll
+      for (int k = 0; k < MM; ++k) acc[k].store_partial(partials, pi + k);
+    }
+  }
+  // 2b. off-diagonal blocks: (element, pair) incidences of each edge, oriented (vmin, vmax)
+  for (int u = threadIdx.x; u < nle; u += THREADS) {
+    const int s = le_off[u], t = le_off[u + 1];
+    Acc<T> acc[MM];
+    for (int j = s; j < t; ++j) {
+      const int code = inc_e[j];
+      const int ep = code >> 1;
+      const int el = ep / NP, p = ep - el * NP;
+      int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
+      if (code & 1) {  // me(a) > me(b): the (vmin, vmax) block is block (b, a)
+        const int t2 = a; a = b; b = t2;
+      }
+      T blk[MM];
+      edge_block<D, T>(Cg + (el * NV + a) * D, Cg + (el * NV + b) * D, LM[2 * el], LM[2 * el + 1], blk);
+#pragma unroll
+      for (int k = 0; k < MM; ++k) {
+        if (j == s) acc[k] = Acc<T>(blk[k]);
+        else acc[k].add(blk[k]);
+      }
+    }
+    const int32_t dst = le_dst[2 * u];
+    if (dst >= 0) {
+      const int32_t dst_t = le_dst[2 * u + 1];
+      const int str = le_str[2 * u], str_t = le_str[2 * u + 1];
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+#pragma unroll
+        for (int n = 0; n < D; ++n) {
+          const T v = acc[l * D + n].value();
+          vals[dst + l * str + n] = v;
+          vals[dst_t + n * str_t + l] = v;
+        }
+    } else {
+      const int64_t pi = (-1 - (int64_t)dst) * MM;
+#pragma unroll
+      for (int k = 0; k < MM; ++k) acc[k].store_partial(partials, pi + k);
+    }
+  }
+}
+
+// Sum, in chunk order, of the partial blocks of each shared vertex / edge.
+template <int D, class T>
+__global__ void k_fixup_elas(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
+                             const int32_t* __restrict__ sh_str, int64_t nsh_v, int64_t nsh,
+                             const void* __restrict__ partials, T* __restrict__ vals) {
+  constexpr int MM = D * D;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nsh) return;
+  const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
+  const int32_t dst = sh_dst[2 * g];
+  const int str = sh_str[2 * g];
+#pragma unroll
+  for (int k = 0; k < MM; ++k) {
+    Acc<T> acc = Acc<T>::from_partial(partials, (int64_t)s * MM + k);
+    for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, (int64_t)i * MM + k);
+    const T v = acc.value();
+    const int l = k / D, n = k % D;
+    vals[dst + l * str + n] = v;
+    if (g >= nsh_v) vals[sh_dst[2 * g + 1] + n * sh_str[2 * g + 1] + l] = v;
+  }
+}
+
+template <int D, class T>
+int launch(fe_pattern_s* h, const ElasArgs& A, T* vals, cudaStream_t s) {
+  constexpr int THREADS = 256;
+  const ElasSmem L = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
+  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  auto kern = k_chunk_elas<D, T, THREADS>;
+  FE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  FE_PROF_BEGIN(h, FE_K_ELAS_CHUNK, s);
+  kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, h->partials);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_PROF_END(h, FE_K_ELAS_CHUNK, s);
+  const int64_t nsh = h->nsh_v + h->nsh_e;
+  if (nsh > 0) {
+    FE_PROF_BEGIN(h, FE_K_ELAS_FIXUP, s);
+    k_fixup_elas<D, T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->sh_str, h->nsh_v, nsh,
+                                                         h->partials, vals);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_PROF_END(h, FE_K_ELAS_FIXUP, s);
+  }
+  return FE_OK;
+}
+
+}  // namespace
+}  // namespace fe
+
+int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_kind, const void* mu,
+                   int mu_kind, int prec, void* vals, cudaStream_t s) {
+  using namespace fe;
+  if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;  // vector problems: chunked only
+  ElasArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, lam, lam_kind,
+             mu, mu_kind, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
+  if (prec == FE_F64)
+    return h->d == 3 ? launch<3, double>(h, A, (double*)vals, s) : launch<2, double>(h, A, (double*)vals, s);
+  return h->d == 3 ? launch<3, float>(h, A, (float*)vals, s) : launch<2, float>(h, A, (float*)vals, s);
 }

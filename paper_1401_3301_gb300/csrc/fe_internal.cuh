@@ -60,10 +60,13 @@ struct fe_pattern_s {
   int32_t* lv_dst = nullptr;        // nlv: diagonal scalar nnz (>= 0) or -1 - partial index
   int32_t* lv_vid = nullptr;        // nlv: vertex id
   int32_t* le_dst = nullptr;        // 2 nle: scalar nnz (i,j), (j,i) with i < j, or -1 - partial
+  uint16_t* lv_str = nullptr;       // m > 1: block row stride of each local vertex (dst = block base)
+  uint16_t* le_str = nullptr;       // m > 1: 2 nle block row strides
   int64_t nsh_v = 0, nsh_e = 0;     // shared vertices / edges
   int64_t npart_v = 0, npart = 0;   // partial sums of shared vertices / all partial sums
   int32_t* sh_ptr = nullptr;        // nsh_v + nsh_e + 1: partial ranges (vertices first)
   int32_t* sh_dst = nullptr;        // 2 per shared entity: vertex (diag nnz, vid), edge (nnz_ij, nnz_ji)
+  int32_t* sh_str = nullptr;        // m > 1: 2 per shared entity, block row strides
   int64_t plan_bytes = 0;
   uint8_t* rec = nullptr;           // per-chunk plan records (plan.cuh)
   uint32_t* rec_off16 = nullptr;    // nchunks: record offset in 16-byte units

@@ -235,8 +235,9 @@ __global__ void k_einc_keys(const int32_t* me_int, int64_t nme, int nv, int npai
 // global destination(s). Shared entities are flagged for the partial-sum pass.
 __global__ void k_local_entities(const uint64_t* keys, const uint32_t* pos, int64_t n, int per_elem,
                                  int chunk, int ebits, int vbits, bool edges, const int32_t* rp,
-                                 const int32_t* ci, const int32_t* nnz_slot_ptr, uint16_t* off,
-                                 int32_t* ch_ptr, int32_t* dst, int32_t* vid, uint32_t* shared_flag) {
+                                 const int32_t* ci, const int32_t* nnz_slot_ptr, int m, uint16_t* off,
+                                 int32_t* ch_ptr, int32_t* dst, int32_t* vid, uint16_t* str,
+                                 uint32_t* shared_flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t key = keys[i];
@@ -256,12 +257,22 @@ __global__ void k_local_entities(const uint64_t* keys, const uint32_t* pos, int6
     dst[u] = dnz;
     vid[u] = v;
     global_count = nnz_slot_ptr[dnz + 1] - nnz_slot_ptr[dnz];
+    if (m > 1) {  // m x m block: entry (l, n) at dst + l * str + n
+      dst[u] = m * m * rp[v] + m * (dnz - rp[v]);
+      str[u] = (uint16_t)(m * (rp[v + 1] - rp[v]));
+    }
   } else {
     const int32_t hi = (int32_t)(key & vmask), lo = (int32_t)((key >> vbits) & vmask);
     const int32_t nij = find_nnz(rp, ci, lo, hi), nji = find_nnz(rp, ci, hi, lo);
     dst[2 * (int64_t)u] = nij;
     dst[2 * (int64_t)u + 1] = nji;
     global_count = nnz_slot_ptr[nij + 1] - nnz_slot_ptr[nij];
+    if (m > 1) {
+      dst[2 * (int64_t)u] = m * m * rp[lo] + m * (nij - rp[lo]);
+      dst[2 * (int64_t)u + 1] = m * m * rp[hi] + m * (nji - rp[hi]);
+      str[2 * (int64_t)u] = (uint16_t)(m * (rp[lo + 1] - rp[lo]));
+      str[2 * (int64_t)u + 1] = (uint16_t)(m * (rp[hi + 1] - rp[hi]));
+    }
   }
   shared_flag[u] = (local_count < global_count) ? 1u : 0u;
 }
@@ -302,7 +313,8 @@ __global__ void k_shared_keys(const uint32_t* shared_flag, const uint32_t* spos,
 __global__ void k_shared_finish(const uint64_t* keys, const uint32_t* vals, const uint32_t* gpos,
                                 int64_t n, int cbits, int64_t part_base, int64_t ent_base,
                                 int32_t* dst, int dst_stride, const int32_t* vid, bool edges,
-                                int32_t* sh_ptr, int32_t* sh_dst, int32_t* lv_dst_or_null) {
+                                int32_t* sh_ptr, int32_t* sh_dst, const uint16_t* str,
+                                int32_t* sh_str) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t u = vals[i];
@@ -314,37 +326,50 @@ __global__ void k_shared_finish(const uint64_t* keys, const uint32_t* vals, cons
     if (!edges) {
       sh_dst[2 * g] = dst[(int64_t)u * dst_stride];
       sh_dst[2 * g + 1] = vid[u];
+      if (sh_str) sh_str[2 * g] = str[u];
     } else {
       sh_dst[2 * g] = dst[(int64_t)u * dst_stride];
       sh_dst[2 * g + 1] = dst[(int64_t)u * dst_stride + 1];
+      if (sh_str) {
+        sh_str[2 * g] = str[2 * (int64_t)u];
+        sh_str[2 * g + 1] = str[2 * (int64_t)u + 1];
+      }
     }
   }
   dst[(int64_t)u * dst_stride] = -1 - (int32_t)(part_base + i);
-  (void)lv_dst_or_null;
 }
 
-__global__ void k_rec_sizes(int64_t nme, int chunk, int nv, int np, int64_t nchunks,
+__global__ void k_rec_sizes(int64_t nme, int chunk, int nv, int np, int m, int64_t nchunks,
                             const int32_t* ch_v_ptr, const int32_t* ch_e_ptr, uint32_t* size16) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nchunks) return;
   const int64_t ne = min((int64_t)chunk, nme - c * chunk);
   const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, ch_v_ptr[c + 1] - ch_v_ptr[c],
-                                         ch_e_ptr[c + 1] - ch_e_ptr[c]);
+                                         ch_e_ptr[c + 1] - ch_e_ptr[c], m > 1);
   size16[c] = L.total / 16u;
 }
 
 // one block per chunk: copy the chunk's slices of the plan arrays into its record
-__global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, const int32_t* ch_v_ptr,
+__global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, int m, const int32_t* ch_v_ptr,
                            const int32_t* ch_e_ptr, const uint16_t* inc_v, const uint16_t* inc_e,
                            const uint16_t* lv_off, const uint16_t* le_off, const int32_t* lv_vid,
-                           const int32_t* lv_dst, const int32_t* le_dst, const uint32_t* off16,
-                           uint8_t* rec) {
+                           const int32_t* lv_dst, const int32_t* le_dst, const uint16_t* lv_str,
+                           const uint16_t* le_str, const uint32_t* off16, uint8_t* rec) {
   const int64_t c = blockIdx.x;
   const int64_t ne = min((int64_t)chunk, nme - c * chunk);
   const int32_t vb = ch_v_ptr[c], nlv = ch_v_ptr[c + 1] - vb;
   const int32_t eb = ch_e_ptr[c], nle = ch_e_ptr[c + 1] - eb;
-  const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, nlv, nle);
+  const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, nlv, nle, m > 1);
   uint8_t* r = rec + (int64_t)off16[c] * 16;
+  if (m > 1) {
+    uint16_t* r_lv_str = (uint16_t*)(r + L.lv_str);
+    uint16_t* r_le_str = (uint16_t*)(r + L.le_str);
+    for (int32_t u = threadIdx.x; u < nlv; u += blockDim.x) r_lv_str[u] = lv_str[vb + u];
+    for (int32_t u = threadIdx.x; u < nle; u += blockDim.x) {
+      r_le_str[2 * u] = le_str[2 * (int64_t)(eb + u)];
+      r_le_str[2 * u + 1] = le_str[2 * (int64_t)(eb + u) + 1];
+    }
+  }
   uint16_t* r_inc_v = (uint16_t*)(r + L.inc_v);
   uint16_t* r_inc_e = (uint16_t*)(r + L.inc_e);
   uint16_t* r_lv_off = (uint16_t*)(r + L.lv_off);
@@ -439,7 +464,9 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     FE_TRY(to_host(&last_flag, flag + n - 1, s));
     const int64_t nloc = (int64_t)last_pos + last_flag;
     uint16_t* inc; uint16_t* off; int32_t* ch_ptr; int32_t* dst; int32_t* vid = nullptr;
+    uint16_t* str = nullptr;
     uint32_t* sflag;
+    if (h->m > 1) FE_TRY(fe_malloc(h, (void**)&str, sizeof(uint16_t) * nloc * (edges ? 2 : 1)));
     FE_TRY(fe_malloc(h, (void**)&inc, sizeof(uint16_t) * n));
     FE_TRY(fe_malloc(h, (void**)&off, sizeof(uint16_t) * nloc));
     FE_TRY(fe_malloc(h, (void**)&ch_ptr, sizeof(int32_t) * (h->nchunks + 1)));
@@ -450,16 +477,18 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     k_to_u16<<<fe_grid(n, T), T, 0, s>>>(vals, inc, n);
     FE_CUDA_TRY(cudaGetLastError());
     k_local_entities<<<fe_grid(n, T), T, 0, s>>>(keys, pos, n, per, C, ebits, vbits, edges,
-                                                  h->row_ptr_s, h->col_idx_s, h->nnz_slot_ptr, off,
-                                                  ch_ptr, dst, vid, sflag);
+                                                  h->row_ptr_s, h->col_idx_s, h->nnz_slot_ptr, h->m,
+                                                  off, ch_ptr, dst, vid, str, sflag);
     FE_CUDA_TRY(cudaGetLastError());
     k_set_last<<<1, 1, 0, s>>>(ch_ptr, h->nchunks, (int32_t)nloc);
     FE_CUDA_TRY(cudaGetLastError());
     if (!edges) {
       h->inc_v = inc; h->lv_off = off; h->ch_v_ptr = ch_ptr; h->lv_dst = dst; h->lv_vid = vid;
+      h->lv_str = str;
       sflag_v = sflag; nlv = nloc;
     } else {
       h->inc_e = inc; h->le_off = off; h->ch_e_ptr = ch_ptr; h->le_dst = dst;
+      h->le_str = str;
       sflag_e = sflag; nle = nloc;
     }
   }
@@ -484,6 +513,8 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
   // with an upper bound (npart) and trim counts later
   FE_TRY(fe_malloc(h, (void**)&h->sh_ptr, sizeof(int32_t) * (npart[0] + npart[1] + 1)));
   FE_TRY(fe_malloc(h, (void**)&h->sh_dst, sizeof(int32_t) * 2 * (npart[0] + npart[1] + 1)));
+  if (h->m > 1)
+    FE_TRY(fe_malloc(h, (void**)&h->sh_str, sizeof(int32_t) * 2 * (npart[0] + npart[1] + 1)));
   int64_t ent_base = 0;
   for (int pass = 0; pass < 2; ++pass) {
     const bool edges = pass == 1;
@@ -496,7 +527,7 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     k_shared_keys<<<fe_grid(nloc, T), T, 0, s>>>(edges ? sflag_e : sflag_v, spos[pass], nloc, dst,
                                                  stride, ch_ptr, h->nchunks, cbits, sb->k0, sb->v0);
     FE_CUDA_TRY(cudaGetLastError());
-    const int kbits = bitlen((uint64_t)(h->nnz_s > 1 ? h->nnz_s - 1 : 1)) + cbits;
+    const int kbits = bitlen((uint64_t)(h->nnz > 1 ? h->nnz - 1 : 1)) + cbits;
     FE_TRY(fe_radix_sort(np, kbits, sb, &keys, &vals, s));
     // distinct entities
     k_entity_change<<<fe_grid(np, T), T, 0, s>>>(keys, np, cbits, flag);
@@ -509,7 +540,7 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     const int64_t part_base = edges ? npart[0] : 0;
     k_shared_finish<<<fe_grid(np, T), T, 0, s>>>(keys, vals, pos, np, cbits, part_base, ent_base,
                                                   dst, stride, h->lv_vid, edges, h->sh_ptr,
-                                                  h->sh_dst, nullptr);
+                                                  h->sh_dst, edges ? h->le_str : h->lv_str, h->sh_str);
     FE_CUDA_TRY(cudaGetLastError());
     ent_base += nsh_ent[pass];
   }
@@ -523,8 +554,8 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
   {
     uint32_t* size16;
     FE_TRY(tmp.get(&size16, h->nchunks + 1));
-    k_rec_sizes<<<fe_grid(h->nchunks, T), T, 0, s>>>(nme, C, nv, npair, h->nchunks, h->ch_v_ptr,
-                                                     h->ch_e_ptr, size16);
+    k_rec_sizes<<<fe_grid(h->nchunks, T), T, 0, s>>>(nme, C, nv, npair, h->m, h->nchunks,
+                                                     h->ch_v_ptr, h->ch_e_ptr, size16);
     FE_CUDA_TRY(cudaGetLastError());
     std::vector<uint32_t> sz(h->nchunks);
     FE_CUDA_TRY(cudaMemcpyAsync(sz.data(), size16, sizeof(uint32_t) * h->nchunks,
@@ -543,10 +574,10 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     h->rec_bytes = (int64_t)total16 * 16;
     h->plan_bytes = h->rec_bytes + (int64_t)sizeof(int32_t) * 2 * (h->nchunks + 1);
     h->rec_max_bytes = (int64_t)max16 * 16;
-    k_rec_fill<<<(unsigned)h->nchunks, 256, 0, s>>>(nme, C, nv, npair, h->ch_v_ptr, h->ch_e_ptr,
-                                                    h->inc_v, h->inc_e, h->lv_off, h->le_off,
-                                                    h->lv_vid, h->lv_dst, h->le_dst, h->rec_off16,
-                                                    h->rec);
+    k_rec_fill<<<(unsigned)h->nchunks, 256, 0, s>>>(nme, C, nv, npair, h->m, h->ch_v_ptr,
+                                                    h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off,
+                                                    h->le_off, h->lv_vid, h->lv_dst, h->le_dst,
+                                                    h->lv_str, h->le_str, h->rec_off16, h->rec);
     FE_CUDA_TRY(cudaGetLastError());
     // max local vertices of a chunk (shared-memory coordinate staging)
     std::vector<int32_t> vp(h->nchunks + 1);

@@ -8,6 +8,9 @@
 //   lv_vid int32[nlv]          global vertex id
 //   lv_dst int32[nlv]          diagonal nonzero (>= 0) or -1 - partial index
 //   le_dst int32[2 * nle]      nonzeros (i,j), (j,i) with i < j, or -1 - partial index
+// Vector problems (m > 1) add the row strides of the m x m blocks, whose entry
+// (l, n) is at dst + l * stride + n:
+//   lv_str uint16[nlv], le_str uint16[2 * nle]
 // Each array starts on a 16-byte boundary.
 #pragma once
 
@@ -16,13 +19,14 @@
 namespace fe {
 
 struct RecLayout {
-  uint32_t inc_v, inc_e, lv_off, le_off, lv_vid, lv_dst, le_dst, total;
+  uint32_t inc_v, inc_e, lv_off, le_off, lv_vid, lv_dst, le_dst, lv_str, le_str, total;
 };
 
 __host__ __device__ __forceinline__ uint32_t pad16(uint32_t x) { return (x + 15u) & ~15u; }
 
 __host__ __device__ __forceinline__ RecLayout rec_layout(uint32_t ne, uint32_t nv, uint32_t np,
-                                                         uint32_t nlv, uint32_t nle) {
+                                                         uint32_t nlv, uint32_t nle,
+                                                         bool vector = false) {
   RecLayout L;
   uint32_t o = 0;
   L.inc_v = o;  o += pad16(2u * nv * ne);
@@ -32,6 +36,8 @@ __host__ __device__ __forceinline__ RecLayout rec_layout(uint32_t ne, uint32_t n
   L.lv_vid = o; o += pad16(4u * nlv);
   L.lv_dst = o; o += pad16(4u * nlv);
   L.le_dst = o; o += pad16(8u * nle);
+  L.lv_str = o; o += vector ? pad16(2u * nlv) : 0u;
+  L.le_str = o; o += vector ? pad16(4u * nle) : 0u;
   L.total = o;
   return L;
 }
