@@ -198,19 +198,40 @@ int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t l
 
 /*
  * fe_assemble_stiff_backward -- gradients of L = u^T S(w) v, S the stiffness
- * matrix of fe_assemble_stiff (the paper has no derivatives; these follow from
- * Eq. stiffelemmat and App. C.1):
- *   dL/dw_K = |K| ubar . vbar,  ubar = sum_a u(me(a,K)) grad lambda_a (same for v),
- *   dL/dq^c = sum_K w_K |K| [(ubar . vbar) g_c - ubar (g_c . vbar) - vbar (g_c . ubar)].
- * u, v: nq values; dL_dw: nme values in the order given by w_kind (input order
- * for FE_COEF_NONE/FE_COEF_P0, internal for FE_COEF_P0_INTERNAL), may be NULL;
- * dL_dq: d x nq like q, may be NULL; L: one value (device), may be NULL. All of
- * u, v, dL_dw, dL_dq, L use the precision of the form. Vertex sums are taken in a
- * fixed order (bit-identical run to run).
+ * matrix of fe_assemble_stiff, without forming any matrix (the paper has no
+ * derivatives; these follow from Eq. stiffelemmat and App. C.1). Per element,
+ * with ubar = sum_a u(me(a)) grad lambda_a and vbar likewise:
+ *   L_K = w_K |K| ubar . vbar,     dL/dw_K = |K| ubar . vbar,
+ *   dL/dq^c = sum_K w_K |K| [(ubar . vbar) g_c - ubar (g_c . vbar) - vbar (g_c . ubar)],
+ * g_c the gradient of the barycentric coordinate of vertex c in K.
+ *   w, w_kind   per-element coefficient (FE_COEF_NONE, FE_COEF_P0, FE_COEF_P0_INTERNAL)
+ *   u, v        nq values each
+ *   L           one value, or NULL
+ *   dL_dw       nme values (input element order, or internal for
+ *               FE_COEF_P0_INTERNAL), or NULL
+ *   dL_dq       d x nq like q, or NULL
+ * All of u, v, L, dL_dw, dL_dq (and w) use the precision of the form. Sums over
+ * the elements of a vertex, and the sum of L, are taken in a fixed order
+ * (bit-identical run to run). The first backward call on a handle allocates its
+ * scratch (d (d+1) values per element) and builds the vertex -> element lists,
+ * synchronously; later calls allocate nothing.
  */
 int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
                                const void* u, const void* v, void* L, void* dL_dw, void* dL_dq,
                                int32_t prec, void* stream);
+
+/*
+ * fe_assemble_stiff_vjp -- vector-Jacobian product of the stiffness assembly: for
+ * any loss L of the CSR values S(w, q), given grad_vals = dL/dS (nnz values, CSR
+ * order), writes dL/dw (nme values, as in fe_assemble_stiff_backward) and dL/dq
+ * (d x nq). Per element the weights G^_ab = grad_vals at the nonzero of slot (a, b)
+ * enter dL/dw_K = |K| sum_ab G^_ab g_a . g_b and
+ * dL/dq^c = w_K |K| [t g_c - sum_x g_x ((G^ + G^T) Gamma)_xc], t = sum_ab G^_ab
+ * Gamma_ab, Gamma_ab = g_a . g_b. Same scratch rules as fe_assemble_stiff_backward.
+ */
+int fe_assemble_stiff_vjp(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
+                          const void* grad_vals, void* dL_dw, void* dL_dq, int32_t prec,
+                          void* stream);
 
 /*
  * Per-kernel timing. fe_profile(h, 1) makes every later kernel launch of h be

@@ -13,6 +13,8 @@ int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_ki
                    int mu_kind, int prec, void* vals, cudaStream_t s);
 int fe_launch_backward(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* u,
                        const void* v, void* L, void* dLdw, void* dLdq, int prec, cudaStream_t s);
+int fe_launch_vjp(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* grad_vals,
+                  void* dLdw, void* dLdq, int prec, cudaStream_t s);
 
 namespace {
 char g_last_cuda_error[256] = "";
@@ -40,7 +42,8 @@ void fe_free_all(fe_pattern_s* h) {
                   h->le_off,  h->inc_v,    h->inc_e,     h->lv_dst,    h->lv_vid,
                   h->le_dst,  h->sh_ptr,   h->sh_dst,    h->partials,  h->kg,
                   h->qsplit,  h->status, h->rec, h->rec_off16,
-                  h->lv_str,  h->le_str,   h->sh_str};
+                  h->lv_str,  h->le_str,   h->sh_str,    h->vmap_ptr,  h->vmap,
+                  h->bwd_scratch, h->bwd_lpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->m > 1) {
@@ -248,6 +251,17 @@ int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, i
     return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
   return fe_launch_backward(h, q, w, w_kind, u, v, L, dL_dw, dL_dq, prec, (cudaStream_t)stream);
+}
+
+int fe_assemble_stiff_vjp(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
+                          const void* grad_vals, void* dL_dw, void* dL_dq, int32_t prec, void* stream) {
+  if (!h || !q || !grad_vals) return FE_ERR_ARG;
+  if (prec != FE_F64 && prec != FE_F32) return FE_ERR_ARG;
+  if (h->m != 1) return FE_ERR_ARG;
+  if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL)
+    return FE_ERR_ARG;
+  if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
+  return fe_launch_vjp(h, q, w, w_kind, grad_vals, dL_dw, dL_dq, prec, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -1,6 +1,241 @@
-// Stiffness backward (placeholder until the kernels land).
-#include "fe_internal.cuh"
-int fe_launch_backward(fe_pattern_s*, const double*, const void*, int, const void*, const void*,
-                       void*, void*, void*, int, cudaStream_t) {
-  return FE_ERR_ARG;
+// Backward pass of the stiffness assembly (the paper has no derivatives; the
+// formulas follow from Eq. stiffelemmat and the geometry of App. C.1).
+//
+// For one element with per-element coefficient w, local stiffness
+// S_ab = w |K| g_a . g_b and a weight matrix G^ (G^_ab multiplies S_ab in the loss):
+//   L_e       = w |K| t,                     t = sum_ab G^_ab g_a . g_b
+//   dL/dw_e   = |K| t
+//   dL/dq^c   = w |K| [ t g_c - sum_x g_x (G^s Gamma)_xc ],  G^s = G^ + G^T,
+//               Gamma_ab = g_a . g_b,
+// the derivative of |det B| / d! and of g_a = B^{-T} g^_a with respect to the
+// columns q^i - q^0 of B (the vertex-0 column is minus the sum of the others, which
+// the same formula gives because sum_a g_a = 0). With cofactor vectors c_a = det B g_a
+// everything is a polynomial in c scaled by 1/(d! |det B|) (and a sign for dq).
+// Two sources of G^:
+//   rank one, G^_ab = u(me(a)) v(me(b)):  L = u^T S(w) v without forming any matrix;
+//   general, G^_ab = dL/dS at the nonzero of slot (a, b) (a vector-Jacobian product
+//   for any loss of the assembled values).
+// Pass 1 (one thread per element) writes dL/dw and each corner's contribution to
+// dL/dq; pass 2 (one thread per vertex) sums the contributions of its incidences in
+// ascending element order, so the result is bit-identical run to run.
+#include "assemble_impl.cuh"
+#include "profile.cuh"
+
+namespace fe {
+namespace {
+
+constexpr int BWD_THREADS = 256;
+
+struct BwdArgs {
+  const int32_t* me;
+  int64_t nme, nq;
+  const double* q;
+  const float4* qs;
+  const void* w;
+  int w_kind;
+  const int32_t* order;
+  const void* u;          // rank one
+  const void* v;
+  const void* grad_vals;  // general
+  const int32_t* slot2nnz;
+  void* dLdw;             // may be null
+  bool dLdw_internal;     // index dLdw by internal element (else input order)
+  void* corner;           // nme * (d+1) * d contributions
+  void* lpart;            // per-block L partial sums (rank one), may be null
+  fe_status_word* st;
+};
+
+template <int D, class T, bool RANK1>
+__global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem(BwdArgs A) {
+  constexpr int NV = D + 1;
+  __shared__ T red[BWD_THREADS];
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  T Le = T(0);
+  if (e < A.nme) {
+    int32_t vv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) vv[a] = __ldg(A.me + (int64_t)a * A.nme + e);
+    Geo<D, T> g;
+    if constexpr (sizeof(T) == 8) {
+      double x[NV][D];
+      load_x64<D>(A.q, A.nq, vv, x);
+      geo_f64<D>(x, g);
+    } else {
+      float xh[NV][D], xl[NV][D];
+      load_x32<D>(A.qs, vv, xh, xl);
+      geo_f32<D>(xh, xl, g);
+    }
+    if (!det_ok(g.det)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e]);
+      g.det = T(1);
+    }
+    form_c0<D, T>(g);
+    T Gh[NV][NV];
+    if constexpr (RANK1) {
+      const T* u = (const T*)A.u;
+      const T* v = (const T*)A.v;
+      T uu[NV], vw[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) { uu[a] = u[vv[a]]; vw[a] = v[vv[a]]; }
+#pragma unroll
+      for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int b = 0; b < NV; ++b) Gh[a][b] = uu[a] * vw[b];
+    } else {
+      const T* gv = (const T*)A.grad_vals;
+      const int32_t* m = A.slot2nnz + e * NV * NV;
+#pragma unroll
+      for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int b = 0; b < NV; ++b) Gh[a][b] = gv[m[b * NV + a]];
+    }
+    T Gam[NV][NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int b = a; b < NV; ++b) {
+        T s = g.c[a][0] * g.c[b][0];
+#pragma unroll
+        for (int k = 1; k < D; ++k) s += g.c[a][k] * g.c[b][k];
+        Gam[a][b] = s;
+        Gam[b][a] = s;
+      }
+    T t = T(0);
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int b = 0; b < NV; ++b) t += Gh[a][b] * Gam[a][b];
+    const T adet = tabs(g.det);
+    const T inv = recip<T>(T(factorial(D)) * adet);   // |K| / det^2 = 1 / (d! |det|)
+    const bool has_w = A.w_kind != FE_COEF_NONE;
+    const T w = has_w ? elem_coef<T>(A.w, A.w_kind, A.order, e) : T(1);
+    const T dw = t * inv;
+    if (A.dLdw) ((T*)A.dLdw)[A.dLdw_internal ? e : A.order[e]] = dw;
+    Le = w * dw;
+    const T s = w * inv * recip<T>(g.det);            // w |K| / det^3 = w / (d! det |det|)
+    T* out = (T*)A.corner + e * NV * D;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      // M_xc = sum_y (G^_xy + G^_yx) Gamma_yc
+      T Mx[NV];
+#pragma unroll
+      for (int x = 0; x < NV; ++x) {
+        T m = (Gh[x][0] + Gh[0][x]) * Gam[0][c];
+#pragma unroll
+        for (int y = 1; y < NV; ++y) m += (Gh[x][y] + Gh[y][x]) * Gam[y][c];
+        Mx[x] = m;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        T acc = t * g.c[c][k];
+#pragma unroll
+        for (int x = 0; x < NV; ++x) acc -= g.c[x][k] * Mx[x];
+        out[c * D + k] = s * acc;
+      }
+    }
+  }
+  if (A.lpart) {  // fixed-order block reduction of L
+    red[threadIdx.x] = Le;
+    __syncthreads();
+    for (int o = BWD_THREADS / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) ((T*)A.lpart)[blockIdx.x] = red[0];
+  }
+}
+
+// dL/dq of each vertex: its corner contributions in ascending element order
+template <int D, class T>
+__global__ void k_bwd_vertex(const int32_t* __restrict__ ptr, const int32_t* __restrict__ inc,
+                             int64_t nq, const T* __restrict__ corner, T* __restrict__ dLdq) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= nq) return;
+  const int32_t s = ptr[v], t = ptr[v + 1];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    T acc = T(0);
+    if (s < t) {
+      Acc<T> a(corner[(int64_t)inc[s] * D + k]);
+      for (int32_t j = s + 1; j < t; ++j) a.add(corner[(int64_t)inc[j] * D + k]);
+      acc = a.value();
+    }
+    dLdq[k * nq + v] = acc;
+  }
+}
+
+// L = sum of the block partials, in block order (one block)
+template <class T>
+__global__ void k_bwd_lsum(const T* __restrict__ part, int64_t n, T* __restrict__ L) {
+  __shared__ T red[256];
+  T s = T(0);
+  for (int64_t i = threadIdx.x; i < n; i += 256) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *L = red[0];
+}
+
+template <int D, class T>
+int launch(fe_pattern_s* h, BwdArgs& A, bool rank1, void* L, void* dLdq, cudaStream_t s) {
+  const int nblk = fe_grid(h->nme, BWD_THREADS);
+  FE_PROF_BEGIN(h, FE_K_BWD_CHUNK, s);
+  if (rank1) k_bwd_elem<D, T, true><<<nblk, BWD_THREADS, 0, s>>>(A);
+  else k_bwd_elem<D, T, false><<<nblk, BWD_THREADS, 0, s>>>(A);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_PROF_END(h, FE_K_BWD_CHUNK, s);
+  if (dLdq) {
+    FE_PROF_BEGIN(h, FE_K_BWD_REDUCE, s);
+    k_bwd_vertex<D, T><<<fe_grid(h->nq, 256), 256, 0, s>>>(h->vmap_ptr, h->vmap, h->nq, (const T*)A.corner,
+                                                          (T*)dLdq);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_PROF_END(h, FE_K_BWD_REDUCE, s);
+  }
+  if (L && A.lpart) {
+    k_bwd_lsum<T><<<1, 256, 0, s>>>((const T*)A.lpart, nblk, (T*)L);
+    FE_CUDA_TRY(cudaGetLastError());
+  }
+  return FE_OK;
+}
+
+int prepare(fe_pattern_s* h, cudaStream_t s) {
+  if (!h->vmap_ptr) FE_TRY(fe_build_vertex_map(h, s));
+  if (!h->bwd_scratch) {
+    FE_TRY(fe_malloc(h, &h->bwd_scratch, sizeof(double) * (size_t)h->nme * h->nv * h->d));
+    FE_TRY(fe_malloc(h, &h->bwd_lpart, sizeof(double) * (size_t)fe_grid(h->nme, BWD_THREADS)));
+  }
+  return FE_OK;
+}
+
+int run(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* u, const void* v,
+        const void* grad_vals, void* L, void* dLdw, void* dLdq, int prec, cudaStream_t s) {
+  FE_TRY(prepare(h, s));
+  BwdArgs A{h->me_int, h->nme, h->nq, q, nullptr, w, w_kind, h->order, u, v, grad_vals, h->slot2nnz,
+            dLdw, w_kind == FE_COEF_P0_INTERNAL, h->bwd_scratch, L ? h->bwd_lpart : nullptr, h->status};
+  const bool rank1 = grad_vals == nullptr;
+  if (prec == FE_F32) {
+    float4* qs = (float4*)h->qsplit;
+    if (h->d == 3) k_split_q<3><<<fe_grid(h->nq, 256), 256, 0, s>>>(q, h->nq, qs);
+    else k_split_q<2><<<fe_grid(h->nq, 256), 256, 0, s>>>(q, h->nq, qs);
+    FE_CUDA_TRY(cudaGetLastError());
+    A.qs = qs;
+    return h->d == 3 ? launch<3, float>(h, A, rank1, L, dLdq, s) : launch<2, float>(h, A, rank1, L, dLdq, s);
+  }
+  return h->d == 3 ? launch<3, double>(h, A, rank1, L, dLdq, s) : launch<2, double>(h, A, rank1, L, dLdq, s);
+}
+
+}  // namespace
+}  // namespace fe
+
+int fe_launch_backward(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* u,
+                       const void* v, void* L, void* dLdw, void* dLdq, int prec, cudaStream_t s) {
+  return fe::run(h, q, w, w_kind, u, v, nullptr, L, dLdw, dLdq, prec, s);
+}
+
+int fe_launch_vjp(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* grad_vals,
+                  void* dLdw, void* dLdq, int prec, cudaStream_t s) {
+  return fe::run(h, q, w, w_kind, nullptr, nullptr, grad_vals, nullptr, dLdw, dLdq, prec, s);
 }

@@ -76,7 +76,11 @@ struct fe_pattern_s {
   void* partials = nullptr; size_t partials_bytes = 0;
   void* kg = nullptr; size_t kg_bytes = 0;
   void* qsplit = nullptr; size_t qsplit_bytes = 0;
-  int32_t* elas_dst = nullptr;      // vector problems: expanded destinations (see elas.cu)
+  int32_t* elas_dst = nullptr;      // unused (kept zero)
+  int32_t* vmap_ptr = nullptr;      // nq + 1: vertex -> incidences (backward pass, built on first use)
+  int32_t* vmap = nullptr;          // nv nme: e * nv + a, ascending e within each vertex
+  void* bwd_scratch = nullptr;      // backward: per-corner gradient contributions
+  void* bwd_lpart = nullptr;        // backward: per-block partial sums of L
   fe_status_word* status = nullptr;
   fe_prof_state* prof = nullptr;    // per-kernel event timing (fe_profile)
   int64_t bytes = 0;
@@ -105,6 +109,7 @@ void fe_free_all(fe_pattern_s* h);
 
 // ---------------------------------------------------------------- assemble.cu
 int fe_ensure_scratch(fe_pattern_s* h, int strategy);
+int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s);
 
 static inline int fe_grid(int64_t work, int per_block, int max_blocks = 1 << 30) {
   int64_t g = (work + per_block - 1) / per_block;

@@ -596,7 +596,53 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
   return FE_OK;
 }
 
+__global__ void k_vmap_keys(const int32_t* me_int, int64_t nme, int nv, uint64_t* keys, uint32_t* vals) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nme * nv) return;
+  const int64_t e = i / nv;
+  const int a = (int)(i - e * nv);
+  keys[i] = (uint64_t)me_int[(int64_t)a * nme + e];
+  vals[i] = (uint32_t)i;  // e * nv + a
+}
+
+__global__ void k_vmap_ptr(const uint64_t* keys, int64_t n, int64_t nq, int32_t* ptr) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t v = (int64_t)keys[i];
+  const int64_t vprev = (i == 0) ? -1 : (int64_t)keys[i - 1];
+  for (int64_t r = vprev + 1; r <= v; ++r) ptr[r] = (int32_t)i;
+  if (i == n - 1)
+    for (int64_t r = v + 1; r <= nq; ++r) ptr[r] = (int32_t)n;
+}
+
 }  // namespace
+
+// Vertex -> (element, corner) incidence lists, ascending element order within each
+// vertex (a stable sort of the corners by vertex). Built on first use.
+int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s) {
+  if (h->vmap_ptr) return FE_OK;
+  const int64_t n = h->nme * h->nv;
+  dev_tmp tmp;
+  fe_sort_buffers sb;
+  FE_TRY(tmp.get(&sb.k0, n));
+  FE_TRY(tmp.get(&sb.k1, n));
+  FE_TRY(tmp.get(&sb.v0, n));
+  FE_TRY(tmp.get(&sb.v1, n));
+  FE_TRY(tmp.get(&sb.hist, fe_sort_hist_size(n)));
+  FE_TRY(tmp.get(&sb.scan_tmp, fe_scan_tmp_size((int64_t)fe_sort_hist_size(n)) + 1));
+  const int T = 256;
+  k_vmap_keys<<<fe_grid(n, T), T, 0, s>>>(h->me_int, h->nme, h->nv, sb.k0, sb.v0);
+  FE_CUDA_TRY(cudaGetLastError());
+  uint64_t* keys; uint32_t* vals;
+  FE_TRY(fe_radix_sort(n, bitlen((uint64_t)(h->nq > 1 ? h->nq - 1 : 1)), &sb, &keys, &vals, s));
+  FE_TRY(fe_malloc(h, (void**)&h->vmap_ptr, sizeof(int32_t) * (h->nq + 1)));
+  FE_TRY(fe_malloc(h, (void**)&h->vmap, sizeof(int32_t) * n));
+  k_vmap_ptr<<<fe_grid(n, T), T, 0, s>>>(keys, n, h->nq, h->vmap_ptr);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_CUDA_TRY(cudaMemcpyAsync(h->vmap, vals, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  FE_CUDA_TRY(cudaStreamSynchronize(s));
+  return FE_OK;
+}
 
 extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
                           fe_pattern_h* out) {

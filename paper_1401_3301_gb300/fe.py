@@ -54,6 +54,7 @@ def lib() -> C.CDLL:
         L.fe_assemble_elas.argtypes = [P, P, P, I32, P, I32, I32, P, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
+        L.fe_assemble_stiff_vjp.argtypes = [P, P, P, I32, P, P, P, I32, P]
         L.fe_profile.argtypes = [P, I32]
         L.fe_profile_read.argtypes = [P, I32, P, P, P, P]
         L.fe_version.restype = C.c_char_p
@@ -62,7 +63,8 @@ def lib() -> C.CDLL:
                      "fe_pattern_set_strategy", "fe_pattern_memory", "fe_pattern_plan_info",
                      "fe_pattern_destroy", "fe_status", "fe_assemble_mass", "fe_assemble_wmass",
                      "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward",
-                     "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc"):
+                     "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
+                     "fe_assemble_stiff_vjp"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -248,6 +250,15 @@ def fe_assemble_stiff_backward(p: Pattern, q: torch.Tensor, w, w_kind: int, u: t
         p.handle, _dev(q, torch.float64, "q"), _dev(w, T, "w"), w_kind, _dev(u, T, "u"), _dev(v, T, "v"),
         _dev(L, T, "L"), _dev(dL_dw, T, "dL_dw"), _dev(dL_dq, T, "dL_dq"), prec, _stream(stream)))
     return L, dL_dw, dL_dq
+
+
+def fe_assemble_stiff_vjp(p: Pattern, q: torch.Tensor, w, w_kind: int, grad_vals: torch.Tensor,
+                          dL_dw=None, dL_dq=None, prec: int = F64, stream=None):
+    T = _vtype(prec)
+    _check(lib().fe_assemble_stiff_vjp(
+        p.handle, _dev(q, torch.float64, "q"), _dev(w, T, "w"), w_kind, _dev(grad_vals, T, "grad_vals"),
+        _dev(dL_dw, T, "dL_dw"), _dev(dL_dq, T, "dL_dq"), prec, _stream(stream)))
+    return dL_dw, dL_dq
 
 
 def fe_assemble_stiff_noalloc(p: Pattern, q: torch.Tensor, vals: torch.Tensor, w=None,
