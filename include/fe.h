@@ -71,6 +71,9 @@ extern "C" {
 /* ---- pattern flags */
 #define FE_PATTERN_KEEP_ORDER 1 /* do not reorder elements internally (default:
                                    Morton order of element centroids) */
+/* elements per chunk of the chunked reassembly, 32..4096 (0: the default, 512 in
+   3D and 1024 in 2D for scalar problems, 256 / 512 for elasticity) */
+#define FE_PATTERN_CHUNK(c) ((int32_t)(c) << 8)
 
 typedef struct fe_mesh {
   int32_t d;          /* 2 or 3 */
@@ -101,6 +104,30 @@ typedef struct fe_pattern_s* fe_pattern_h;
  * slots, nonzeros or rows), FE_ERR_NOMEM, FE_ERR_CUDA.
  */
 int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out);
+
+/*
+ * fe_batch_pattern -- one pattern for `count` meshes at once (host array of
+ * descriptors, all of dimension d): the disjoint union of the meshes, with the
+ * vertices of mesh b numbered after those of meshes 0..b-1 and its elements after
+ * theirs. The global matrix is block diagonal and the CSR rows of mesh b form one
+ * contiguous range (fe_batch_offsets), so every assembly call covers all meshes in
+ * one launch. Coordinates for the assembly calls are the union array (d x total
+ * vertices, SoA), which fe_batch_gather_q fills from the per-mesh arrays;
+ * per-element coefficients are in the concatenated element order. Synchronous.
+ */
+int fe_batch_pattern(const fe_mesh* meshes, int32_t count, int32_t m, int32_t flags, void* stream,
+                     fe_pattern_h* out);
+
+/* Host arrays of count+1 offsets of a batch pattern: first vertex, first element and
+ * first nonzero of each mesh (the last entry is the total). Any pointer may be NULL. */
+int fe_batch_offsets(fe_pattern_h h, int64_t* vert_off, int64_t* elem_off, int64_t* nnz_off);
+
+/* Number of meshes of a batch pattern (0 for a single-mesh pattern). */
+int fe_batch_count(fe_pattern_h h, int32_t* count);
+
+/* Copy the coordinates of the batch's meshes into the union array q_union
+ * (d x total vertices), stream-ordered (one device copy per mesh and coordinate). */
+int fe_batch_gather_q(fe_pattern_h h, const fe_mesh* meshes, double* q_union, void* stream);
 
 /* Borrowed CSR arrays (int32, device): row_ptr[n+1], col_idx[nnz]. */
 int fe_pattern_csr(fe_pattern_h h, int64_t* n, int64_t* nnz, const int32_t** row_ptr,

@@ -313,7 +313,8 @@ int launch(fe_pattern_s* h, const ElasArgs& A, T* vals, cudaStream_t s) {
   const ElasSmem L = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   auto kern = k_chunk_elas<D, T, THREADS>;
-  FE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  static size_t configured = 0;
+  FE_TRY(fe_smem_limit(kern, L.total, configured));
   FE_PROF_BEGIN(h, FE_K_ELAS_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, h->partials);
   FE_CUDA_TRY(cudaGetLastError());

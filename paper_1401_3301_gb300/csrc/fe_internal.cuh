@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/fe.h"
 
 #define FE_CUDA_TRY(expr)                                   \
@@ -83,6 +85,7 @@ struct fe_pattern_s {
   void* bwd_lpart = nullptr;        // backward: per-block partial sums of L
   fe_status_word* status = nullptr;
   fe_prof_state* prof = nullptr;    // per-kernel event timing (fe_profile)
+  std::vector<int64_t> batch_voff, batch_eoff, batch_noff;  // batches: per-mesh offsets
   int64_t bytes = 0;
 };
 
@@ -110,6 +113,17 @@ void fe_free_all(fe_pattern_s* h);
 // ---------------------------------------------------------------- assemble.cu
 int fe_ensure_scratch(fe_pattern_s* h, int strategy);
 int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s);
+
+// Raise a kernel's dynamic shared-memory limit once (not again inside a stream
+// capture): one static high-water mark per kernel instantiation.
+template <class K>
+int fe_smem_limit(K kernel, size_t bytes, size_t& configured) {
+  if (bytes <= configured) return FE_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return fe_cuda_fail(e);
+  configured = bytes;
+  return FE_OK;
+}
 
 static inline int fe_grid(int64_t work, int per_block, int max_blocks = 1 << 30) {
   int64_t g = (work + per_block - 1) / per_block;

@@ -419,7 +419,9 @@ int to_host(T* dst, const T* src, cudaStream_t s) {
   return FE_OK;
 }
 
-int default_chunk(int d, int m) {
+int default_chunk(int d, int m, int flags) {
+  const int fc = (flags >> 8) & 0xFFFF;
+  if (fc >= 32 && fc <= 4096) return fc;
   const char* env = getenv("FE_CHUNK");
   if (env) {
     const int c = atoi(env);
@@ -617,6 +619,16 @@ __global__ void k_vmap_ptr(const uint64_t* keys, int64_t n, int64_t nq, int32_t*
 
 }  // namespace
 
+namespace {
+__global__ void k_union_me(const int32_t* me, int64_t nme, int nv, int64_t voff, int64_t eoff,
+                           int64_t nme_total, int32_t* me_u) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nme) return;
+  for (int a = 0; a < nv; ++a)
+    me_u[(int64_t)a * nme_total + eoff + k] = me[(int64_t)a * nme + k] + (int32_t)voff;
+}
+}  // namespace
+
 // Vertex -> (element, corner) incidence lists, ascending element order within each
 // vertex (a stable sort of the corners by vertex). Built on first use.
 int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s) {
@@ -644,6 +656,82 @@ int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s) {
   return FE_OK;
 }
 
+extern "C" int fe_batch_pattern(const fe_mesh* meshes, int32_t count, int32_t m, int32_t flags,
+                                void* stream, fe_pattern_h* out) {
+  if (!meshes || !out || count < 1) return FE_ERR_ARG;
+  *out = nullptr;
+  const int d = meshes[0].d;
+  std::vector<int64_t> voff(count + 1, 0), eoff(count + 1, 0);
+  for (int b = 0; b < count; ++b) {
+    const fe_mesh& mb = meshes[b];
+    if (mb.d != d || mb.nq < 1 || mb.nme < 1 || !mb.q || !mb.me) return FE_ERR_ARG;
+    voff[b + 1] = voff[b] + mb.nq;
+    eoff[b + 1] = eoff[b] + mb.nme;
+  }
+  if (voff[count] > INT32_MAX) return FE_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nv = d + 1;
+  dev_tmp tmp;
+  double* qu;
+  int32_t* meu;
+  FE_TRY(tmp.get(&qu, (size_t)d * voff[count]));
+  FE_TRY(tmp.get(&meu, (size_t)nv * eoff[count]));
+  for (int b = 0; b < count; ++b) {
+    const fe_mesh& mb = meshes[b];
+    for (int c = 0; c < d; ++c)
+      FE_CUDA_TRY(cudaMemcpyAsync(qu + c * voff[count] + voff[b], mb.q + c * mb.nq,
+                                  sizeof(double) * mb.nq, cudaMemcpyDeviceToDevice, s));
+    k_union_me<<<fe_grid(mb.nme, 256), 256, 0, s>>>(mb.me, mb.nme, nv, voff[b], eoff[b], eoff[count], meu);
+    FE_CUDA_TRY(cudaGetLastError());
+  }
+  fe_mesh u{d, voff[count], eoff[count], qu, meu};
+  FE_TRY(fe_pattern(&u, m, flags, stream, out));
+  fe_pattern_s* h = *out;
+  h->batch_voff = voff;
+  h->batch_eoff = eoff;
+  // nonzero offsets: row_ptr at the first row of every mesh
+  h->batch_noff.assign(count + 1, 0);
+  for (int b = 0; b <= count; ++b) {
+    int32_t r = 0;
+    FE_CUDA_TRY(cudaMemcpyAsync(&r, h->row_ptr + (int64_t)m * voff[b], sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, s));
+    FE_CUDA_TRY(cudaStreamSynchronize(s));
+    h->batch_noff[b] = r;
+  }
+  return FE_OK;
+}
+
+extern "C" int fe_batch_offsets(fe_pattern_h h, int64_t* vert_off, int64_t* elem_off, int64_t* nnz_off) {
+  if (!h || h->batch_voff.empty()) return FE_ERR_ARG;
+  const size_t n = h->batch_voff.size();
+  for (size_t b = 0; b < n; ++b) {
+    if (vert_off) vert_off[b] = h->batch_voff[b];
+    if (elem_off) elem_off[b] = h->batch_eoff[b];
+    if (nnz_off) nnz_off[b] = h->batch_noff[b];
+  }
+  return FE_OK;
+}
+
+extern "C" int fe_batch_count(fe_pattern_h h, int32_t* count) {
+  if (!h || !count) return FE_ERR_ARG;
+  *count = h->batch_voff.empty() ? 0 : (int32_t)h->batch_voff.size() - 1;
+  return FE_OK;
+}
+
+extern "C" int fe_batch_gather_q(fe_pattern_h h, const fe_mesh* meshes, double* q_union, void* stream) {
+  if (!h || !meshes || !q_union || h->batch_voff.empty()) return FE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int count = (int)h->batch_voff.size() - 1;
+  const int64_t nq = h->nq;
+  for (int b = 0; b < count; ++b) {
+    if (meshes[b].nq != h->batch_voff[b + 1] - h->batch_voff[b] || !meshes[b].q) return FE_ERR_ARG;
+    for (int c = 0; c < h->d; ++c)
+      FE_CUDA_TRY(cudaMemcpyAsync(q_union + c * nq + h->batch_voff[b], meshes[b].q + c * meshes[b].nq,
+                                  sizeof(double) * meshes[b].nq, cudaMemcpyDeviceToDevice, s));
+  }
+  return FE_OK;
+}
+
 extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
                           fe_pattern_h* out) {
   if (!mesh || !out) return FE_ERR_ARG;
@@ -659,7 +747,7 @@ extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* s
   fe_pattern_s* h = new fe_pattern_s();
   h->d = d; h->m = m; h->nv = nv; h->npair = nv * d / 2; h->flags = flags;
   h->nq = nq; h->nme = nme; h->n = (int64_t)m * nq;
-  h->chunk = default_chunk(d, m);
+  h->chunk = default_chunk(d, m, flags);
   int rc = FE_OK;
   dev_tmp tmp;
   do {

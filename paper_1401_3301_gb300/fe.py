@@ -17,6 +17,11 @@ F64, F32 = 0, 1
 COEF_NONE, COEF_SCALAR, COEF_P0, COEF_P1, COEF_P0_INTERNAL = 0, 1, 2, 3, 4
 REASM_CHUNKED, REASM_GATHER, REASM_ATOMIC = 0, 1, 2
 PATTERN_KEEP_ORDER = 1
+
+
+def PATTERN_CHUNK(c: int) -> int:
+    """Pattern flag: elements per chunk of the chunked reassembly (32..4096)."""
+    return int(c) << 8
 ERRORS = {1: "FE_ERR_ARG", 2: "FE_ERR_INDEX", 3: "FE_ERR_DEGENERATE", 4: "FE_ERR_OVERFLOW",
           5: "FE_ERR_CUDA", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NOMEM", 8: "FE_ERR_SCRATCH_LIMIT"}
 
@@ -55,6 +60,10 @@ def lib() -> C.CDLL:
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff_vjp.argtypes = [P, P, P, I32, P, P, P, I32, P]
+        L.fe_batch_pattern.argtypes = [P, I32, I32, I32, P, P]
+        L.fe_batch_offsets.argtypes = [P, P, P, P]
+        L.fe_batch_count.argtypes = [P, P]
+        L.fe_batch_gather_q.argtypes = [P, P, P, P]
         L.fe_profile.argtypes = [P, I32]
         L.fe_profile_read.argtypes = [P, I32, P, P, P, P]
         L.fe_version.restype = C.c_char_p
@@ -64,7 +73,8 @@ def lib() -> C.CDLL:
                      "fe_pattern_destroy", "fe_status", "fe_assemble_mass", "fe_assemble_wmass",
                      "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward",
                      "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
-                     "fe_assemble_stiff_vjp"):
+                     "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
+                     "fe_batch_count", "fe_batch_gather_q"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -200,6 +210,44 @@ def fe_pattern(q: torch.Tensor, me: torch.Tensor, m: int = 1, flags: int = 0, st
     h = C.c_void_p()
     _check(lib().fe_pattern(C.byref(mesh), m, flags, _stream(stream), C.byref(h)))
     return Pattern(h)
+
+
+def _meshes(qs, mes):
+    arr = (_Mesh * len(qs))()
+    for b, (q, me) in enumerate(zip(qs, mes)):
+        if me.shape[0] != q.shape[0] + 1:
+            raise ValueError("me must be (d+1, nme)")
+        arr[b] = _Mesh(q.shape[0], q.shape[1], me.shape[1], _dev(q, torch.float64, "q").value,
+                       _dev(me, torch.int32, "me").value)
+    return arr
+
+
+def fe_batch_pattern(qs: list, mes: list, m: int = 1, flags: int = 0, stream=None) -> Pattern:
+    """Pattern of the disjoint union of several meshes (see include/fe.h)."""
+    arr = _meshes(qs, mes)
+    h = C.c_void_p()
+    _check(lib().fe_batch_pattern(arr, len(qs), m, flags, _stream(stream), C.byref(h)))
+    p = Pattern(h)
+    p._batch_keep = (qs, mes)
+    return p
+
+
+def fe_batch_offsets(p: Pattern):
+    """(vertex, element, nonzero) offsets of the meshes of a batch pattern, numpy int64."""
+    import numpy as np
+    cnt = C.c_int32()
+    _check(lib().fe_batch_count(p.handle, C.byref(cnt)))
+    n = cnt.value + 1
+    vo, eo, no = (np.zeros(n, dtype=np.int64) for _ in range(3))
+    _check(lib().fe_batch_offsets(p.handle, vo.ctypes.data_as(C.c_void_p), eo.ctypes.data_as(C.c_void_p),
+                                  no.ctypes.data_as(C.c_void_p)))
+    return vo, eo, no
+
+
+def fe_batch_gather_q(p: Pattern, qs: list, mes: list, q_union: torch.Tensor, stream=None):
+    arr = _meshes(qs, mes)
+    _check(lib().fe_batch_gather_q(p.handle, arr, _dev(q_union, torch.float64, "q_union"), _stream(stream)))
+    return q_union
 
 
 def _out(p: Pattern, vals, prec):
