@@ -165,6 +165,10 @@ int fe_pattern_element_order(fe_pattern_h h, const int32_t** order);
  * assembly call. */
 int fe_pattern_set_strategy(fe_pattern_h h, int32_t strategy);
 
+/* Threads per block of the chunked kernel of the scalar operators: 128, 256
+ * (default) or 512. Set by the autotuner (paper_1401_3301_gb300/tune.py). */
+int fe_pattern_set_threads(fe_pattern_h h, int32_t threads);
+
 /* Device bytes held by the handle (pattern, plan and scratch). */
 int fe_pattern_memory(fe_pattern_h h, int64_t* bytes);
 

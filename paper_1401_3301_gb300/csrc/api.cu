@@ -151,6 +151,12 @@ int fe_pattern_set_strategy(fe_pattern_h h, int32_t strategy) {
   return FE_OK;
 }
 
+int fe_pattern_set_threads(fe_pattern_h h, int32_t threads) {
+  if (!h || (threads != 128 && threads != 256 && threads != 512)) return FE_ERR_ARG;
+  h->threads = threads;
+  return FE_OK;
+}
+
 int fe_pattern_memory(fe_pattern_h h, int64_t* bytes) {
   if (!h || !bytes) return FE_ERR_ARG;
   *bytes = h->bytes;

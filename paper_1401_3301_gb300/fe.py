@@ -61,6 +61,7 @@ def lib() -> C.CDLL:
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff_vjp.argtypes = [P, P, P, I32, P, P, P, I32, P]
         L.fe_batch_pattern.argtypes = [P, I32, I32, I32, P, P]
+        L.fe_pattern_set_threads.argtypes = [P, I32]
         L.fe_batch_offsets.argtypes = [P, P, P, P]
         L.fe_batch_count.argtypes = [P, P]
         L.fe_batch_gather_q.argtypes = [P, P, P, P]
@@ -74,7 +75,7 @@ def lib() -> C.CDLL:
                      "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward",
                      "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
-                     "fe_batch_count", "fe_batch_gather_q"):
+                     "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -159,6 +160,9 @@ class Pattern:
 
     def set_strategy(self, strategy: int):
         _check(lib().fe_pattern_set_strategy(self.handle, strategy))
+
+    def set_threads(self, threads: int):
+        _check(lib().fe_pattern_set_threads(self.handle, threads))
 
     def memory(self) -> int:
         b = C.c_int64()

@@ -1,0 +1,113 @@
+"""Autotuner of the fixed-pattern reassembly.
+
+For one mesh and operator it times the chunked kernel over a grid of chunk sizes
+(elements per block, i.e. work per thread) and threads per block, and optionally
+the two-pass gather and atomic strategies, with CUDA events (median of `reps`
+calls after one warm-up). The winner is cached in a JSON file keyed by GPU name,
+dimension, dofs per vertex, operator, precision and the element count's power of
+two, so later meshes of the same class reuse it without timing.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+import torch
+
+from . import build_ext, fe
+
+CHUNKS = (256, 384, 512, 768, 1024)
+THREADS = (128, 256, 512)
+
+
+def cache_path() -> str:
+    return os.environ.get("FE_TUNE_CACHE", os.path.join(build_ext.BUILD, "tune.json"))
+
+
+def _key(d, m, kind, prec, nme) -> str:
+    name = torch.cuda.get_device_name().replace(" ", "_")
+    return f"{name}|d{d}|m{m}|{kind}|{'f64' if prec == fe.F64 else 'f32'}|2^{int(math.log2(max(nme, 1)))}"
+
+
+def _call(p, q, kind, prec, w, w_kind, vals):
+    if kind == "stiff":
+        return fe.fe_assemble_stiff(p, q, w, w_kind, prec=prec, vals=vals)
+    if kind == "mass":
+        return fe.fe_assemble_mass(p, q, prec=prec, vals=vals)
+    if kind == "wmass":
+        return fe.fe_assemble_wmass(p, q, w, w_kind, prec=prec, vals=vals)
+    raise ValueError(f"unknown operator {kind}")
+
+
+def _time(fn, reps: int) -> float:
+    fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int = fe.F64, w=None,
+             w_kind: int | None = None, reps: int = 10, chunks=CHUNKS, threads=THREADS,
+             deterministic_only: bool = True, use_cache: bool = True) -> dict:
+    """Best {strategy, chunk, threads, ms} for this mesh class, from the cache or by timing."""
+    if w_kind is None:
+        w_kind = fe.COEF_NONE if w is None else fe.COEF_P0
+    d, nme = q.shape[0], me.shape[1]
+    key = _key(d, 1, kind, prec, nme)
+    path = cache_path()
+    cache = _load(path)
+    if use_cache and key in cache:
+        return cache[key]
+    T = torch.float64 if prec == fe.F64 else torch.float32
+    results = []
+    vals = None
+    for c in chunks:
+        p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(c))
+        if vals is None:
+            vals = torch.empty(p.nnz, dtype=T, device=q.device)
+        for t in threads:
+            p.set_threads(t)
+            ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals), reps)
+            results.append({"strategy": "chunked", "chunk": c, "threads": t, "ms": ms})
+        p.destroy()
+    if not deterministic_only:
+        p = fe.fe_pattern(q, me)
+        for name, s in (("gather", fe.REASM_GATHER), ("atomic", fe.REASM_ATOMIC)):
+            p.set_strategy(s)
+            ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals), reps)
+            results.append({"strategy": name, "chunk": 0, "threads": 256, "ms": ms})
+        p.destroy()
+    best = dict(min(results, key=lambda r: r["ms"]))
+    best["tried"] = len(results)
+    cache = _load(path)
+    cache[key] = best
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return best
+
+
+def tuned_pattern(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int = fe.F64, **kw) -> fe.Pattern:
+    """A pattern built and configured with the autotuned chunk size, threads and strategy."""
+    best = autotune(q, me, kind=kind, prec=prec, **kw)
+    strategy = {"chunked": fe.REASM_CHUNKED, "gather": fe.REASM_GATHER, "atomic": fe.REASM_ATOMIC}[best["strategy"]]
+    p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(best["chunk"]) if best["chunk"] else 0)
+    p.set_strategy(strategy)
+    p.set_threads(best["threads"])
+    return p

@@ -1,0 +1,45 @@
+"""Autotuner: times a grid of chunk sizes / threads, caches the winner, and the
+tuned pattern assembles the same matrix."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_3301_gb300 import meshgen
+from helpers import fe_or_skip, normalised_error, to_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_caches_and_tuned_pattern_is_correct(tmp_path, monkeypatch):
+    fe = fe_or_skip()
+    from paper_1401_3301_gb300 import tune
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("FE_TUNE_CACHE", str(cache))
+    m = meshgen.kuhn_cube_mesh(10, seed=31)
+    q, me = to_cuda(m.q), to_cuda(m.me)
+    best = tune.autotune(q, me, chunks=(256, 512), threads=(128, 256), reps=3, deterministic_only=False)
+    assert best["tried"] == 6 and best["ms"] > 0
+    stored = json.loads(cache.read_text())
+    assert len(stored) == 1 and list(stored.values())[0]["ms"] == best["ms"]
+    again = tune.autotune(q, me, chunks=(256, 512), threads=(128, 256), reps=3)
+    assert again == best  # served from the cache
+    p = tune.tuned_pattern(q, me, chunks=(256, 512), threads=(128, 256), reps=3)
+    ref = oracle.assemble(oracle.STIFF, m.q, m.me)
+    vals = fe.fe_assemble_stiff(p, q)
+    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
+
+
+@pytest.mark.parametrize("chunk,threads", [(256, 128), (768, 512), (1024, 256)])
+def test_chunk_and_thread_variants_agree_with_oracle(chunk, threads):
+    fe = fe_or_skip()
+    m = meshgen.kuhn_cube_mesh(9, seed=32)
+    q, me = to_cuda(m.q), to_cuda(m.me)
+    p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(chunk))
+    p.set_threads(threads)
+    assert p.plan_info()["chunk"] == chunk
+    ref = oracle.assemble(oracle.STIFF, m.q, m.me)
+    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+        vals = fe.fe_assemble_stiff(p, q, prec=prec)
+        assert normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"]) <= tol
