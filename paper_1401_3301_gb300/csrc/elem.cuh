@@ -49,6 +49,16 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   return fast_two_sum(p, e);
 }
 
+// a*b - c*d of floats as an unevaluated double-float sum: the products are exact
+// (two-product by FMA), their difference is an exact two-sum plus the product
+// errors; relative error about 2^-48 of the terms.
+__device__ __forceinline__ df diff_of_products(float a, float b, float c, float d) {
+  const float p = __fmul_rn(a, b), q = __fmul_rn(c, d);
+  const float ep = __fmaf_rn(a, b, -p), eq = __fmaf_rn(c, d, -q);
+  const df s = two_sum(p, -q);
+  return {s.hi, __fadd_rn(s.lo, __fsub_rn(ep, eq))};
+}
+
 // Exact-ish split of a double into two floats: hi = x truncated to 24 significant
 // bits, lo = the next 24 bits, so |x - hi - lo| < 2^-47 |x|. Integer operations
 // only (the FP64 and conversion pipes are slow on this part). Inputs with
@@ -70,13 +80,15 @@ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
   lo = __int_as_float(sign | ((unsigned int)eo << 23) | ((r << (lz + 1)) >> 9));
 }
 
-// compensated float accumulator (two-sum, Knuth)
+// Compensated float accumulator (Kahan's summation): the value is s + c, where c
+// carries the low-order part lost by each addition.
 struct csum {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float x) {
-    const df t = two_sum(s, x);
-    s = t.hi;
-    c = __fadd_rn(c, t.lo);
+    const float y = __fadd_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(y, __fsub_rn(t, s));
+    s = t;
   }
   __device__ __forceinline__ void add2(float xs, float xc) {
     add(xs);
@@ -164,17 +176,37 @@ __device__ __forceinline__ void geo_f32(const float xh[D + 1][D], const float xl
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int c = 0; c < D; ++c) eh[i][c] = e[i][c].hi;
+  // det B = det(eh) + sum_i el_i . c_i + O(el^2): det(eh) in double-float from exact
+  // products of the rounded edges, the low parts el against the float cofactors.
   if constexpr (D == 3) {
-    const df cx = df_add(df_mul(e[1][1], e[2][2]), df_neg(df_mul(e[1][2], e[2][1])));
-    const df cy = df_add(df_mul(e[1][2], e[2][0]), df_neg(df_mul(e[1][0], e[2][2])));
-    const df cz = df_add(df_mul(e[1][0], e[2][1]), df_neg(df_mul(e[1][1], e[2][0])));
-    const df dt = df_add(df_add(df_mul(e[0][0], cx), df_mul(e[0][1], cy)), df_mul(e[0][2], cz));
-    g.det = __fadd_rn(dt.hi, dt.lo);
     cofactors3(eh, g);
+    df cr[3];
+    cr[0] = diff_of_products(eh[1][1], eh[2][2], eh[1][2], eh[2][1]);
+    cr[1] = diff_of_products(eh[1][2], eh[2][0], eh[1][0], eh[2][2]);
+    cr[2] = diff_of_products(eh[1][0], eh[2][1], eh[1][1], eh[2][0]);
+    float p[3], lo = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      p[k] = __fmul_rn(eh[0][k], cr[k].hi);
+      lo = __fadd_rn(lo, __fmaf_rn(eh[0][k], cr[k].lo, __fmaf_rn(eh[0][k], cr[k].hi, -p[k])));
+    }
+    df s = two_sum(p[0], p[1]);
+    const df s2 = two_sum(s.hi, p[2]);
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, s2.lo));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) lo = __fmaf_rn(e[i][k].lo, g.c[i + 1][k], lo);
+    g.det = __fadd_rn(s2.hi, lo);
   } else {
-    const df dt = df_add(df_mul(e[0][0], e[1][1]), df_neg(df_mul(e[0][1], e[1][0])));
-    g.det = __fadd_rn(dt.hi, dt.lo);
     cofactors2(eh, g);
+    const df dh = diff_of_products(eh[0][0], eh[1][1], eh[0][1], eh[1][0]);
+    float lo = dh.lo;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) lo = __fmaf_rn(e[i][k].lo, g.c[i + 1][k], lo);
+    g.det = __fadd_rn(dh.hi, lo);
   }
 }
 
@@ -222,8 +254,19 @@ __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 
 template <class T>
 __device__ __forceinline__ T recip(T x);
+// FP64 reciprocal: hardware approximation refined by two Newton-Raphson steps
+// (r <- r + r (1 - x r), each step roughly doubling the correct bits); within a
+// couple of ulps of 1/x for the normal, finite x the kernels pass (checked by
+// the tests against CUDA's division).
 template <>
-__device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ double recip<double>(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 template <>
 __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 
