@@ -213,11 +213,20 @@ def chunk_algorithmic_bytes(p, prec, info):
     return reads + writes
 
 
-def fp64_instr_per_tet(info, nme):
-    """FP64-pipe instructions per tet of the FP64 chunk kernel, counted from the source:
-    edges 9 DADD, cofactors 18, det 3, 1/(6|det|) 6, Gram 18 + 6 scalings, row sums 9,
-    plus one DADD per incidence summed (4 vertex + 6 edge incidences per tet)."""
-    return 9 + 18 + 3 + 6 + 24 + 9 + 10
+def fp64_instr_per_tet():
+    """FP64-pipe instructions (DADD + DMUL + DFMA) per tet of the FP64 chunk kernel:
+    ncu-counted when the committed profile matches the current kernel sources, else
+    the count from the source (edges 9, cofactors 18, det 3, 1/(6|det|) 5, Gram 18,
+    scaling 6, row sums 8, about 8 incidence sums)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            ent = json.load(f)["f64"]
+        if ent.get("source_hash") == kernel_source_hash() and "fp64_instr_per_tet" in ent:
+            return float(ent["fp64_instr_per_tet"]), "ncu (profiles/traffic.json)"
+    except Exception:
+        pass
+    return 75.0, "from source"
 
 
 def run_gpu(args):
@@ -301,13 +310,14 @@ def run_gpu(args):
         forms[prec_name]["path_effective"]["frac"] = forms[prec_name]["path_effective"]["GBps"] / hbm_peak
         if prec == fe.F64:
             clock = sm_max
-            instr = fp64_instr_per_tet(info, p.nme) * p.nme
+            ipt, counted = fp64_instr_per_tet()
+            instr = ipt * p.nme
             peak_ops = FP64_PIPE_PER_SM_CLK * SM_COUNT * clock * 1e6 / 1e9
             forms[prec_name]["roofline_alu"] = {
                 "bound": "alu", "kernel": dom, "achieved": instr / (dom_ms * 1e-3) / 1e9,
                 "peak": peak_ops, "unit": "G FP64 instr/s",
                 "frac": instr / (dom_ms * 1e-3) / 1e9 / peak_ops,
-                "instr_per_tet": fp64_instr_per_tet(info, p.nme), "counted": "from source",
+                "instr_per_tet": ipt, "counted": counted,
                 "peak_source": f"{FP64_PIPE_PER_SM_CLK:.0f} FP64 instr/SM/clk x {SM_COUNT} SMs x {clock:.0f} MHz"}
     clocks = sampler.stop()
 
