@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--strategy", default="chunked", choices=["chunked", "gather", "atomic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
+    ap.add_argument("--workload", default="stiffness",
+                    choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff"],
+                    help="stiffness (default, the headline); the others print one JSON line each "
+                         "for the other configurations of the hot path")
     return ap.parse_args()
 
 
@@ -176,6 +180,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """Largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, steps: int, total_ms_max: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank processes its own
+    copy of the workload, so the job processes world * units per step, in the time of the
+    slowest rank."""
+    return units_per_rank * world * steps / (total_ms_max * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------------ GPU arm
 def kernel_source_hash():
     h = hashlib.sha256()
@@ -278,11 +300,7 @@ def run_gpu(args):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         step_ms = [a.elapsed_time(b) for a, b in ev]
-        total_ms = float(sum(step_ms))
-        if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(float(sum(step_ms)), world, "cuda")
         prof = p.profile_read()
         p.profile(False)
         p.check()
@@ -297,8 +315,7 @@ def run_gpu(args):
                     "algorithmic_bytes_per_launch": abytes, "kernel_ms": dom_ms,
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                     else "fallback 6.8 TB/s"}
-        tets = p.nme * world
-        value = tets * args.steps / (total_ms * 1e-3) / 1e6
+        value = replica_throughput(p.nme, world, args.steps, total_ms)
         forms[prec_name] = {"value": value, "ms_per_step": total_ms / args.steps,
                             "step_ms_median": statistics.median(step_ms), "kernels": {
                                 k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()},
@@ -371,10 +388,175 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------ other configurations
+def _timed(fn, steps, warmup, flush=None):
+    """Median and mean ms of fn over `steps` calls (CUDA events; optional L2 flush, untimed)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        if flush is not None:
+            flush.fill_(1)
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    t = [a.elapsed_time(b) for a, b in ev]
+    return statistics.median(t), sum(t) / len(t)
+
+
+def run_other(args):
+    import torch
+    from paper_1401_3301_gb300 import build_ext, fe, meshgen
+    build_ext.build()
+    fe.lib()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, W = args.steps, args.warmup
+    out = {"workload": args.workload, "data": "synthetic", "steps": K, "warmup": W, "n_gpus": 1,
+           "higher_is_better": True, "forms": {}}
+    if args.workload in ("mass", "wmass"):
+        m = meshgen.kuhn_cube_mesh(args.N, seed=0)
+        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        p = fe.fe_pattern(q, me)
+        wv = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            w = wv.to(T)
+            fn = (lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)) if args.workload == "mass" else \
+                 (lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec, vals=vals))
+            med, mean = _timed(fn, K, W, flush)
+            p.check()
+            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+        out.update(metric=f"3D P1 {'mass' if args.workload == 'mass' else 'weighted mass (P1 vertex weight)'} "
+                          "Mtets/s, fixed pattern", unit="Mtets/s",
+                   config=workload_config(args.N))
+    elif args.workload == "elas":
+        N = 80 if args.N == 100 else args.N
+        m = meshgen.kuhn_cube_mesh(N, seed=0)
+        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        t0 = time.perf_counter()
+        p = fe.fe_pattern(q, me, m=3)
+        pms = (time.perf_counter() - t0) * 1e3
+        lam0, mu0 = meshgen.lame_from_young(1.0, 0.3)
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            lam = torch.tensor([lam0], dtype=T, device="cuda")
+            mu = torch.tensor([mu0], dtype=T, device="cuda")
+            med, mean = _timed(lambda: fe.fe_assemble_elas(p, q, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR,
+                                                          prec=prec, vals=vals), K, W, flush)
+            p.check()
+            # rigid-mode residual: K r for the 6 rigid modes, relative to |K| |r|
+            rp, ci = p.csr()
+            rows = torch.repeat_interleave(torch.arange(p.n, device="cuda"), (rp[1:] - rp[:-1]).long())
+            X = q.T.double()
+            res = 0.0
+            for mode in range(6):
+                r = torch.zeros((m.nq, 3), dtype=torch.float64, device="cuda")
+                if mode < 3:
+                    r[:, mode] = 1.0
+                else:
+                    axis = torch.zeros(3, dtype=torch.float64, device="cuda")
+                    axis[mode - 3] = 1.0
+                    r = torch.linalg.cross(axis.expand_as(X), X)
+                r = r.reshape(-1)
+                y = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+                y.index_add_(0, rows, vals.double() * r[ci.long()])
+                res = max(res, float(y.abs().max() / (vals.double().abs().max() * r.abs().max())))
+            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6,
+                                  "rigid_mode_residual": res}
+        out.update(metric="3D P1 linear elasticity (12x12 element blocks) Mtets/s, fixed pattern", unit="Mtets/s",
+                   config={**workload_config(N), "E": 1.0, "nu": 0.3, "nnz": p.nnz, "pattern_build_ms": pms})
+    elif args.workload == "2d":
+        m = meshgen.square_mesh(100, seed=0)
+        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        p = fe.fe_pattern(q, me)
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            v1 = torch.empty(p.nnz, dtype=T, device="cuda")
+            v2 = torch.empty(p.nnz, dtype=T, device="cuda")
+
+            def step():
+                fe.fe_assemble_mass(p, q, prec=prec, vals=v1)
+                fe.fe_assemble_stiff(p, q, prec=prec, vals=v2)
+            step()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step()
+            med, mean = _timed(g.replay, K, W)
+            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+        out.update(metric="2D P1 mass + stiffness Mtris/s (both matrices per step, CUDA graph)", unit="Mtris/s",
+                   config={"workload": "unit square N=100, 20,000 triangles, 10,201 vertices, jitter 0.2h, "
+                                       "vertices and elements permuted", "nnz": p.nnz})
+    elif args.workload == "batched":
+        sizes = meshgen.batch_sizes(0, 256, 16, 512)
+        meshes = [meshgen.square_mesh(int(n), seed=b + 1) for b, n in enumerate(sizes)]
+        qs = [torch.from_numpy(mm.q).cuda() for mm in meshes]
+        mes = [torch.from_numpy(mm.me).cuda() for mm in meshes]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = fe.fe_batch_pattern(qs, mes)
+        pms = (time.perf_counter() - t0) * 1e3
+        vo, eo, _ = fe.fe_batch_offsets(p)
+        qu = torch.empty((2, int(vo[-1])), dtype=torch.float64, device="cuda")
+        fe.fe_batch_gather_q(p, qs, mes, qu)
+        del qs, mes
+        ntri = int(eo[-1])
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            w = torch.ones(ntri, dtype=T, device="cuda")
+            s = torch.empty(p.nnz, dtype=T, device="cuda")
+            mm_ = torch.empty(p.nnz, dtype=T, device="cuda")
+            torch.cuda.manual_seed(0)
+
+            def step():
+                w.copy_(torch.randn(w.shape, device="cuda", dtype=T).exp_())
+                fe.fe_assemble_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=s)
+                fe.fe_assemble_wmass(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=mm_)
+            step()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step()
+            med, mean = _timed(g.replay, K, W)
+            p.check()
+            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": ntri / (mean * 1e-3) / 1e6}
+        out.update(metric="Batched 2D weighted mass + stiffness reassembly with fresh lognormal weights, "
+                          "Mtris/s (CUDA graph replay)", unit="Mtris/s",
+                   config={"workload": f"256 jittered unit-square meshes, N uniform in [16, 512] "
+                                       f"({ntri:,} triangles, {int(vo[-1]):,} vertices)", "nnz": p.nnz,
+                           "pattern_build_ms": pms})
+    elif args.workload == "diff":
+        N = 64 if args.N == 100 else args.N
+        m = meshgen.kuhn_cube_mesh(N, seed=0)
+        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        p = fe.fe_pattern(q, me)
+        w64 = torch.from_numpy(meshgen.element_weights(0, m.nme)).cuda()
+        u64, v64 = (torch.from_numpy(x).cuda() for x in meshgen.random_vectors(0, m.nq))
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            w, u, v = w64.to(T), u64.to(T), v64.to(T)
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            L = torch.empty(1, dtype=T, device="cuda")
+            dw = torch.empty(m.nme, dtype=T, device="cuda")
+            dq = torch.empty((3, m.nq), dtype=T, device="cuda")
+
+            def step():
+                fe.fe_assemble_stiff(p, q, w, fe.COEF_P0, prec=prec, vals=vals)
+                fe.fe_assemble_stiff_backward(p, q, w, fe.COEF_P0, u, v, L, dw, dq, prec=prec)
+            med, mean = _timed(step, K, W, flush)
+            p.check()
+            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+        out.update(metric="3D stiffness K(w) forward + backward (L = u^T K v, dL/dw, dL/dq) Mtets/s",
+                   unit="Mtets/s", config={**workload_config(N)})
+    out["value"] = out["forms"]["f64"]["value"]
+    out["dtype"] = "f64"
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "stiffness":
+        run_other(args)
     else:
         run_gpu(args)
 

@@ -168,25 +168,6 @@ struct Acc<float> {
 };
 
 // ---------------------------------------------------------------- FE_REASM_CHUNKED
-// Shared-memory layout of the staged chunk kernel (byte offsets).
-struct StagedSmem {
-  uint32_t q, w, lvid, kd, ko, total;
-};
-__host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, bool p1_weight,
-                                                           uint32_t rec_max, uint32_t max_lv,
-                                                           uint32_t chunk) {
-  const uint32_t nv = D + 1, np = D * (D + 1) / 2;
-  StagedSmem L;
-  uint32_t o = pad16(rec_max);
-  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
-  L.w = o;    o += p1_weight ? pad16(sizeT * max_lv) : 0u;
-  L.lvid = o; o += pad16(2u * nv * chunk);
-  L.kd = o;   o += pad16(sizeT * nv * chunk);
-  L.ko = o;   o += pad16(sizeT * np * chunk);
-  L.total = o;
-  return L;
-}
-
 struct StagedArgs {
   int64_t nme, nq;
   int chunk;

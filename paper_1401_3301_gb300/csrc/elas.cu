@@ -34,23 +34,6 @@ struct ElasArgs {
   fe_status_word* st;
 };
 
-struct ElasSmem {
-  uint32_t q, coef, lvid, cg, lm, total;
-};
-__host__ __device__ __forceinline__ ElasSmem elas_smem(int D, int sizeT, uint32_t rec_max,
-                                                       uint32_t max_lv, uint32_t chunk) {
-  const uint32_t nv = D + 1;
-  ElasSmem L;
-  uint32_t o = pad16(rec_max);
-  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
-  L.coef = o; o += pad16(2u * sizeT * max_lv);
-  L.lvid = o; o += pad16(2u * nv * chunk);
-  L.cg = o;   o += pad16(sizeT * nv * D * chunk);
-  L.lm = o;   o += pad16(2u * sizeT * chunk);
-  L.total = o;
-  return L;
-}
-
 // sum over the element's vertices of a coefficient's P1 values (lambda^s, mu^s)
 template <int D, class T>
 __device__ __forceinline__ T coef_sum(const void* c, int kind, const int32_t* order, int64_t e,

@@ -91,7 +91,8 @@ __device__ __forceinline__ uint64_t spread_bits(uint64_t x, int d) {
 }
 
 __global__ void k_morton_keys(const double* q, int64_t nq, const int32_t* me, int64_t nme, int d,
-                              const double* bbox, int qbits, uint64_t* keys, uint32_t* vals) {
+                              const double* bbox, int qbits, const int32_t* group, uint64_t* keys,
+                              uint32_t* vals) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nme) return;
   const double scale = (double)(1u << qbits);
@@ -107,6 +108,7 @@ __global__ void k_morton_keys(const double* q, int64_t nq, const int32_t* me, in
     if (iq >= (1ull << qbits)) iq = (1ull << qbits) - 1;
     code |= spread_bits(iq, d) << c;
   }
+  if (group) code |= (uint64_t)group[k] << (qbits * d);
   keys[k] = code;
   vals[k] = (uint32_t)k;
 }
@@ -210,8 +212,11 @@ __global__ void k_vinc_keys(const int32_t* me_int, int64_t nme, int nv, int chun
 
 // edge incidences: entry i = e * npair + p, key (chunk, vmin, vmax),
 // value ((e_local * npair + p) << 1) | (me(a) > me(b)) for pair p = (a, b), a < b
-__global__ void k_einc_keys(const int32_t* me_int, int64_t nme, int nv, int npair, int chunk,
-                            int vbits, uint64_t* keys, uint32_t* vals) {
+// edge incidences: entry i = e * npair + p, key (chunk, nonzero of the edge oriented
+// (vmin, vmax)) taken from the slot map, value ((e_local * npair + p) << 1) |
+// (me(a) > me(b)) for pair p = (a, b), a < b
+__global__ void k_einc_keys(const int32_t* me_int, const int32_t* slot2nnz, int64_t nme, int nv,
+                            int npair, int chunk, int nbits, uint64_t* keys, uint32_t* vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nme * npair) return;
   const int64_t e = i / npair;
@@ -222,12 +227,23 @@ __global__ void k_einc_keys(const int32_t* me_int, int64_t nme, int nv, int npai
       if (cnt == p) { a = x; b = y; }
       ++cnt;
     }
-  const uint64_t va = (uint64_t)me_int[(int64_t)a * nme + e];
-  const uint64_t vb = (uint64_t)me_int[(int64_t)b * nme + e];
-  const uint64_t lo = va < vb ? va : vb, hi = va < vb ? vb : va;
+  const int32_t va = me_int[(int64_t)a * nme + e];
+  const int32_t vb = me_int[(int64_t)b * nme + e];
+  // slot (row a, col b) is e*nv^2 + b*nv + a; take the one whose row is the smaller vertex
+  const int64_t slot = va < vb ? e * nv * nv + (int64_t)b * nv + a : e * nv * nv + (int64_t)a * nv + b;
   const uint64_t c = (uint64_t)(e / chunk);
-  keys[i] = (c << (2 * vbits)) | (lo << vbits) | hi;
+  keys[i] = (c << nbits) | (uint64_t)slot2nnz[slot];
   vals[i] = (uint32_t)((((e % chunk) * npair + p) << 1) | (va > vb ? 1 : 0));
+}
+
+// row of nonzero j of a CSR matrix (last row r with rp[r] <= j)
+__device__ __forceinline__ int32_t row_of(const int32_t* rp, int64_t nrows, int32_t j) {
+  int64_t lo = 0, hi = nrows - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (rp[mid] <= j) lo = mid; else hi = mid - 1;
+  }
+  return (int32_t)lo;
 }
 
 // Local entities from sorted incidence keys. For a head at sorted position i with
@@ -235,7 +251,8 @@ __global__ void k_einc_keys(const int32_t* me_int, int64_t nme, int nv, int npai
 // global destination(s). Shared entities are flagged for the partial-sum pass.
 __global__ void k_local_entities(const uint64_t* keys, const uint32_t* pos, int64_t n, int per_elem,
                                  int chunk, int ebits, int vbits, bool edges, const int32_t* rp,
-                                 const int32_t* ci, const int32_t* nnz_slot_ptr, int m, uint16_t* off,
+                                 const int32_t* ci, const int32_t* nnz_slot_ptr, int64_t nq, int m,
+                                 uint16_t* off,
                                  int32_t* ch_ptr, int32_t* dst, int32_t* vid, uint16_t* str,
                                  uint32_t* shared_flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -262,8 +279,9 @@ __global__ void k_local_entities(const uint64_t* keys, const uint32_t* pos, int6
       str[u] = (uint16_t)(m * (rp[v + 1] - rp[v]));
     }
   } else {
-    const int32_t hi = (int32_t)(key & vmask), lo = (int32_t)((key >> vbits) & vmask);
-    const int32_t nij = find_nnz(rp, ci, lo, hi), nji = find_nnz(rp, ci, hi, lo);
+    const int32_t nij = (int32_t)(key & ((1ull << ebits) - 1ull));
+    const int32_t lo = row_of(rp, nq, nij), hi = ci[nij];
+    const int32_t nji = find_nnz(rp, ci, hi, lo);
     dst[2 * (int64_t)u] = nij;
     dst[2 * (int64_t)u + 1] = nji;
     global_count = nnz_slot_ptr[nij + 1] - nnz_slot_ptr[nij];
@@ -438,6 +456,7 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
   h->nchunks = (nme + C - 1) / C;
   const int cbits = bitlen((uint64_t)(h->nchunks > 1 ? h->nchunks - 1 : 1));
   const int vbits = bitlen((uint64_t)(h->nq > 1 ? h->nq - 1 : 1));
+  const int nbits = bitlen((uint64_t)(h->nnz_s > 1 ? h->nnz_s - 1 : 1));
   const int T = 256;
   uint32_t *flag, *pos;
   const int64_t nmax = nme * (nv > npair ? nv : npair);
@@ -454,9 +473,11 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     if (!edges)
       k_vinc_keys<<<fe_grid(n, T), T, 0, s>>>(h->me_int, nme, nv, C, vbits, sb->k0, sb->v0);
     else
-      k_einc_keys<<<fe_grid(n, T), T, 0, s>>>(h->me_int, nme, nv, npair, C, vbits, sb->k0, sb->v0);
+      k_einc_keys<<<fe_grid(n, T), T, 0, s>>>(h->me_int, h->slot2nnz, nme, nv, npair, C, nbits, sb->k0,
+                                              sb->v0);
     FE_CUDA_TRY(cudaGetLastError());
-    const int ebits = edges ? 2 * vbits : vbits;
+    const int ebits = edges ? nbits : vbits;
+    if (ebits + cbits > 64) return FE_ERR_OVERFLOW;
     FE_TRY(fe_radix_sort(n, ebits + cbits, sb, &keys, &vals, s));
     k_key_change<<<fe_grid(n, T), T, 0, s>>>(keys, n, flag);
     FE_CUDA_TRY(cudaGetLastError());
@@ -479,8 +500,8 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     k_to_u16<<<fe_grid(n, T), T, 0, s>>>(vals, inc, n);
     FE_CUDA_TRY(cudaGetLastError());
     k_local_entities<<<fe_grid(n, T), T, 0, s>>>(keys, pos, n, per, C, ebits, vbits, edges,
-                                                  h->row_ptr_s, h->col_idx_s, h->nnz_slot_ptr, h->m,
-                                                  off, ch_ptr, dst, vid, str, sflag);
+                                                  h->row_ptr_s, h->col_idx_s, h->nnz_slot_ptr, h->nq,
+                                                  h->m, off, ch_ptr, dst, vid, str, sflag);
     FE_CUDA_TRY(cudaGetLastError());
     k_set_last<<<1, 1, 0, s>>>(ch_ptr, h->nchunks, (int32_t)nloc);
     FE_CUDA_TRY(cudaGetLastError());
@@ -620,6 +641,11 @@ __global__ void k_vmap_ptr(const uint64_t* keys, int64_t n, int64_t nq, int32_t*
 }  // namespace
 
 namespace {
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
 __global__ void k_union_me(const int32_t* me, int64_t nme, int nv, int64_t voff, int64_t eoff,
                            int64_t nme_total, int32_t* me_u) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -656,6 +682,11 @@ int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s) {
   return FE_OK;
 }
 
+namespace {
+int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
+                    const int32_t* group, int group_bits);
+}  // namespace
+
 extern "C" int fe_batch_pattern(const fe_mesh* meshes, int32_t count, int32_t m, int32_t flags,
                                 void* stream, fe_pattern_h* out) {
   if (!meshes || !out || count < 1) return FE_ERR_ARG;
@@ -684,8 +715,15 @@ extern "C" int fe_batch_pattern(const fe_mesh* meshes, int32_t count, int32_t m,
     k_union_me<<<fe_grid(mb.nme, 256), 256, 0, s>>>(mb.me, mb.nme, nv, voff[b], eoff[b], eoff[count], meu);
     FE_CUDA_TRY(cudaGetLastError());
   }
+  // order elements by (mesh, Morton code) so that chunks stay inside one mesh
+  int32_t* grp;
+  FE_TRY(tmp.get(&grp, (size_t)eoff[count]));
+  for (int b = 0; b < count; ++b) {
+    k_fill_i32<<<fe_grid(eoff[b + 1] - eoff[b], 256), 256, 0, s>>>(grp + eoff[b], eoff[b + 1] - eoff[b], b);
+    FE_CUDA_TRY(cudaGetLastError());
+  }
   fe_mesh u{d, voff[count], eoff[count], qu, meu};
-  FE_TRY(fe_pattern(&u, m, flags, stream, out));
+  FE_TRY(fe_pattern_impl(&u, m, flags, stream, out, grp, bitlen((uint64_t)count)));
   fe_pattern_s* h = *out;
   h->batch_voff = voff;
   h->batch_eoff = eoff;
@@ -732,8 +770,31 @@ extern "C" int fe_batch_gather_q(fe_pattern_h h, const fe_mesh* meshes, double* 
   return FE_OK;
 }
 
+namespace {
+void free_plan(fe_pattern_s* h) {
+  void** ptrs[] = {(void**)&h->ch_v_ptr, (void**)&h->ch_e_ptr, (void**)&h->lv_off, (void**)&h->le_off,
+                   (void**)&h->inc_v,    (void**)&h->inc_e,    (void**)&h->lv_dst, (void**)&h->lv_vid,
+                   (void**)&h->le_dst,   (void**)&h->lv_str,   (void**)&h->le_str, (void**)&h->sh_ptr,
+                   (void**)&h->sh_dst,   (void**)&h->sh_str,   (void**)&h->rec,    (void**)&h->rec_off16,
+                   &h->partials};
+  for (void** p : ptrs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+}
+
+int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
+                    const int32_t* group, int group_bits);
+}  // namespace
+
 extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
                           fe_pattern_h* out) {
+  return fe_pattern_impl(mesh, m, flags, stream, out, nullptr, 0);
+}
+
+namespace {
+int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
+                    const int32_t* group, int group_bits) {
   if (!mesh || !out) return FE_ERR_ARG;
   *out = nullptr;
   const int d = mesh->d;
@@ -791,10 +852,12 @@ extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* s
       k_bbox_final<<<1, 32, 0, s>>>(bb, nblk, d);
       int qbits = (bitlen((uint64_t)nme) + d - 1) / d + 2;
       if (qbits > 21) qbits = 21;
-      k_morton_keys<<<fe_grid(nme, T), T, 0, s>>>(mesh->q, nq, mesh->me, nme, d, bb, qbits, sb.k0,
-                                                 sb.v0);
+      const int gbits = group ? group_bits : 0;
+      if (qbits * d + gbits > 64) qbits = (64 - gbits) / d;
+      k_morton_keys<<<fe_grid(nme, T), T, 0, s>>>(mesh->q, nq, mesh->me, nme, d, bb, qbits, group,
+                                                 sb.k0, sb.v0);
       if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
-      if ((rc = fe_radix_sort(nme, qbits * d, &sb, &keys, &vals, s))) break;
+      if ((rc = fe_radix_sort(nme, qbits * d + (group ? group_bits : 0), &sb, &keys, &vals, s))) break;
     }
     k_permute_me<<<fe_grid(nme, T), T, 0, s>>>(mesh->me, nme, nv, vals, h->me_int, h->order);
     if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
@@ -841,7 +904,17 @@ extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* s
     }
 
     // 5. chunk plan
-    if ((rc = build_chunk_plan(h, &sb, tmp, s))) break;
+    // shrink the chunk until the worst-case block's shared memory fits (227 KB)
+    for (;;) {
+      if ((rc = build_chunk_plan(h, &sb, tmp, s))) break;
+      const uint32_t need = fe::plan_smem_worst(d, m, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,
+                                                (uint32_t)h->chunk);
+      if (need <= 227u * 1024u || h->chunk <= 32) break;
+      if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
+      free_plan(h);
+      h->chunk /= 2;
+    }
+    if (rc) break;
     if ((rc = fe_ensure_scratch(h, h->strategy))) break;
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
   } while (0);
@@ -854,3 +927,4 @@ extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* s
   *out = h;
   return FE_OK;
 }
+}  // namespace

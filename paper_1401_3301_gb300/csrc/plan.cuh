@@ -42,4 +42,48 @@ __host__ __device__ __forceinline__ RecLayout rec_layout(uint32_t ne, uint32_t n
   return L;
 }
 
+// Shared-memory layout of the staged chunk kernel (byte offsets).
+struct StagedSmem {
+  uint32_t q, w, lvid, kd, ko, total;
+};
+__host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, bool p1_weight,
+                                                           uint32_t rec_max, uint32_t max_lv,
+                                                           uint32_t chunk) {
+  const uint32_t nv = D + 1, np = D * (D + 1) / 2;
+  StagedSmem L;
+  uint32_t o = pad16(rec_max);
+  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
+  L.w = o;    o += p1_weight ? pad16(sizeT * max_lv) : 0u;
+  L.lvid = o; o += pad16(2u * nv * chunk);
+  L.kd = o;   o += pad16(sizeT * nv * chunk);
+  L.ko = o;   o += pad16(sizeT * np * chunk);
+  L.total = o;
+  return L;
+}
+
+struct ElasSmem {
+  uint32_t q, coef, lvid, cg, lm, total;
+};
+__host__ __device__ __forceinline__ ElasSmem elas_smem(int D, int sizeT, uint32_t rec_max,
+                                                       uint32_t max_lv, uint32_t chunk) {
+  const uint32_t nv = D + 1;
+  ElasSmem L;
+  uint32_t o = pad16(rec_max);
+  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
+  L.coef = o; o += pad16(2u * sizeT * max_lv);
+  L.lvid = o; o += pad16(2u * nv * chunk);
+  L.cg = o;   o += pad16(sizeT * nv * D * chunk);
+  L.lm = o;   o += pad16(2u * sizeT * chunk);
+  L.total = o;
+  return L;
+}
+
+// Largest shared-memory footprint of any chunked kernel for a plan (FP64, with a P1
+// coefficient): the plan build shrinks the chunk until it fits in one block.
+__host__ __device__ __forceinline__ uint32_t plan_smem_worst(int D, int m, uint32_t rec_max,
+                                                             uint32_t max_lv, uint32_t chunk) {
+  return m == 1 ? staged_smem(D, 8, true, rec_max, max_lv, chunk).total
+                : elas_smem(D, 8, rec_max, max_lv, chunk).total;
+}
+
 }  // namespace fe

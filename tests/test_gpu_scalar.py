@@ -200,3 +200,19 @@ def test_split_coordinates_fp32_form_accuracy_on_large_offsets():
     err = normalised_error(fe.fe_assemble_stiff(p, q, prec=1).double().cpu().numpy(), ref["val"],
                            ref["scale"])
     assert err <= 1e-5, err
+
+
+def test_unordered_mesh_shrinks_chunks_and_stays_correct():
+    # KEEP_ORDER on a randomly ordered mesh: chunks touch most of the mesh, so the plan
+    # build halves the chunk until a block's shared memory fits
+    fe = fe_or_skip()
+    m = meshgen.kuhn_cube_mesh(16, seed=12)
+    q, me = to_cuda(m.q), to_cuda(m.me)
+    p = fe.fe_pattern(q, me, flags=fe.PATTERN_KEEP_ORDER | fe.PATTERN_CHUNK(4096))
+    assert p.plan_info()["chunk"] < 4096
+    ref = oracle.assemble(oracle.WMASS, m.q, m.me, c1=(oracle.COEF_P1, meshgen.vertex_weights(1, m.nq)))
+    import torch
+    vals = fe.fe_assemble_wmass(p, q, to_cuda(meshgen.vertex_weights(1, m.nq)), fe.COEF_P1)
+    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
+    ref_s = oracle.assemble(oracle.STIFF, m.q, m.me)
+    assert normalised_error(fe.fe_assemble_stiff(p, q).cpu().numpy(), ref_s["val"], ref_s["scale"]) <= 1e-12
