@@ -15,6 +15,7 @@ template <int D, class T>
 struct ScalarVals {
   T diag[D + 1];
   T off[Pairs<D>::n];
+  T scale;  // common factor still to be applied (1 unless the scaling is deferred)
 };
 
 // per-element coefficient (P0 kinds); 1 when there is none
@@ -28,14 +29,21 @@ __device__ __forceinline__ T elem_coef(const void* w, int w_kind, const int32_t*
 }
 
 // Local matrix entries from the geometry. wv: vertex values of the weight (P1 kind).
-template <int D, class T, int KIND>
+// DEFER (stiffness): leave the per-element factor w / (d! |det B|) in out.scale for the
+// caller to apply while summing (one FMA per incidence instead of six products here).
+template <int D, class T, int KIND, bool DEFER = false>
 __device__ __forceinline__ void values_from_geo(const Geo<D, T>& g, bool has_coef, T coef,
                                                 const T* wv, ScalarVals<D, T>& out) {
   constexpr int NV = D + 1;
   const T adet = tabs(g.det);
+  out.scale = T(1);
   if constexpr (KIND == K_STIFF) {
     T inv = recip<T>(T(factorial(D)) * adet);
     if (has_coef) inv *= coef;
+    if constexpr (DEFER) {
+      out.scale = inv;
+      inv = T(1);
+    }
     // scaled Gram matrix of c_1..c_D; the row of vertex 0 follows from sum_a c_a = 0
     T G[D][D];
 #pragma unroll
@@ -45,7 +53,7 @@ __device__ __forceinline__ void values_from_geo(const Geo<D, T>& g, bool has_coe
         T s = g.c[i + 1][0] * g.c[j + 1][0];
 #pragma unroll
         for (int k = 1; k < D; ++k) s += g.c[i + 1][k] * g.c[j + 1][k];
-        G[i][j] = s * inv;
+        G[i][j] = DEFER ? s : s * inv;
         G[j][i] = G[i][j];
       }
     T nr[D];  // nr[i] = S_{0, i+1} = -sum_j G[i][j]
@@ -138,12 +146,14 @@ struct Acc<double> {
   Acc() = default;
   __device__ __forceinline__ explicit Acc(double first) : s(first) {}
   __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_scaled(double x, double f) { s = fma(x, f, s); }
   __device__ __forceinline__ double value() const { return s; }
   __device__ __forceinline__ void store_partial(void* p, int64_t i) const { ((double*)p)[i] = s; }
   __device__ __forceinline__ static Acc from_partial(const void* p, int64_t i) {
     return Acc(((const double*)p)[i]);
   }
   __device__ __forceinline__ void add_partial(const void* p, int64_t i) { s += ((const double*)p)[i]; }
+  __device__ __forceinline__ void add_acc(const Acc& o) { s += o.s; }
 };
 template <>
 struct Acc<float> {
@@ -151,6 +161,7 @@ struct Acc<float> {
   Acc() = default;
   __device__ __forceinline__ explicit Acc(float first) { s.s = first; s.c = 0.f; }
   __device__ __forceinline__ void add(float x) { s.add(x); }
+  __device__ __forceinline__ void add_scaled(float x, float f) { s.add(x * f); }
   __device__ __forceinline__ float value() const { return s.value(); }
   __device__ __forceinline__ void store_partial(void* p, int64_t i) const {
     ((float2*)p)[i] = make_float2(s.s, s.c);
@@ -165,6 +176,7 @@ struct Acc<float> {
     const float2 v = ((const float2*)p)[i];
     s.add2(v.x, v.y);
   }
+  __device__ __forceinline__ void add_acc(const Acc& o) { s.add2(o.s.s, o.s.c); }
 };
 
 // ---------------------------------------------------------------- FE_REASM_CHUNKED
@@ -198,6 +210,8 @@ template <int D, class T, int KIND, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __restrict__ vals,
                                                           void* __restrict__ partials) {
   constexpr int NV = D + 1, NP = Pairs<D>::n;
+  // FP64 stiffness: apply each element's scale while summing (FMA) instead of per entry
+  constexpr bool DEFER = (KIND == K_STIFF) && (sizeof(T) == 8);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   const int64_t c = blockIdx.x;
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
-  const StagedSmem S = staged_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
+  const StagedSmem S = staged_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, DEFER);
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_arrive_expect_tx(&bar, R.total);
@@ -232,6 +246,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   T* Kd = (T*)(smem + S.kd);
   T* Ko = (T*)(smem + S.ko);
   T* wl = (T*)(smem + S.w);
+  T* Sc = (T*)(smem + S.sc);
 
   // 0. vertex coordinates of the chunk, and the local vertex of every element corner
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
@@ -310,27 +325,36 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
     }
     const T coef = has_coef ? elem_coef<T>(A.w, A.w_kind, A.order, e0 + el) : T(1);
     ScalarVals<D, T> v;
-    values_from_geo<D, T, KIND>(g, has_coef, coef, wv, v);
+    values_from_geo<D, T, KIND, DEFER>(g, has_coef, coef, wv, v);
 #pragma unroll
     for (int a = 0; a < NV; ++a) Kd[el * NV + a] = v.diag[a];
 #pragma unroll
     for (int p = 0; p < NP; ++p) Ko[el * NP + p] = v.off[p];
+    if constexpr (DEFER) Sc[el] = v.scale;
   }
   __syncthreads();
 
   // 2. sums over the incidences of each distinct vertex and edge, in element order
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int s = lv_off[u], t = lv_off[u + 1];
-    Acc<T> acc(Kd[inc_v[s]]);
-    for (int j = s + 1; j < t; ++j) acc.add(Kd[inc_v[j]]);
+    Acc<T> acc = DEFER ? Acc<T>(Kd[inc_v[s]] * Sc[inc_v[s] / NV]) : Acc<T>(Kd[inc_v[s]]);
+    for (int j = s + 1; j < t; ++j) {
+      if constexpr (DEFER) acc.add_scaled(Kd[inc_v[j]], Sc[inc_v[j] / NV]);
+      else acc.add(Kd[inc_v[j]]);
+    }
     const int32_t dst = lv_dst[u];
     if (dst >= 0) vals[dst] = acc.value();
     else acc.store_partial(partials, -1 - (int64_t)dst);
   }
   for (int u = threadIdx.x; u < nle; u += THREADS) {
     const int s = le_off[u], t = le_off[u + 1];
-    Acc<T> acc(Ko[inc_e[s] >> 1]);
-    for (int j = s + 1; j < t; ++j) acc.add(Ko[inc_e[j] >> 1]);
+    const int i0 = inc_e[s] >> 1;
+    Acc<T> acc = DEFER ? Acc<T>(Ko[i0] * Sc[i0 / NP]) : Acc<T>(Ko[i0]);
+    for (int j = s + 1; j < t; ++j) {
+      const int ij = inc_e[j] >> 1;
+      if constexpr (DEFER) acc.add_scaled(Ko[ij], Sc[ij / NP]);
+      else acc.add(Ko[ij]);
+    }
     const int32_t dst = le_dst[2 * u];
     if (dst >= 0) {
       const T val = acc.value();
@@ -350,11 +374,20 @@ __global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nsh) return;
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
+  const int32_t d0 = sh_dst[2 * g], d1 = sh_dst[2 * g + 1];
   Acc<T> acc = Acc<T>::from_partial(partials, s);
-  for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, i);
+  int32_t i = s + 1;
+  for (; i + 2 < t; i += 3) {  // three independent loads in flight, summed in order
+    Acc<T> b0 = Acc<T>::from_partial(partials, i), b1 = Acc<T>::from_partial(partials, i + 1),
+           b2 = Acc<T>::from_partial(partials, i + 2);
+    acc.add_acc(b0);
+    acc.add_acc(b1);
+    acc.add_acc(b2);
+  }
+  for (; i < t; ++i) acc.add_partial(partials, i);
   const T val = acc.value();
-  vals[sh_dst[2 * g]] = val;
-  if (g >= nsh_v) vals[sh_dst[2 * g + 1]] = val;
+  vals[d0] = val;
+  if (g >= nsh_v) vals[d1] = val;
 }
 
 // ---------------------------------------------------------------- FE_REASM_GATHER

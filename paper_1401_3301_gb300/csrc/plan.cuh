@@ -44,11 +44,11 @@ __host__ __device__ __forceinline__ RecLayout rec_layout(uint32_t ne, uint32_t n
 
 // Shared-memory layout of the staged chunk kernel (byte offsets).
 struct StagedSmem {
-  uint32_t q, w, lvid, kd, ko, total;
+  uint32_t q, w, lvid, kd, ko, sc, total;
 };
 __host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, bool p1_weight,
                                                            uint32_t rec_max, uint32_t max_lv,
-                                                           uint32_t chunk) {
+                                                           uint32_t chunk, bool scale = false) {
   const uint32_t nv = D + 1, np = D * (D + 1) / 2;
   StagedSmem L;
   uint32_t o = pad16(rec_max);
@@ -57,6 +57,7 @@ __host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, boo
   L.lvid = o; o += pad16(2u * nv * chunk);
   L.kd = o;   o += pad16(sizeT * nv * chunk);
   L.ko = o;   o += pad16(sizeT * np * chunk);
+  L.sc = o;   o += scale ? pad16(sizeT * chunk) : 0u;
   L.total = o;
   return L;
 }
@@ -82,8 +83,10 @@ __host__ __device__ __forceinline__ ElasSmem elas_smem(int D, int sizeT, uint32_
 // coefficient): the plan build shrinks the chunk until it fits in one block.
 __host__ __device__ __forceinline__ uint32_t plan_smem_worst(int D, int m, uint32_t rec_max,
                                                              uint32_t max_lv, uint32_t chunk) {
-  return m == 1 ? staged_smem(D, 8, true, rec_max, max_lv, chunk).total
-                : elas_smem(D, 8, rec_max, max_lv, chunk).total;
+  if (m > 1) return elas_smem(D, 8, rec_max, max_lv, chunk).total;
+  const uint32_t a = staged_smem(D, 8, true, rec_max, max_lv, chunk).total;
+  const uint32_t b = staged_smem(D, 8, false, rec_max, max_lv, chunk, true).total;
+  return a > b ? a : b;
 }
 
 }  // namespace fe
