@@ -49,6 +49,11 @@ extern "C" {
 #define FE_F64 0 /* FP64 arithmetic, FP64 values */
 #define FE_F32 1 /* FP32 values; det B and |K| from FP64-accurate coordinates
                     differences in double-float arithmetic; compensated sums */
+#define FE_F64X 2 /* fe_assemble_stiff only: FP64 values of FP64-class accuracy
+                    computed in double-float (pairs of floats, about 48 bits) on the
+                    FP32 pipe; native FP64 only for coordinates relative to a vertex of
+                    each element chunk and for converting sums to double. Coefficients
+                    are double, as for FE_F64. */
 
 /* ---- coefficient kinds (coefficient arrays use the precision of the form:
  *      double for FE_F64, float for FE_F32) */

@@ -1,0 +1,304 @@
+// FE_F64X form of the stiffness assembly: FP64 inputs and outputs, FP64-class
+// accuracy, arithmetic in double-float (unevaluated sums of two floats, about 48
+// significant bits) on the FP32 pipe, which on this part issues 64 times as many
+// operations per clock as the FP64 pipe. Native FP64 is used only to take each
+// chunk vertex's coordinates relative to a reference vertex of the chunk (so that
+// large coordinate offsets cannot cost accuracy) and to convert each final sum to
+// double.
+//
+// Local stiffness (Eq. stiffelemmat): S_ab = w (c_a . c_b) / (d! |det B|) with the
+// cofactor vectors c_a of B = [q^1 - q^0, ...]; the row of vertex 0 follows from
+// sum_a c_a = 0. Sums over the incidences of each chunk vertex / edge run in
+// ascending element order, then over chunks in chunk order (as in the other forms).
+#include "assemble_impl.cuh"
+#include "profile.cuh"
+
+namespace fe {
+namespace {
+
+// double-float helpers on top of elem.cuh: products with the low parts, reciprocal
+__device__ __forceinline__ df df_mul_full(df a, df b) {  // relative error ~2^-47
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_recip(df a) {  // one Newton step from the float reciprocal
+  const float r = __frcp_rn(a.hi);
+  // e = 1 - a r in double-float, then r (1 + e)
+  const df ar = df_mul_full(a, df{r, 0.f});
+  const df e = df_add(df{1.f, 0.f}, df_neg(ar));
+  return df_add(df{r, 0.f}, df_mul_full(df{r, 0.f}, e));
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// a*b - c*d for double-float operands: exact double-float of the high parts plus the
+// first-order terms of the low parts
+__device__ __forceinline__ df df_cross_term(df a, df b, df c, df d) {
+  const df h = diff_of_products(a.hi, b.hi, c.hi, d.hi);
+  float lo = h.lo;
+  lo = __fmaf_rn(a.lo, b.hi, lo);
+  lo = __fmaf_rn(a.hi, b.lo, lo);
+  lo = __fmaf_rn(-c.lo, d.hi, lo);
+  lo = __fmaf_rn(-c.hi, d.lo, lo);
+  return fast_two_sum(h.hi, lo);
+}
+
+template <int D>
+__device__ __forceinline__ df df_dot(const df* x, const df* y) {
+  df s = df_mul_full(x[0], y[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) s = df_add(s, df_mul_full(x[k], y[k]));
+  return s;
+}
+
+struct X64Args {
+  int64_t nme, nq;
+  int chunk;
+  uint32_t rec_max, max_lv;
+  const double* q;
+  const double* w;
+  int w_kind;
+  const int32_t* order;
+  const int32_t* ch_v_ptr;
+  const int32_t* ch_e_ptr;
+  const uint8_t* rec;
+  const uint32_t* rec_off16;
+  fe_status_word* st;
+};
+
+template <int D, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double* __restrict__ vals,
+                                                              float2* __restrict__ partials) {
+  constexpr int NV = D + 1, NP = Pairs<D>::n;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t c = blockIdx.x;
+  const int64_t e0 = c * A.chunk;
+  const int ne = (int)min((int64_t)A.chunk, A.nme - e0);
+  const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
+  const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
+  const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
+  // same footprint as the FP32 form: split coordinates, uint16 corner map, float2 values
+  const StagedSmem S = staged_smem(D, 8, false, A.rec_max, A.max_lv, A.chunk);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, R.total);
+    bulk_copy_g2s(smem, A.rec + (int64_t)A.rec_off16[c] * 16, R.total, &bar);
+  }
+  __syncthreads();
+  const bool landed = __syncthreads_and(mbar_wait_bounded(&bar, 0, kBarrierSpin));
+  if (!landed) {
+    if (threadIdx.x == 0) {
+      fe_report(A.st, FE_ERR_TIMEOUT, e0);
+      mbar_wait_bounded(&bar, 0, kBarrierSpin);
+    }
+    return;
+  }
+  const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
+  const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
+  const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
+  const uint16_t* le_off = (const uint16_t*)(smem + R.le_off);
+  const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
+  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  float2* Kd = (float2*)(smem + S.kd);
+  float2* Ko = (float2*)(smem + S.ko);
+
+  // 0. coordinates relative to the chunk's first vertex (FP64), split into float pairs
+  double xr[D];
+  {
+    const int64_t v0 = lv_vid[0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
+  }
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int64_t vid = lv_vid[u];
+    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < D; ++k) split_f64(__ldg(A.q + k * A.nq + vid) - xr[k], h[k], l[k]);
+    float4* xs = (float4*)(smem + S.q) + (D == 3 ? 2 : 1) * u;
+    if constexpr (D == 3) {
+      xs[0] = make_float4(h[0], h[1], h[2], 0.f);
+      xs[1] = make_float4(l[0], l[1], l[2], 0.f);
+    } else {
+      xs[0] = make_float4(h[0], h[1], l[0], l[1]);
+    }
+    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
+  }
+  __syncthreads();
+
+  // 1. element entries in double-float
+  for (int el = threadIdx.x; el < ne; el += THREADS) {
+    float xh[NV][D], xl[NV][D];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lvid[el * NV + a];
+      const float4 h = xs[0];
+      if constexpr (D == 3) {
+        const float4 l = xs[1];
+        xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
+        xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
+      } else {
+        xh[a][0] = h.x; xh[a][1] = h.y;
+        xl[a][0] = h.z; xl[a][1] = h.w;
+      }
+    }
+    df e[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const df s = two_sum(xh[i + 1][k], -xh[0][k]);
+        e[i][k] = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][k], xl[0][k])));
+      }
+    df cf[D][D];  // cofactor vectors c_1..c_D
+    df det;
+    if constexpr (D == 3) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const df* u1 = e[(i + 1) % 3];
+        const df* u2 = e[(i + 2) % 3];
+        cf[i][0] = df_cross_term(u1[1], u2[2], u1[2], u2[1]);
+        cf[i][1] = df_cross_term(u1[2], u2[0], u1[0], u2[2]);
+        cf[i][2] = df_cross_term(u1[0], u2[1], u1[1], u2[0]);
+      }
+      det = df_dot<3>(e[0], cf[0]);
+    } else {
+      cf[0][0] = e[1][1];
+      cf[0][1] = df_neg(e[1][0]);
+      cf[1][0] = df_neg(e[0][1]);
+      cf[1][1] = e[0][0];
+      det = df_cross_term(e[0][0], e[1][1], e[0][1], e[1][0]);
+    }
+    const float dh = __fadd_rn(det.hi, det.lo);
+    const unsigned int ex = (__float_as_uint(dh) >> 23) & 0xFFu;
+    if (ex == 0u || ex == 0xFFu) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+      det = df{1.f, 0.f};
+    }
+    if (det.hi < 0.f) det = df_neg(det);
+    df inv = df_recip(df_mul_full(det, df{(float)factorial(D), 0.f}));
+    if (A.w_kind != FE_COEF_NONE) {
+      const double wv = elem_coef<double>(A.w, A.w_kind, A.order, e0 + el);
+      float wh, wl;
+      split_f64(wv, wh, wl);
+      inv = df_mul_full(inv, df{wh, wl});
+    }
+    df G[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) {
+        G[i][j] = df_mul_full(df_dot<D>(cf[i], cf[j]), inv);
+        G[j][i] = G[i][j];
+      }
+    df nr[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      df s = df_neg(G[i][0]);
+#pragma unroll
+      for (int j = 1; j < D; ++j) s = df_sub(s, G[i][j]);
+      nr[i] = s;
+    }
+    df d0 = df_neg(nr[0]);
+#pragma unroll
+    for (int i = 1; i < D; ++i) d0 = df_sub(d0, nr[i]);
+    Kd[el * NV] = make_float2(d0.hi, d0.lo);
+#pragma unroll
+    for (int i = 0; i < D; ++i) Kd[el * NV + i + 1] = make_float2(G[i][i].hi, G[i][i].lo);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
+      const df v = (a == 0) ? nr[b - 1] : G[a - 1][b - 1];
+      Ko[el * NP + p] = make_float2(v.hi, v.lo);
+    }
+  }
+  __syncthreads();
+
+  // 2. sums in element order; owned sums become doubles, shared ones stay float pairs
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int s = lv_off[u], t = lv_off[u + 1];
+    float2 v = Kd[inc_v[s]];
+    df acc{v.x, v.y};
+    for (int j = s + 1; j < t; ++j) {
+      v = Kd[inc_v[j]];
+      acc = df_add(acc, df{v.x, v.y});
+    }
+    const int32_t dst = lv_dst[u];
+    if (dst >= 0) vals[dst] = df_to_double(acc);
+    else partials[-1 - (int64_t)dst] = make_float2(acc.hi, acc.lo);
+  }
+  for (int u = threadIdx.x; u < nle; u += THREADS) {
+    const int s = le_off[u], t = le_off[u + 1];
+    float2 v = Ko[inc_e[s] >> 1];
+    df acc{v.x, v.y};
+    for (int j = s + 1; j < t; ++j) {
+      v = Ko[inc_e[j] >> 1];
+      acc = df_add(acc, df{v.x, v.y});
+    }
+    const int32_t dst = le_dst[2 * u];
+    if (dst >= 0) {
+      const double val = df_to_double(acc);
+      vals[dst] = val;
+      vals[le_dst[2 * u + 1]] = val;
+    } else {
+      partials[-1 - (int64_t)dst] = make_float2(acc.hi, acc.lo);
+    }
+  }
+}
+
+__global__ void k_fixup_f64x(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
+                             int64_t nsh_v, int64_t nsh, const float2* __restrict__ partials,
+                             double* __restrict__ vals) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nsh) return;
+  const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
+  float2 v = partials[s];
+  df acc{v.x, v.y};
+  for (int32_t i = s + 1; i < t; ++i) {
+    v = partials[i];
+    acc = df_add(acc, df{v.x, v.y});
+  }
+  const double val = df_to_double(acc);
+  vals[sh_dst[2 * g]] = val;
+  if (g >= nsh_v) vals[sh_dst[2 * g + 1]] = val;
+}
+
+template <int D>
+int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
+  constexpr int THREADS = 256;
+  const StagedSmem L = staged_smem(D, 8, false, A.rec_max, A.max_lv, A.chunk);
+  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  auto kern = k_chunk_stiff_f64x<D, THREADS>;
+  static size_t configured = 0;
+  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_PROF_BEGIN(h, FE_K_CHUNK, s);
+  kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, (float2*)h->partials);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_PROF_END(h, FE_K_CHUNK, s);
+  const int64_t nsh = h->nsh_v + h->nsh_e;
+  if (nsh > 0) {
+    FE_PROF_BEGIN(h, FE_K_FIXUP, s);
+    k_fixup_f64x<<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
+                                                   (const float2*)h->partials, vals);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_PROF_END(h, FE_K_FIXUP, s);
+  }
+  return FE_OK;
+}
+
+}  // namespace
+}  // namespace fe
+
+int fe_launch_stiff_f64x(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals,
+                         cudaStream_t s) {
+  using namespace fe;
+  if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
+  X64Args A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, (const double*)w,
+            w_kind, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
+  return h->d == 3 ? launch<3>(h, A, (double*)vals, s) : launch<2>(h, A, (double*)vals, s);
+}

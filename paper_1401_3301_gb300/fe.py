@@ -13,7 +13,7 @@ import torch
 
 from . import build_ext
 
-F64, F32 = 0, 1
+F64, F32, F64X = 0, 1, 2
 COEF_NONE, COEF_SCALAR, COEF_P0, COEF_P1, COEF_P0_INTERNAL = 0, 1, 2, 3, 4
 REASM_CHUNKED, REASM_GATHER, REASM_ATOMIC = 0, 1, 2
 PATTERN_KEEP_ORDER = 1
@@ -109,7 +109,7 @@ class _Mesh(C.Structure):
 
 
 def _vtype(prec: int):
-    return torch.float64 if prec == F64 else torch.float32
+    return torch.float32 if prec == F32 else torch.float64
 
 
 class Pattern:
