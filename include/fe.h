@@ -134,6 +134,17 @@ int fe_batch_count(fe_pattern_h h, int32_t* count);
  * (d x total vertices), stream-ordered (one device copy per mesh and coordinate). */
 int fe_batch_gather_q(fe_pattern_h h, const fe_mesh* meshes, double* q_union, void* stream);
 
+/*
+ * fe_boundary_pattern -- pattern of a mesh of boundary facets: (d-1)-simplices in
+ * d-space (segments in 2D, triangles in 3D), for Neumann / Robin terms (Remark
+ * after Algorithm 6: the weighted mass algorithm applies to n-simplices, n <= d).
+ * facets->me has d rows (the facet's vertices, 0-based into q); q is d x nq.
+ * Only fe_assemble_mass and fe_assemble_wmass accept such a pattern; the facet
+ * measure is the Gram determinant sqrt(det(B^T B)) / (d-1)! with B the d x (d-1)
+ * matrix of edge vectors. Other conventions as fe_pattern (m = 1).
+ */
+int fe_boundary_pattern(const fe_mesh* facets, int32_t flags, void* stream, fe_pattern_h* out);
+
 /* Borrowed CSR arrays (int32, device): row_ptr[n+1], col_idx[nnz]. */
 int fe_pattern_csr(fe_pattern_h h, int64_t* n, int64_t* nnz, const int32_t** row_ptr,
                    const int32_t** col_idx);

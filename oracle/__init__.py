@@ -47,6 +47,8 @@ def _load():
         lib.orc_assemble.argtypes = [I32, I32, I64, I64, P, P, I32, P, I32, P,
                                      P, P, P, P, P, P, P]
         lib.orc_stiff_loss.argtypes = [I32, I64, I64, P, P, P, P, P, P, P, P, P]
+        lib.orc_facet.argtypes = [I32, P, P]
+        lib.orc_assemble_boundary.argtypes = [I32, I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P]
         lib.orc_free.argtypes = [P]
         _lib = lib
     return _lib
@@ -136,6 +138,43 @@ def assemble(kind: int, q: np.ndarray, me: np.ndarray, c1=None, c2=None) -> dict
                 row_ptr=take(rp, C.c_int64, N + 1, np.int64),
                 col_idx=take(ci, C.c_int32, NNZ, np.int32),
                 val=take(va, C.c_double, NNZ, np.float64),
+                scale=take(sc, C.c_double, NNZ, np.float64))
+
+
+def facet_measure(X: np.ndarray) -> float:
+    """Measure of a (d-1)-simplex in d-space; X is (d, d): one vertex per row."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    meas = C.c_double()
+    rc = _load().orc_facet(X.shape[1], _ptr(X), C.byref(meas))
+    if rc:
+        raise OracleError(rc)
+    return meas.value
+
+
+def assemble_boundary(kind: int, q: np.ndarray, facets: np.ndarray, c1=None) -> dict:
+    """Boundary (facet) mass / weighted mass; same result dict as assemble()."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    fa = np.ascontiguousarray(facets, dtype=np.int32)
+    d, nq = q.shape
+    k1, a1 = _coef(c1)
+    n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
+    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    lib = _load()
+    rc = lib.orc_assemble_boundary(kind, d, nq, fa.shape[1], _ptr(q), _ptr(fa), k1, _ptr(a1),
+                                   C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
+                                   C.byref(sc), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+
+    def take(p, ctype, count, dtype):
+        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
+        out = np.array(arr, dtype=dtype)
+        lib.orc_free(p)
+        return out
+
+    N, NNZ = n.value, nnz.value
+    return dict(n=N, nnz=NNZ, row_ptr=take(rp, C.c_int64, N + 1, np.int64),
+                col_idx=take(ci, C.c_int32, NNZ, np.int32), val=take(va, C.c_double, NNZ, np.float64),
                 scale=take(sc, C.c_double, NNZ, np.float64))
 
 

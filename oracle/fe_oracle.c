@@ -269,6 +269,36 @@ static int cmp_triplet(const void* pa, const void* pb) {
   return 0;
 }
 
+/* Sort the triplets by (row, column, element, slot) and sum equal (row, column)
+ * into a CSR matrix of order n (the `sparse` constructor of Section 3). */
+static int triplets_to_csr(triplet* t, int64_t nt, int64_t n, int64_t** row_ptr, int32_t** col_idx,
+                           double** val, double** scale, int64_t* nnz_out) {
+  qsort(t, (size_t)nt, sizeof(triplet), cmp_triplet);
+  int64_t nnz = 0;
+  for (int64_t i = 0; i < nt; ++i)
+    if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) ++nnz;
+  *row_ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  *col_idx = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+  *val = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+  *scale = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+  if (!*row_ptr || !*col_idx || !*val || !*scale) return ORC_ERR_NOMEM;
+  int64_t j = -1;
+  for (int64_t i = 0; i < nt; ++i) {
+    if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) {
+      ++j;
+      (*col_idx)[j] = (int32_t)t[i].col;
+      (*val)[j] = 0.0;
+      (*scale)[j] = 0.0;
+      (*row_ptr)[t[i].row + 1] += 1;
+    }
+    (*val)[j] += t[i].v;
+    (*scale)[j] += t[i].s;
+  }
+  for (int64_t r = 0; r < n; ++r) (*row_ptr)[r + 1] += (*row_ptr)[r];
+  *nnz_out = nnz;
+  return ORC_OK;
+}
+
 /*
  * Full assembly (Algorithm 2 followed by `sparse`). q is d x nq (q[c*nq + v]),
  * me is (d+1) x nme (me[a*nme + k]). The result is a CSR matrix of order
@@ -315,35 +345,92 @@ int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, cons
       }
   }
   if (rc) { free(t); return rc; }
-  qsort(t, (size_t)nt, sizeof(triplet), cmp_triplet);
-  int64_t nnz = 0;
-  for (int64_t i = 0; i < nt; ++i)
-    if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) ++nnz;
-  *row_ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
-  *col_idx = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
-  *val = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
-  *scale = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
-  if (!*row_ptr || !*col_idx || !*val || !*scale) { free(t); return ORC_ERR_NOMEM; }
-  int64_t j = -1;
-  for (int64_t i = 0; i < nt; ++i) {
-    if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) {
-      ++j;
-      (*col_idx)[j] = (int32_t)t[i].col;
-      (*val)[j] = 0.0;
-      (*scale)[j] = 0.0;
-      (*row_ptr)[t[i].row + 1] += 1;
-    }
-    (*val)[j] += t[i].v;
-    (*scale)[j] += t[i].s;
-  }
-  for (int64_t r = 0; r < n; ++r) (*row_ptr)[r + 1] += (*row_ptr)[r];
+  rc = triplets_to_csr(t, nt, n, row_ptr, col_idx, val, scale, nnz_out);
   free(t);
+  if (rc) return rc;
   *n_out = n;
-  *nnz_out = nnz;
   return ORC_OK;
 }
 
 void orc_free(void* p) { free(p); }
+
+/*
+ * Measure of a (d-1)-simplex in d-space with vertices X (d vertices x d coordinates):
+ * sqrt(det(B^T B)) / (d-1)!, B the d x (d-1) matrix of edge vectors q^i - q^0 (the
+ * Gram determinant; for a segment its length, for a triangle half the parallelogram).
+ */
+int orc_facet(int d, const double* X, double* meas) {
+  const int k = d - 1;
+  if (k < 1 || k > 2) return ORC_ERR_ARG;
+  double B[3][2], M[2][2];
+  for (int c = 0; c < d; ++c)
+    for (int i = 0; i < k; ++i) B[c][i] = X[(i + 1) * d + c] - X[c];
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int c = 0; c < d; ++c) s += B[c][i] * B[c][j];
+      M[i][j] = s;
+    }
+  const double g = (k == 1) ? M[0][0] : M[0][0] * M[1][1] - M[0][1] * M[1][0];
+  *meas = sqrt(g) / factorial(k);
+  if (!(*meas > 0.0) || !isfinite(*meas)) return ORC_ERR_DEGENERATE;
+  return ORC_OK;
+}
+
+/*
+ * Boundary mass / weighted mass: facets (d rows, 0-based) of dimension k = d - 1;
+ * local entries int_K w phi_b phi_a by the magic formula with k in place of d and w
+ * P1-interpolated (COEF_P1) or per facet (COEF_P0); kind ORC_MASS or ORC_WMASS.
+ */
+int orc_assemble_boundary(int kind, int d, int64_t nq, int64_t nf, const double* q, const int32_t* fa,
+                          int c1_kind, const double* c1, int64_t* n_out, int64_t* nnz_out,
+                          int64_t** row_ptr, int32_t** col_idx, double** val, double** scale,
+                          int64_t* bad_id) {
+  *bad_id = -1;
+  if (d < 2 || d > 3 || (kind != ORC_MASS && kind != ORC_WMASS)) return ORC_ERR_ARG;
+  const int k = d - 1, nv = d, ns = nv * nv;
+  triplet* t = (triplet*)malloc((size_t)(nf * ns > 0 ? nf * ns : 1) * sizeof(triplet));
+  if (!t) return ORC_ERR_NOMEM;
+  double X[9], w[3];
+  int rc = ORC_OK;
+  for (int64_t f = 0; f < nf && rc == ORC_OK; ++f) {
+    for (int a = 0; a < nv; ++a) {
+      const int32_t v = fa[(int64_t)a * nf + f];
+      if (v < 0 || v >= nq) { *bad_id = f; rc = ORC_ERR_INDEX; break; }
+      for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
+      w[a] = (kind == ORC_MASS || c1_kind == ORC_COEF_NONE) ? 1.0
+             : (c1_kind == ORC_COEF_SCALAR) ? c1[0]
+             : (c1_kind == ORC_COEF_P0) ? c1[f] : c1[v];
+    }
+    if (rc) break;
+    double meas;
+    rc = orc_facet(d, X, &meas);
+    if (rc) { *bad_id = f; break; }
+    for (int b = 0; b < nv; ++b)
+      for (int a = 0; a < nv; ++a) {
+        double s = 0.0, sa = 0.0;
+        int n[4];
+        for (int g = 0; g < nv; ++g) {
+          for (int i = 0; i < nv; ++i) n[i] = (i == a) + (i == b) + (i == g);
+          const double tg = w[g] * orc_magic(k, n, meas);  /* int w_g lambda_g lambda_a lambda_b */
+          s += tg;
+          sa += fabs(tg);
+        }
+        triplet* p = &t[f * ns + b * nv + a];
+        p->row = fa[(int64_t)a * nf + f];
+        p->col = fa[(int64_t)b * nf + f];
+        p->k = f;
+        p->slot = b * nv + a;
+        p->v = s;
+        p->s = sa;
+      }
+  }
+  if (rc) { free(t); return rc; }
+  rc = triplets_to_csr(t, nf * ns, nq, row_ptr, col_idx, val, scale, nnz_out);
+  free(t);
+  *n_out = nq;
+  return rc;
+}
 
 /*
  * Loss L = u^T K(w) v for the stiffness matrix with per-element coefficient w

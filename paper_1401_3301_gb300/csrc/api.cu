@@ -11,6 +11,8 @@ int fe_launch_scalar_f32(fe_pattern_s* h, int kind, const double* q, const void*
                          void* vals, cudaStream_t s);
 int fe_launch_stiff_f64x(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals,
                          cudaStream_t s);
+int fe_launch_boundary(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, int prec,
+                       void* vals, cudaStream_t s);
 int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_kind, const void* mu,
                    int mu_kind, int prec, void* vals, cudaStream_t s);
 int fe_launch_backward(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* u,
@@ -210,6 +212,11 @@ static int check_common(fe_pattern_h h, const double* q, int32_t prec, const voi
 
 static int scalar_call(fe_pattern_h h, int kind, const double* q, const void* w, int32_t w_kind,
                        int32_t prec, void* vals, void* stream) {
+  if (h && h->kdim != h->d) {  // boundary facets: mass and weighted mass only
+    FE_TRY(check_common(h, q, prec, vals));
+    if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
+    return fe_launch_boundary(h, kind, q, w, w_kind, prec, vals, (cudaStream_t)stream);
+  }
   if (prec == FE_F64X && kind == 3) {  // stiffness only
     if (!h || !q || !vals || h->m != 1) return FE_ERR_ARG;
     if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;

@@ -1,0 +1,235 @@
+// Boundary (facet) mass and weighted mass: (d-1)-simplices in d-space, for the
+// Neumann and Robin terms the paper's remark after Algorithm 6 mentions. The local
+// matrices are those of Section 4.1 with the facet's own dimension k = d - 1 in the
+// magic formula (Eq. MagicFormula):
+//   mass:          |K| k!/(k+2)! (1 + delta_ab)
+//   P1 weighted:   |K| k!/(k+3)! (1 + delta_ab)(w^s + w_a + w_b)
+//   P0 weighted:   w_K times the mass
+// and |K| the facet measure: the length of a segment (2D), half the norm of the
+// cross product of two edges of a triangle (3D), i.e. sqrt(det(B^T B)) / k!.
+// Same chunk plan and fixed-order sums as the volume kernels.
+#include "assemble_impl.cuh"
+#include "profile.cuh"
+
+namespace fe {
+namespace {
+
+template <int D, class T, int KIND, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_chunk_boundary(StagedArgs A, T* __restrict__ vals,
+                                                            void* __restrict__ partials) {
+  constexpr int KD = D - 1, NV = D, NP = Pairs<KD>::n;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t c = blockIdx.x;
+  const int64_t e0 = c * A.chunk;
+  const int ne = (int)min((int64_t)A.chunk, A.nme - e0);
+  const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
+  const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
+  const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
+  const StagedSmem S = boundary_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, R.total);
+    bulk_copy_g2s(smem, A.rec + (int64_t)A.rec_off16[c] * 16, R.total, &bar);
+  }
+  __syncthreads();
+  const bool landed = __syncthreads_and(mbar_wait_bounded(&bar, 0, kBarrierSpin));
+  if (!landed) {
+    if (threadIdx.x == 0) {
+      fe_report(A.st, FE_ERR_TIMEOUT, e0);
+      mbar_wait_bounded(&bar, 0, kBarrierSpin);
+    }
+    return;
+  }
+  const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
+  const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
+  const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
+  const uint16_t* le_off = (const uint16_t*)(smem + R.le_off);
+  const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
+  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  T* Kd = (T*)(smem + S.kd);
+  T* Ko = (T*)(smem + S.ko);
+  T* wl = (T*)(smem + S.w);
+
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int64_t vid = lv_vid[u];
+    double x[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = __ldg(A.q + k * A.nq + vid);
+    if constexpr (sizeof(T) == 8) {
+      double* xs = (double*)(smem + S.q) + (D == 3 ? 4 : 2) * u;
+      ((double2*)xs)[0] = make_double2(x[0], x[1]);
+      if constexpr (D == 3) xs[2] = x[2];
+    } else {
+      float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < D; ++k) split_f64(x[k], h[k], l[k]);
+      float4* xs = (float4*)(smem + S.q) + (D == 3 ? 2 : 1) * u;
+      if constexpr (D == 3) {
+        xs[0] = make_float4(h[0], h[1], h[2], 0.f);
+        xs[1] = make_float4(l[0], l[1], l[2], 0.f);
+      } else {
+        xs[0] = make_float4(h[0], h[1], l[0], l[1]);
+      }
+    }
+    if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
+    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
+  }
+  __syncthreads();
+
+  const bool has_coef = A.w_kind != FE_COEF_NONE && KIND != K_WMASS_P1;
+  for (int el = threadIdx.x; el < ne; el += THREADS) {
+    int lv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
+    T e[KD][D];  // edge vectors from vertex 0
+    if constexpr (sizeof(T) == 8) {
+      double x[NV][D];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const double* xs = (const double*)(smem + S.q) + (D == 3 ? 4 : 2) * lv[a];
+        const double2 xy = ((const double2*)xs)[0];
+        x[a][0] = xy.x;
+        x[a][1] = xy.y;
+        if constexpr (D == 3) x[a][2] = xs[2];
+      }
+#pragma unroll
+      for (int i = 0; i < KD; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) e[i][k] = x[i + 1][k] - x[0][k];
+    } else {
+      float xh[NV][D], xl[NV][D];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lv[a];
+        const float4 h = xs[0];
+        if constexpr (D == 3) {
+          const float4 l = xs[1];
+          xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
+          xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
+        } else {
+          xh[a][0] = h.x; xh[a][1] = h.y;
+          xl[a][0] = h.z; xl[a][1] = h.w;
+        }
+      }
+      // correctly rounded edges from the split coordinates
+#pragma unroll
+      for (int i = 0; i < KD; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const df s = two_sum(xh[i + 1][k], -xh[0][k]);
+          e[i][k] = __fadd_rn(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][k], xl[0][k])));
+        }
+    }
+    T meas;  // facet measure |K|
+    if constexpr (D == 2) {
+      meas = sqrt(e[0][0] * e[0][0] + e[0][1] * e[0][1]);
+    } else {
+      const T nx = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+      const T ny = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+      const T nz = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+      meas = T(0.5) * sqrt(nx * nx + ny * ny + nz * nz);
+    }
+    if (!det_ok(meas)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+      meas = T(1);
+    }
+    T diag[NV], off[NP];
+    if constexpr (KIND == K_WMASS_P1) {
+      T wv[NV], ws = T(0);
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        wv[a] = wl[lv[a]];
+        ws += wv[a];
+      }
+      const T base = meas * T((double)factorial(KD) / (double)factorial(KD + 3));
+#pragma unroll
+      for (int a = 0; a < NV; ++a) diag[a] = T(2) * base * (ws + T(2) * wv[a]);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) off[p] = base * (ws + wv[Pairs<KD>::a(p)] + wv[Pairs<KD>::b(p)]);
+    } else {
+      T m = meas * T(1.0 / ((KD + 1) * (KD + 2)));
+      if (has_coef) m *= elem_coef<T>(A.w, A.w_kind, A.order, e0 + el);
+#pragma unroll
+      for (int a = 0; a < NV; ++a) diag[a] = T(2) * m;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) off[p] = m;
+    }
+#pragma unroll
+    for (int a = 0; a < NV; ++a) Kd[el * NV + a] = diag[a];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Ko[el * NP + p] = off[p];
+  }
+  __syncthreads();
+
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int s = lv_off[u], t = lv_off[u + 1];
+    Acc<T> acc(Kd[inc_v[s]]);
+    for (int j = s + 1; j < t; ++j) acc.add(Kd[inc_v[j]]);
+    const int32_t dst = lv_dst[u];
+    if (dst >= 0) vals[dst] = acc.value();
+    else acc.store_partial(partials, -1 - (int64_t)dst);
+  }
+  for (int u = threadIdx.x; u < nle; u += THREADS) {
+    const int s = le_off[u], t = le_off[u + 1];
+    Acc<T> acc(Ko[inc_e[s] >> 1]);
+    for (int j = s + 1; j < t; ++j) acc.add(Ko[inc_e[j] >> 1]);
+    const int32_t dst = le_dst[2 * u];
+    if (dst >= 0) {
+      const T val = acc.value();
+      vals[dst] = val;
+      vals[le_dst[2 * u + 1]] = val;
+    } else {
+      acc.store_partial(partials, -1 - (int64_t)dst);
+    }
+  }
+}
+
+template <int D, class T, int KIND>
+int launch(fe_pattern_s* h, const StagedArgs& A, T* vals, cudaStream_t s) {
+  constexpr int THREADS = 256;
+  const StagedSmem L = boundary_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
+  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  auto kern = k_chunk_boundary<D, T, KIND, THREADS>;
+  static size_t configured = 0;
+  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_PROF_BEGIN(h, FE_K_CHUNK, s);
+  kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, h->partials);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_PROF_END(h, FE_K_CHUNK, s);
+  const int64_t nsh = h->nsh_v + h->nsh_e;
+  if (nsh > 0) {
+    FE_PROF_BEGIN(h, FE_K_FIXUP, s);
+    k_fixup_scalar<T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->partials, vals);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_PROF_END(h, FE_K_FIXUP, s);
+  }
+  return FE_OK;
+}
+
+template <class T>
+int dispatch(fe_pattern_s* h, int kind, const StagedArgs& A, T* vals, cudaStream_t s) {
+  if (h->d == 3) {
+    if (kind == K_MASS) return launch<3, T, K_MASS>(h, A, vals, s);
+    if (kind == K_WMASS_P1) return launch<3, T, K_WMASS_P1>(h, A, vals, s);
+    return launch<3, T, K_WMASS_P0>(h, A, vals, s);
+  }
+  if (kind == K_MASS) return launch<2, T, K_MASS>(h, A, vals, s);
+  if (kind == K_WMASS_P1) return launch<2, T, K_WMASS_P1>(h, A, vals, s);
+  return launch<2, T, K_WMASS_P0>(h, A, vals, s);
+}
+
+}  // namespace
+}  // namespace fe
+
+int fe_launch_boundary(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, int prec,
+                       void* vals, cudaStream_t s) {
+  using namespace fe;
+  if (h->strategy != FE_REASM_CHUNKED || kind == K_STIFF) return FE_ERR_ARG;
+  StagedArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, w, w_kind,
+               h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
+  if (prec == FE_F64) return dispatch<double>(h, kind, A, (double*)vals, s);
+  return dispatch<float>(h, kind, A, (float*)vals, s);
+}

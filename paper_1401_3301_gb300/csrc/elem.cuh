@@ -276,6 +276,12 @@ __host__ __device__ constexpr int factorial(int n) { return n <= 1 ? 1 : n * fac
 template <int D>
 struct Pairs;
 template <>
+struct Pairs<1> {
+  static constexpr int n = 1;
+  __device__ static constexpr int a(int) { return 0; }
+  __device__ static constexpr int b(int) { return 1; }
+};
+template <>
 struct Pairs<2> {
   static constexpr int n = 3;
   __device__ static constexpr int a(int p) { return p == 2 ? 1 : 0; }

@@ -41,6 +41,7 @@ void fe_prof_free(struct fe_pattern_s* h);
 struct fe_pattern_s {
   int d = 0, m = 1, nv = 0, npair = 0, flags = 0, strategy = FE_REASM_CHUNKED;
   int threads = 256;                // threads per block of the chunked scalar kernel
+  int kdim = 0;                     // element dimension: d (volume) or d - 1 (boundary facets)
   int64_t nq = 0, nme = 0, n = 0, nnz_s = 0, nnz = 0;
   int32_t* me_int = nullptr;        // (d+1) x nme, internal element order
   int32_t* order = nullptr;         // internal -> input element id

@@ -91,16 +91,16 @@ __device__ __forceinline__ uint64_t spread_bits(uint64_t x, int d) {
 }
 
 __global__ void k_morton_keys(const double* q, int64_t nq, const int32_t* me, int64_t nme, int d,
-                              const double* bbox, int qbits, const int32_t* group, uint64_t* keys,
-                              uint32_t* vals) {
+                              int nv, const double* bbox, int qbits, const int32_t* group,
+                              uint64_t* keys, uint32_t* vals) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nme) return;
   const double scale = (double)(1u << qbits);
   uint64_t code = 0;
   for (int c = 0; c < d; ++c) {
     double s = 0.0;
-    for (int a = 0; a <= d; ++a) s += q[(int64_t)c * nq + me[(int64_t)a * nme + k]];
-    s /= (double)(d + 1);
+    for (int a = 0; a < nv; ++a) s += q[(int64_t)c * nq + me[(int64_t)a * nme + k]];
+    s /= (double)nv;
     const double lo = bbox[c], hi = bbox[d + c];
     double t = (hi > lo) ? (s - lo) / (hi - lo) : 0.0;
     t = fmin(fmax(t, 0.0), 1.0);
@@ -684,7 +684,7 @@ int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s) {
 
 namespace {
 int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
-                    const int32_t* group, int group_bits);
+                    const int32_t* group, int group_bits, int kdim);
 }  // namespace
 
 extern "C" int fe_batch_pattern(const fe_mesh* meshes, int32_t count, int32_t m, int32_t flags,
@@ -723,7 +723,7 @@ extern "C" int fe_batch_pattern(const fe_mesh* meshes, int32_t count, int32_t m,
     FE_CUDA_TRY(cudaGetLastError());
   }
   fe_mesh u{d, voff[count], eoff[count], qu, meu};
-  FE_TRY(fe_pattern_impl(&u, m, flags, stream, out, grp, bitlen((uint64_t)count)));
+  FE_TRY(fe_pattern_impl(&u, m, flags, stream, out, grp, bitlen((uint64_t)count), d));
   fe_pattern_s* h = *out;
   h->batch_voff = voff;
   h->batch_eoff = eoff;
@@ -784,31 +784,39 @@ void free_plan(fe_pattern_s* h) {
 }
 
 int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
-                    const int32_t* group, int group_bits);
+                    const int32_t* group, int group_bits, int kdim);
 }  // namespace
 
 extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
                           fe_pattern_h* out) {
-  return fe_pattern_impl(mesh, m, flags, stream, out, nullptr, 0);
+  if (!mesh) return FE_ERR_ARG;
+  return fe_pattern_impl(mesh, m, flags, stream, out, nullptr, 0, mesh->d);
+}
+
+extern "C" int fe_boundary_pattern(const fe_mesh* facets, int32_t flags, void* stream, fe_pattern_h* out) {
+  if (!facets) return FE_ERR_ARG;
+  return fe_pattern_impl(facets, 1, flags, stream, out, nullptr, 0, facets->d - 1);
 }
 
 namespace {
 int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
-                    const int32_t* group, int group_bits) {
+                    const int32_t* group, int group_bits, int kdim) {
   if (!mesh || !out) return FE_ERR_ARG;
   *out = nullptr;
   const int d = mesh->d;
   if (d != 2 && d != 3) return FE_ERR_ARG;
   if (m != 1 && m != d) return FE_ERR_ARG;
   if (mesh->nq < 1 || mesh->nme < 1 || !mesh->q || !mesh->me) return FE_ERR_ARG;
-  const int nv = d + 1, S = nv * nv;
+  if (kdim != d && !(kdim == d - 1 && m == 1)) return FE_ERR_ARG;
+  const int nv = kdim + 1, S = nv * nv;
   const int64_t nq = mesh->nq, nme = mesh->nme;
   if (nq > INT32_MAX / m || nme > INT32_MAX / S) return FE_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   fe_pattern_s* h = new fe_pattern_s();
-  h->d = d; h->m = m; h->nv = nv; h->npair = nv * d / 2; h->flags = flags;
+  h->d = d; h->m = m; h->nv = nv; h->npair = nv * (nv - 1) / 2; h->flags = flags;
+  h->kdim = kdim;
   h->nq = nq; h->nme = nme; h->n = (int64_t)m * nq;
-  h->chunk = default_chunk(d, m, flags);
+  h->chunk = kdim == d ? default_chunk(d, m, flags) : default_chunk(2, 1, flags);
   int rc = FE_OK;
   dev_tmp tmp;
   do {
@@ -854,7 +862,7 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
       if (qbits > 21) qbits = 21;
       const int gbits = group ? group_bits : 0;
       if (qbits * d + gbits > 64) qbits = (64 - gbits) / d;
-      k_morton_keys<<<fe_grid(nme, T), T, 0, s>>>(mesh->q, nq, mesh->me, nme, d, bb, qbits, group,
+      k_morton_keys<<<fe_grid(nme, T), T, 0, s>>>(mesh->q, nq, mesh->me, nme, d, nv, bb, qbits, group,
                                                  sb.k0, sb.v0);
       if (cudaGetLastError() != cudaSuccess) { rc = FE_ERR_CUDA; break; }
       if ((rc = fe_radix_sort(nme, qbits * d + (group ? group_bits : 0), &sb, &keys, &vals, s))) break;
@@ -907,8 +915,10 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
     // shrink the chunk until the worst-case block's shared memory fits (227 KB)
     for (;;) {
       if ((rc = build_chunk_plan(h, &sb, tmp, s))) break;
-      const uint32_t need = fe::plan_smem_worst(d, m, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,
-                                                (uint32_t)h->chunk);
+      const uint32_t need = kdim == d
+          ? fe::plan_smem_worst(d, m, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->chunk)
+          : fe::boundary_smem(d, 8, true, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,
+                              (uint32_t)h->chunk).total;
       if (need <= 227u * 1024u || h->chunk <= 32) break;
       if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
       free_plan(h);

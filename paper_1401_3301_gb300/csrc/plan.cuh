@@ -79,6 +79,24 @@ __host__ __device__ __forceinline__ ElasSmem elas_smem(int D, int sizeT, uint32_
   return L;
 }
 
+// Shared-memory layout of the boundary (facet) kernel: D-dimensional coordinates,
+// D vertices and D (D-1)/2 edges per facet.
+__host__ __device__ __forceinline__ StagedSmem boundary_smem(int D, int sizeT, bool p1_weight,
+                                                             uint32_t rec_max, uint32_t max_lv,
+                                                             uint32_t chunk) {
+  const uint32_t nv = D, np = D * (D - 1) / 2;
+  StagedSmem L;
+  uint32_t o = pad16(rec_max);
+  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
+  L.w = o;    o += p1_weight ? pad16(sizeT * max_lv) : 0u;
+  L.lvid = o; o += pad16(2u * nv * chunk);
+  L.kd = o;   o += pad16(sizeT * nv * chunk);
+  L.ko = o;   o += pad16(sizeT * np * chunk);
+  L.sc = o;
+  L.total = o;
+  return L;
+}
+
 // Largest shared-memory footprint of any chunked kernel for a plan (FP64, with a P1
 // coefficient): the plan build shrinks the chunk until it fits in one block.
 __host__ __device__ __forceinline__ uint32_t plan_smem_worst(int D, int m, uint32_t rec_max,

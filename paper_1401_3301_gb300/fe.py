@@ -61,6 +61,7 @@ def lib() -> C.CDLL:
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff_vjp.argtypes = [P, P, P, I32, P, P, P, I32, P]
         L.fe_batch_pattern.argtypes = [P, I32, I32, I32, P, P]
+        L.fe_boundary_pattern.argtypes = [P, I32, P, P]
         L.fe_pattern_set_threads.argtypes = [P, I32]
         L.fe_batch_offsets.argtypes = [P, P, P, P]
         L.fe_batch_count.argtypes = [P, P]
@@ -75,7 +76,8 @@ def lib() -> C.CDLL:
                      "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward",
                      "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
-                     "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads"):
+                     "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads",
+                     "fe_boundary_pattern"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -224,6 +226,18 @@ def _meshes(qs, mes):
         arr[b] = _Mesh(q.shape[0], q.shape[1], me.shape[1], _dev(q, torch.float64, "q").value,
                        _dev(me, torch.int32, "me").value)
     return arr
+
+
+def fe_boundary_pattern(q: torch.Tensor, facets: torch.Tensor, flags: int = 0, stream=None) -> Pattern:
+    """Pattern of a mesh of boundary facets ((d-1)-simplices in d-space, d rows of vertices)."""
+    d = q.shape[0]
+    if facets.shape[0] != d:
+        raise ValueError("facets must be (d, nfacets)")
+    mesh = _Mesh(d, q.shape[1], facets.shape[1], _dev(q, torch.float64, "q").value,
+                 _dev(facets, torch.int32, "facets").value)
+    h = C.c_void_p()
+    _check(lib().fe_boundary_pattern(C.byref(mesh), flags, _stream(stream), C.byref(h)))
+    return Pattern(h)
 
 
 def fe_batch_pattern(qs: list, mes: list, m: int = 1, flags: int = 0, stream=None) -> Pattern:

@@ -156,6 +156,17 @@ def kuhn_cube_mesh(N: int, seed: int = 0, jitter: float = 0.15, perm_vertices: b
     return _finish(3, q, me, seed, jitter, interior, 1.0 / N, perm_vertices, perm_elements)
 
 
+def boundary_facets(mesh: Mesh) -> np.ndarray:
+    """Facets (d-1 simplices) that belong to exactly one element: (d, nfacets) int32,
+    vertex indices into the same q, in the order of first appearance."""
+    d, me = mesh.d, mesh.me
+    faces = np.concatenate([np.delete(me, drop, axis=0) for drop in range(d + 1)], axis=1).T
+    key = np.sort(faces, axis=1)
+    _, first, counts = np.unique(key, axis=0, return_index=True, return_counts=True)
+    keep = np.sort(first[counts == 1])
+    return np.ascontiguousarray(faces[keep].T.astype(np.int32))
+
+
 def vertex_weights(seed: int, nq: int) -> np.ndarray:
     """Per-vertex weight w = exp(g), g ~ N(0, 1) iid."""
     return np.exp(normal(stream_key(seed, VERT_WEIGHT), nq))

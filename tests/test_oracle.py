@@ -337,3 +337,37 @@ def test_oracle_reports_bad_input():
     with pytest.raises(oracle.OracleError) as e:
         oracle.assemble(oracle.STIFF, q, m.me)
     assert e.value.code == 3
+
+
+# ---------------------------------------------------------------- boundary (facet) mass
+def test_facet_measure_against_heron_and_length():
+    rng = np.random.default_rng(20)
+    for _ in range(10):
+        X = rng.normal(size=(3, 3))
+        a, b, c = (np.linalg.norm(X[i] - X[j]) for i, j in ((0, 1), (1, 2), (2, 0)))
+        s = 0.5 * (a + b + c)
+        heron = np.sqrt(s * (s - a) * (s - b) * (s - c))
+        assert oracle.facet_measure(X) == pytest.approx(heron, rel=1e-10)
+        Y = rng.normal(size=(2, 2))
+        assert oracle.facet_measure(Y) == pytest.approx(np.hypot(*(Y[1] - Y[0])), rel=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_boundary_mass_integrals(d):
+    m = meshgen.square_mesh(7, seed=21) if d == 2 else meshgen.kuhn_cube_mesh(4, seed=21)
+    fa = meshgen.boundary_facets(m)
+    M = oracle.to_dense(oracle.assemble_boundary(oracle.MASS, m.q, fa))
+    one = np.ones(m.nq)
+    x = m.q[0]
+    assert one @ M @ one == pytest.approx(4.0 if d == 2 else 6.0, rel=1e-13)          # perimeter / area
+    assert x @ M @ x == pytest.approx(5.0 / 3.0 if d == 2 else 7.0 / 3.0, rel=1e-12)  # int x^2 ds
+    # P1 weight w = 1 + x is integrated exactly: int (1 + x) ds = 6 (square), 6 + 3 (cube)
+    Mw = oracle.to_dense(oracle.assemble_boundary(oracle.WMASS, m.q, fa, c1=(oracle.COEF_P1, 1.0 + x)))
+    assert one @ Mw @ one == pytest.approx(6.0 if d == 2 else 9.0, rel=1e-12)
+    # element closed forms: segment |K|/6 (1 + delta), triangle |K|/12 (1 + delta)
+    X = m.q[:, fa[:, 0]].T
+    _, meas = None, oracle.facet_measure(X)
+    single = oracle.to_dense(oracle.assemble_boundary(oracle.MASS, m.q, fa[:, :1]))
+    idx = fa[:, 0]
+    np.testing.assert_allclose(single[np.ix_(idx, idx)], meas / (6.0 if d == 2 else 12.0) * (1 + np.eye(d)),
+                               rtol=1e-14)
