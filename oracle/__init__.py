@@ -49,6 +49,7 @@ def _load():
         lib.orc_stiff_loss.argtypes = [I32, I64, I64, P, P, P, P, P, P, P, P, P]
         lib.orc_facet.argtypes = [I32, P, P]
         lib.orc_assemble_boundary.argtypes = [I32, I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P]
+        lib.orc_assemble_general.argtypes = [I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P]
         lib.orc_free.argtypes = [P]
         _lib = lib
     return _lib
@@ -163,6 +164,34 @@ def assemble_boundary(kind: int, q: np.ndarray, facets: np.ndarray, c1=None) -> 
     rc = lib.orc_assemble_boundary(kind, d, nq, fa.shape[1], _ptr(q), _ptr(fa), k1, _ptr(a1),
                                    C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
                                    C.byref(sc), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+
+    def take(p, ctype, count, dtype):
+        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
+        out = np.array(arr, dtype=dtype)
+        lib.orc_free(p)
+        return out
+
+    N, NNZ = n.value, nnz.value
+    return dict(n=N, nnz=NNZ, row_ptr=take(rp, C.c_int64, N + 1, np.int64),
+                col_idx=take(ci, C.c_int32, NNZ, np.int32), val=take(va, C.c_double, NNZ, np.float64),
+                scale=take(sc, C.c_double, NNZ, np.float64))
+
+
+def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, per_element: bool) -> dict:
+    """General operator of Eq. EDP; coef is (d*d + 2d + 1,) or (d*d + 2d + 1, nme):
+    A row-major, b, c, a0. Same result dict as assemble()."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    me = np.ascontiguousarray(me, dtype=np.int32)
+    cf = np.ascontiguousarray(coef, dtype=np.float64)
+    d, nq = q.shape
+    n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
+    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    lib = _load()
+    rc = lib.orc_assemble_general(d, nq, me.shape[1], _ptr(q), _ptr(me), COEF_P0 if per_element else COEF_SCALAR,
+                                  _ptr(cf), C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
+                                  C.byref(sc), C.byref(bad))
     if rc:
         raise OracleError(rc, bad.value)
 

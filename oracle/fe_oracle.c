@@ -355,6 +355,83 @@ int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, cons
 void orc_free(void* p) { free(p); }
 
 /*
+ * General second-order operator of Eq. EDP, -div(A grad u) + div(b u) + c . grad u + a0 u,
+ * in weak form (the divergence terms integrated by parts, boundary terms left out):
+ *   a(u, v) = int (A grad u) . grad v - int u b . grad v + int (c . grad u) v + int a0 u v,
+ * with constant A, b, c, a0 on each element. The matrix entry of row i, column j is
+ * a(phi_j, phi_i), so the local entry (a, b) (test vertex a, trial vertex b) is
+ *   |K| g_a^T A g_b - (b . g_a) int phi_b + (c . g_b) int phi_a + a0 int phi_a phi_b,
+ * the integrals by the magic formula. coef holds per element (coef_kind ORC_COEF_P0,
+ * SoA: coef[j * nme + k]) or once (ORC_COEF_SCALAR: coef[j]) the d*d + 2d + 1 values
+ * A (row-major), b, c, a0.
+ */
+int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                         int coef_kind, const double* coef, int64_t* n_out, int64_t* nnz_out,
+                         int64_t** row_ptr, int32_t** col_idx, double** val, double** scale,
+                         int64_t* bad_id) {
+  *bad_id = -1;
+  if (d < 2 || d > 3) return ORC_ERR_ARG;
+  const int nv = d + 1, ns = nv * nv, nc = d * d + 2 * d + 1;
+  triplet* t = (triplet*)malloc((size_t)(nme * ns > 0 ? nme * ns : 1) * sizeof(triplet));
+  if (!t) return ORC_ERR_NOMEM;
+  double X[12], G[12], det, vol, cf[16];
+  int rc = ORC_OK;
+  for (int64_t k = 0; k < nme && rc == ORC_OK; ++k) {
+    for (int a = 0; a < nv; ++a) {
+      const int32_t v = me[(int64_t)a * nme + k];
+      if (v < 0 || v >= nq) { *bad_id = k; rc = ORC_ERR_INDEX; break; }
+      for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
+    }
+    if (rc) break;
+    rc = orc_simplex(d, X, &det, &vol, G);
+    if (rc) { *bad_id = k; break; }
+    for (int j = 0; j < nc; ++j) cf[j] = (coef_kind == ORC_COEF_P0) ? coef[(int64_t)j * nme + k] : coef[j];
+    const double* A = cf;
+    const double* bv = cf + d * d;
+    const double* cv = cf + d * d + d;
+    const double a0 = cf[d * d + 2 * d];
+    double anorm = 0.0, bn = 0.0, cn = 0.0, gn[4];
+    for (int j = 0; j < d * d; ++j) anorm += A[j] * A[j];
+    for (int i = 0; i < d; ++i) { bn += bv[i] * bv[i]; cn += cv[i] * cv[i]; }
+    anorm = sqrt(anorm); bn = sqrt(bn); cn = sqrt(cn);
+    for (int a = 0; a < nv; ++a) {
+      double s = 0.0;
+      for (int i = 0; i < d; ++i) s += G[a * d + i] * G[a * d + i];
+      gn[a] = sqrt(s);
+    }
+    for (int b = 0; b < nv; ++b)
+      for (int a = 0; a < nv; ++a) {
+        int n1[4], n2[4];
+        for (int i = 0; i < nv; ++i) { n1[i] = (i == b); n2[i] = (i == a) + (i == b); }
+        const double int_phib = orc_magic(d, n1, vol);
+        for (int i = 0; i < nv; ++i) n1[i] = (i == a);
+        const double int_phia = orc_magic(d, n1, vol);
+        const double int_ab = orc_magic(d, n2, vol);
+        double diff = 0.0, bga = 0.0, cgb = 0.0;
+        for (int i = 0; i < d; ++i) {
+          double Agb = 0.0;
+          for (int j = 0; j < d; ++j) Agb += A[i * d + j] * G[b * d + j];
+          diff += G[a * d + i] * Agb;
+          bga += bv[i] * G[a * d + i];
+          cgb += cv[i] * G[b * d + i];
+        }
+        triplet* p = &t[k * ns + b * nv + a];
+        p->row = me[(int64_t)a * nme + k];
+        p->col = me[(int64_t)b * nme + k];
+        p->k = k;
+        p->slot = b * nv + a;
+        p->v = vol * diff - bga * int_phib + cgb * int_phia + a0 * int_ab;
+        p->s = vol * gn[a] * anorm * gn[b] + bn * gn[a] * int_phib + cn * gn[b] * int_phia + fabs(a0) * int_ab;
+      }
+  }
+  if (rc) { free(t); return rc; }
+  rc = triplets_to_csr(t, nme * ns, nq, row_ptr, col_idx, val, scale, nnz_out);
+  free(t);
+  *n_out = nq;
+  return rc;
+}
+
+/*
  * Measure of a (d-1)-simplex in d-space with vertices X (d vertices x d coordinates):
  * sqrt(det(B^T B)) / (d-1)!, B the d x (d-1) matrix of edge vectors q^i - q^0 (the
  * Gram determinant; for a segment its length, for a triangle half the parallelogram).

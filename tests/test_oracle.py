@@ -371,3 +371,59 @@ def test_boundary_mass_integrals(d):
     idx = fa[:, 0]
     np.testing.assert_allclose(single[np.ix_(idx, idx)], meas / (6.0 if d == 2 else 12.0) * (1 + np.eye(d)),
                                rtol=1e-14)
+
+
+# ---------------------------------------------------------------- general operator (Eq. EDP)
+def general_coef(d, A, b, c, a0):
+    return np.concatenate([np.asarray(A, float).ravel(), b, c, [a0]])
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_general_operator_reduces_to_stiffness_and_mass(d):
+    m = meshgen.square_mesh(6, seed=30) if d == 2 else meshgen.kuhn_cube_mesh(3, seed=30)
+    z = np.zeros(d)
+    S = oracle.to_dense(oracle.assemble(oracle.STIFF, m.q, m.me))
+    G = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, np.eye(d), z, z, 0.0), False))
+    np.testing.assert_allclose(G, S, atol=1e-14)
+    M = oracle.to_dense(oracle.assemble(oracle.MASS, m.q, m.me))
+    G0 = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, np.zeros((d, d)), z, z, 2.5), False))
+    np.testing.assert_allclose(G0, 2.5 * M, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_general_operator_bilinear_form_on_linear_functions(d):
+    # v^T M u = a(u, v) exactly for P1 u = alpha.x + alpha0, v = gamma.x + gamma0 (polynomial
+    # integrands of degree <= 2 over the unit square / cube)
+    m = meshgen.square_mesh(5, seed=31) if d == 2 else meshgen.kuhn_cube_mesh(3, seed=31)
+    rng = np.random.default_rng(32)
+    A, bv, cv, a0 = rng.normal(size=(d, d)), rng.normal(size=d), rng.normal(size=d), 0.7
+    M = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, A, bv, cv, a0), False))
+    al, al0, ga, ga0 = rng.normal(size=d), 0.3, rng.normal(size=d), -0.4
+    u = al @ m.q + al0
+    v = ga @ m.q + ga0
+    mean_u = al.sum() / 2 + al0          # int_Omega u over the unit cube/square
+    mean_v = ga.sum() / 2 + ga0
+    Exx = np.full((d, d), 0.25) + np.eye(d) * (1 / 3 - 0.25)   # int x_i x_j
+    int_uv = al @ Exx @ ga + al0 * ga.sum() / 2 + ga0 * al.sum() / 2 + al0 * ga0
+    exact = (A @ al) @ ga - (bv @ ga) * mean_u + (cv @ al) * mean_v + a0 * int_uv
+    assert v @ M @ u == pytest.approx(exact, rel=1e-12)
+    # transposed orientation would differ: the operator is not symmetric
+    assert abs(u @ M @ v - exact) > 1e-6
+
+
+def test_general_operator_per_element_coefficients():
+    # constant per-element columns equal the scalar form; the matrix is linear in each
+    # element's coefficients, so two halves of a coefficient field add up
+    m = meshgen.square_mesh(5, seed=33)
+    rng = np.random.default_rng(34)
+    cf = general_coef(2, rng.normal(size=(2, 2)), rng.normal(size=2), rng.normal(size=2), 1.3)
+    S = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, False))
+    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[:, None], m.nme, 1), True))
+    np.testing.assert_allclose(P, S, atol=1e-14)
+    F = rng.normal(size=(cf.size, m.nme))
+    mask = np.arange(m.nme) % 2 == 0
+    Fa, Fb = F * mask, F * ~mask
+    T = oracle.to_dense(oracle.assemble_general(m.q, m.me, F, True))
+    Ta = oracle.to_dense(oracle.assemble_general(m.q, m.me, Fa, True))
+    Tb = oracle.to_dense(oracle.assemble_general(m.q, m.me, Fb, True))
+    np.testing.assert_allclose(Ta + Tb, T, atol=1e-13)
