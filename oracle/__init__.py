@@ -179,9 +179,10 @@ def assemble_boundary(kind: int, q: np.ndarray, facets: np.ndarray, c1=None) -> 
                 scale=take(sc, C.c_double, NNZ, np.float64))
 
 
-def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, per_element: bool) -> dict:
-    """General operator of Eq. EDP; coef is (d*d + 2d + 1,) or (d*d + 2d + 1, nme):
-    A row-major, b, c, a0. Same result dict as assemble()."""
+def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, kind: int) -> dict:
+    """General operator of Eq. EDP. coef: the d*d + 2d + 1 values A (row-major), b, c, a0,
+    as (nc,) for COEF_SCALAR, (nc, nme) for COEF_P0, (nc, nq) for COEF_P1.
+    Same result dict as assemble()."""
     q = np.ascontiguousarray(q, dtype=np.float64)
     me = np.ascontiguousarray(me, dtype=np.int32)
     cf = np.ascontiguousarray(coef, dtype=np.float64)
@@ -189,7 +190,7 @@ def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, per_elemen
     n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
     rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
     lib = _load()
-    rc = lib.orc_assemble_general(d, nq, me.shape[1], _ptr(q), _ptr(me), COEF_P0 if per_element else COEF_SCALAR,
+    rc = lib.orc_assemble_general(d, nq, me.shape[1], _ptr(q), _ptr(me), kind,
                                   _ptr(cf), C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
                                   C.byref(sc), C.byref(bad))
     if rc:

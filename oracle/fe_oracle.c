@@ -357,13 +357,19 @@ void orc_free(void* p) { free(p); }
 /*
  * General second-order operator of Eq. EDP, -div(A grad u) + div(b u) + c . grad u + a0 u,
  * in weak form (the divergence terms integrated by parts, boundary terms left out):
- *   a(u, v) = int (A grad u) . grad v - int u b . grad v + int (c . grad u) v + int a0 u v,
- * with constant A, b, c, a0 on each element. The matrix entry of row i, column j is
- * a(phi_j, phi_i), so the local entry (a, b) (test vertex a, trial vertex b) is
- *   |K| g_a^T A g_b - (b . g_a) int phi_b + (c . g_b) int phi_a + a0 int phi_a phi_b,
- * the integrals by the magic formula. coef holds per element (coef_kind ORC_COEF_P0,
- * SoA: coef[j * nme + k]) or once (ORC_COEF_SCALAR: coef[j]) the d*d + 2d + 1 values
- * A (row-major), b, c, a0.
+ *   a(u, v) = int (A grad u) . grad v - int u b . grad v + int (c . grad u) v + int a0 u v.
+ * The matrix entry of row i, column j is a(phi_j, phi_i), so the local entry (a, b)
+ * (test vertex a, trial vertex b) is
+ *   int (A g_b) . g_a - int lambda_b (b . g_a) + int lambda_a (c . g_b) + int a0 lambda_a lambda_b.
+ * Each coefficient is written on K as sum_c f(c) lambda_c: f(c) its value at local vertex
+ * c (P1, interpolated) or the element's value for every c (scalar, P0; then sum_c lambda_c = 1
+ * gives back the constant), and every integral of a product of barycentric coordinates is
+ * taken by the magic formula (Eq. MagicFormula).
+ * coef holds the nc = d*d + 2d + 1 values A (row-major), b, c, a0: once (ORC_COEF_SCALAR:
+ * coef[j]), per element (ORC_COEF_P0: coef[j * nme + k]) or per vertex (ORC_COEF_P1:
+ * coef[j * nq + v]).
+ * The condition scale of an entry is the same sum with every term replaced by its absolute
+ * bound: |A(c)|_F |g_a| |g_b|, |b(c)| |g_a|, |c(c)| |g_b|, |a0(c)| under the same integrals.
  */
 int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const int32_t* me,
                          int coef_kind, const double* coef, int64_t* n_out, int64_t* nnz_out,
@@ -371,29 +377,31 @@ int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const 
                          int64_t* bad_id) {
   *bad_id = -1;
   if (d < 2 || d > 3) return ORC_ERR_ARG;
+  if (coef_kind != ORC_COEF_SCALAR && coef_kind != ORC_COEF_P0 && coef_kind != ORC_COEF_P1)
+    return ORC_ERR_ARG;
   const int nv = d + 1, ns = nv * nv, nc = d * d + 2 * d + 1;
   triplet* t = (triplet*)malloc((size_t)(nme * ns > 0 ? nme * ns : 1) * sizeof(triplet));
   if (!t) return ORC_ERR_NOMEM;
-  double X[12], G[12], det, vol, cf[16];
+  double X[12], G[12], det, vol, cf[4][16];
   int rc = ORC_OK;
   for (int64_t k = 0; k < nme && rc == ORC_OK; ++k) {
+    int32_t vid[4];
     for (int a = 0; a < nv; ++a) {
       const int32_t v = me[(int64_t)a * nme + k];
       if (v < 0 || v >= nq) { *bad_id = k; rc = ORC_ERR_INDEX; break; }
+      vid[a] = v;
       for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
     }
     if (rc) break;
     rc = orc_simplex(d, X, &det, &vol, G);
     if (rc) { *bad_id = k; break; }
-    for (int j = 0; j < nc; ++j) cf[j] = (coef_kind == ORC_COEF_P0) ? coef[(int64_t)j * nme + k] : coef[j];
-    const double* A = cf;
-    const double* bv = cf + d * d;
-    const double* cv = cf + d * d + d;
-    const double a0 = cf[d * d + 2 * d];
-    double anorm = 0.0, bn = 0.0, cn = 0.0, gn[4];
-    for (int j = 0; j < d * d; ++j) anorm += A[j] * A[j];
-    for (int i = 0; i < d; ++i) { bn += bv[i] * bv[i]; cn += cv[i] * cv[i]; }
-    anorm = sqrt(anorm); bn = sqrt(bn); cn = sqrt(cn);
+    /* cf[c][j]: coefficient j at local vertex c */
+    for (int c = 0; c < nv; ++c)
+      for (int j = 0; j < nc; ++j)
+        cf[c][j] = coef_kind == ORC_COEF_SCALAR ? coef[j]
+                 : coef_kind == ORC_COEF_P0     ? coef[(int64_t)j * nme + k]
+                                                : coef[(int64_t)j * nq + vid[c]];
+    double gn[4];
     for (int a = 0; a < nv; ++a) {
       double s = 0.0;
       for (int i = 0; i < d; ++i) s += G[a * d + i] * G[a * d + i];
@@ -401,27 +409,45 @@ int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const 
     }
     for (int b = 0; b < nv; ++b)
       for (int a = 0; a < nv; ++a) {
-        int n1[4], n2[4];
-        for (int i = 0; i < nv; ++i) { n1[i] = (i == b); n2[i] = (i == a) + (i == b); }
-        const double int_phib = orc_magic(d, n1, vol);
-        for (int i = 0; i < nv; ++i) n1[i] = (i == a);
-        const double int_phia = orc_magic(d, n1, vol);
-        const double int_ab = orc_magic(d, n2, vol);
-        double diff = 0.0, bga = 0.0, cgb = 0.0;
-        for (int i = 0; i < d; ++i) {
-          double Agb = 0.0;
-          for (int j = 0; j < d; ++j) Agb += A[i * d + j] * G[b * d + j];
-          diff += G[a * d + i] * Agb;
-          bga += bv[i] * G[a * d + i];
-          cgb += cv[i] * G[b * d + i];
+        double v = 0.0, sc = 0.0;
+        for (int c = 0; c < nv; ++c) {
+          const double* A = cf[c];
+          const double* bv = cf[c] + d * d;
+          const double* cv = cf[c] + d * d + d;
+          const double a0 = cf[c][d * d + 2 * d];
+          int n[4];
+          for (int i = 0; i < nv; ++i) n[i] = (i == c);
+          const double i_c = orc_magic(d, n, vol);                 /* int lambda_c */
+          n[b] += 1;
+          const double i_cb = orc_magic(d, n, vol);                /* int lambda_c lambda_b */
+          n[a] += 1;
+          const double i_cab = orc_magic(d, n, vol);               /* int lambda_c lambda_a lambda_b */
+          for (int i = 0; i < nv; ++i) n[i] = (i == c) + (i == a);
+          const double i_ca = orc_magic(d, n, vol);                /* int lambda_c lambda_a */
+          double diff = 0.0, bga = 0.0, cgb = 0.0, an = 0.0, bn = 0.0, cn = 0.0;
+          for (int i = 0; i < d; ++i) {
+            double Agb = 0.0;
+            for (int j = 0; j < d; ++j) {
+              Agb += A[i * d + j] * G[b * d + j];
+              an += A[i * d + j] * A[i * d + j];
+            }
+            diff += G[a * d + i] * Agb;
+            bga += bv[i] * G[a * d + i];
+            cgb += cv[i] * G[b * d + i];
+            bn += bv[i] * bv[i];
+            cn += cv[i] * cv[i];
+          }
+          v += i_c * diff - i_cb * bga + i_ca * cgb + i_cab * a0;
+          sc += i_c * sqrt(an) * gn[a] * gn[b] + i_cb * sqrt(bn) * gn[a] + i_ca * sqrt(cn) * gn[b] +
+                i_cab * fabs(a0);
         }
         triplet* p = &t[k * ns + b * nv + a];
-        p->row = me[(int64_t)a * nme + k];
-        p->col = me[(int64_t)b * nme + k];
+        p->row = vid[a];
+        p->col = vid[b];
         p->k = k;
         p->slot = b * nv + a;
-        p->v = vol * diff - bga * int_phib + cgb * int_phia + a0 * int_ab;
-        p->s = vol * gn[a] * anorm * gn[b] + bn * gn[a] * int_phib + cn * gn[b] * int_phia + fabs(a0) * int_ab;
+        p->v = v;
+        p->s = sc;
       }
   }
   if (rc) { free(t); return rc; }

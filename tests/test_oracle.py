@@ -383,10 +383,10 @@ def test_general_operator_reduces_to_stiffness_and_mass(d):
     m = meshgen.square_mesh(6, seed=30) if d == 2 else meshgen.kuhn_cube_mesh(3, seed=30)
     z = np.zeros(d)
     S = oracle.to_dense(oracle.assemble(oracle.STIFF, m.q, m.me))
-    G = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, np.eye(d), z, z, 0.0), False))
+    G = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, np.eye(d), z, z, 0.0), oracle.COEF_SCALAR))
     np.testing.assert_allclose(G, S, atol=1e-14)
     M = oracle.to_dense(oracle.assemble(oracle.MASS, m.q, m.me))
-    G0 = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, np.zeros((d, d)), z, z, 2.5), False))
+    G0 = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, np.zeros((d, d)), z, z, 2.5), oracle.COEF_SCALAR))
     np.testing.assert_allclose(G0, 2.5 * M, atol=1e-15)
 
 
@@ -397,7 +397,7 @@ def test_general_operator_bilinear_form_on_linear_functions(d):
     m = meshgen.square_mesh(5, seed=31) if d == 2 else meshgen.kuhn_cube_mesh(3, seed=31)
     rng = np.random.default_rng(32)
     A, bv, cv, a0 = rng.normal(size=(d, d)), rng.normal(size=d), rng.normal(size=d), 0.7
-    M = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, A, bv, cv, a0), False))
+    M = oracle.to_dense(oracle.assemble_general(m.q, m.me, general_coef(d, A, bv, cv, a0), oracle.COEF_SCALAR))
     al, al0, ga, ga0 = rng.normal(size=d), 0.3, rng.normal(size=d), -0.4
     u = al @ m.q + al0
     v = ga @ m.q + ga0
@@ -417,13 +417,53 @@ def test_general_operator_per_element_coefficients():
     m = meshgen.square_mesh(5, seed=33)
     rng = np.random.default_rng(34)
     cf = general_coef(2, rng.normal(size=(2, 2)), rng.normal(size=2), rng.normal(size=2), 1.3)
-    S = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, False))
-    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[:, None], m.nme, 1), True))
+    S = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, oracle.COEF_SCALAR))
+    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[:, None], m.nme, 1), oracle.COEF_P0))
     np.testing.assert_allclose(P, S, atol=1e-14)
     F = rng.normal(size=(cf.size, m.nme))
     mask = np.arange(m.nme) % 2 == 0
     Fa, Fb = F * mask, F * ~mask
-    T = oracle.to_dense(oracle.assemble_general(m.q, m.me, F, True))
-    Ta = oracle.to_dense(oracle.assemble_general(m.q, m.me, Fa, True))
-    Tb = oracle.to_dense(oracle.assemble_general(m.q, m.me, Fb, True))
+    T = oracle.to_dense(oracle.assemble_general(m.q, m.me, F, oracle.COEF_P0))
+    Ta = oracle.to_dense(oracle.assemble_general(m.q, m.me, Fa, oracle.COEF_P0))
+    Tb = oracle.to_dense(oracle.assemble_general(m.q, m.me, Fb, oracle.COEF_P0))
     np.testing.assert_allclose(Ta + Tb, T, atol=1e-13)
+
+
+def _gauss_cube(d, npts=3):
+    """Tensor Gauss-Legendre rule on [0, 1]^d: exact for degree <= 2 npts - 1 per variable."""
+    x, w = np.polynomial.legendre.leggauss(npts)
+    x, w = (x + 1) / 2, w / 2
+    grids = np.meshgrid(*([x] * d), indexing="ij")
+    wts = np.prod(np.meshgrid(*([w] * d), indexing="ij"), axis=0)
+    return np.stack([g.ravel() for g in grids]), wts.ravel()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_general_operator_p1_coefficients_by_quadrature(d):
+    # Linear coefficient fields (exactly P1) and linear u, v: every integrand of a(u, v)
+    # is a polynomial of degree <= 3, integrated exactly over the unit square / cube by
+    # 3-point tensor Gauss quadrature, independent of the magic formula.
+    m = meshgen.square_mesh(4, seed=35) if d == 2 else meshgen.kuhn_cube_mesh(3, seed=35)
+    rng = np.random.default_rng(36)
+    nc = d * d + 2 * d + 1
+    slope, base = rng.normal(size=(nc, d)), rng.normal(size=nc)
+    coef_at = lambda x: slope @ x + base[:, None]           # (nc, npoints), linear in x
+    cf = coef_at(m.q)                                        # nodal values (nc, nq)
+    M = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, oracle.COEF_P1))
+    al, al0, ga, ga0 = rng.normal(size=d), 0.3, rng.normal(size=d), -0.4
+    u, v = al @ m.q + al0, ga @ m.q + ga0
+    X, W = _gauss_cube(d)
+    C = coef_at(X)
+    A = C[: d * d].reshape(d, d, -1)
+    bq, cq, a0 = C[d * d: d * d + d], C[d * d + d: nc - 1], C[nc - 1]
+    uq, vq = al @ X + al0, ga @ X + ga0
+    integrand = (np.einsum("ijp,j,i->p", A, al, ga) - uq * (ga @ bq) + (al @ cq) * vq + a0 * uq * vq)
+    assert v @ M @ u == pytest.approx(W @ integrand, rel=1e-12)
+
+
+def test_general_operator_p1_constant_fields_match_scalar():
+    m = meshgen.square_mesh(5, seed=37)
+    cf = general_coef(2, [[1.0, 0.2], [-0.4, 2.0]], [0.3, -1.0], [0.5, 0.25], 1.5)
+    S = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, oracle.COEF_SCALAR))
+    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[:, None], m.nq, 1), oracle.COEF_P1))
+    np.testing.assert_allclose(P, S, atol=1e-14)
