@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
     ap.add_argument("--workload", default="stiffness",
-                    choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff"],
+                    choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general"],
                     help="stiffness (default, the headline); the others print one JSON line each "
                          "for the other configurations of the hot path")
     return ap.parse_args()
@@ -432,6 +432,30 @@ def run_other(args):
         out.update(metric=f"3D P1 {'mass' if args.workload == 'mass' else 'weighted mass (P1 vertex weight)'} "
                           "Mtets/s, fixed pattern", unit="Mtets/s",
                    config=workload_config(args.N))
+    elif args.workload == "general":
+        # convection-diffusion-reaction operator (non-symmetric), per-element and per-vertex
+        # coefficient sets of 16 values each
+        import numpy as np
+        m = meshgen.kuhn_cube_mesh(args.N, seed=0)
+        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        p = fe.fe_pattern(q, me)
+        c0 = meshgen.general_coefficients(0, 3, m.nme)
+        c1 = meshgen.general_coefficients(1, 3, m.nq)
+        order = p.element_order().long().cpu().numpy()
+        c0i = np.ascontiguousarray(c0[order])
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            res = {}
+            for label, arr, kind in (("p0_internal", c0i, fe.COEF_P0_INTERNAL), ("p0", c0, fe.COEF_P0),
+                                     ("p1", c1, fe.COEF_P1)):
+                cf = torch.from_numpy(arr).cuda().to(T)
+                med, mean = _timed(lambda: fe.fe_assemble_general(p, q, cf, kind, prec=prec, vals=vals), K, W,
+                                   flush)
+                p.check()
+                res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+            out["forms"][name] = {"value": res["p0_internal"]["value"], "coefficients": res}
+        out.update(metric="3D P1 general operator -div(A grad u) + div(b u) + c.grad u + a0 u (non-symmetric) "
+                          "Mtets/s, fixed pattern", unit="Mtets/s", config=workload_config(args.N))
     elif args.workload == "elas":
         N = 80 if args.N == 100 else args.N
         m = meshgen.kuhn_cube_mesh(N, seed=0)

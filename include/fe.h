@@ -244,6 +244,31 @@ int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t l
                      const void* mu, int32_t mu_kind, int32_t prec, void* vals, void* stream);
 
 /*
+ * fe_assemble_general -- the general second-order operator of Eq. EDP,
+ *   -div(A grad u) + div(b u) + c . grad u + a0 u,
+ * which the paper states its algorithms extend to (remark after Eq. MagicFormula).
+ * Weak form with the divergence terms on the test function and no boundary terms:
+ *   a(u, v) = int (A grad u).grad v - int u b.grad v + int (c.grad u) v + int a0 u v,
+ * entry (i, j) = a(phi_j, phi_i), NOT symmetric. Local entry of test vertex a and
+ * trial vertex b (coefficients constant on K, g_a = grad lambda_a):
+ *   |K| g_a^T A g_b - |K|/(d+1) b.g_a + |K|/(d+1) c.g_b + a0 |K| d!/(d+2)! (1 + delta_ab).
+ * coef holds records of nc = d*d + 2d + 1 values (A row-major, b, c, a0), in the
+ * precision of the form (double for FE_F64, float for FE_F32):
+ *   FE_COEF_SCALAR       one record, coef[j];
+ *   FE_COEF_P0           one per element in input element order, coef[k * nc + j];
+ *   FE_COEF_P0_INTERNAL  the same in the pattern's internal element order;
+ *   FE_COEF_P1           one per vertex, coef[v * nc + j], each coefficient
+ *                        P1-interpolated on K and the integrals taken by the magic
+ *                        formula (Eq. MagicFormula), as for Eq. MatElemMassWP1.
+ * Records are read whole; a 16-byte aligned coef lets 3D records load as vectors.
+ * Pattern: m = 1, built by fe_pattern or fe_batch_pattern (not a boundary pattern).
+ * Every reassembly strategy; FE_F64X is not a form of this operator (FE_ERR_ARG).
+ * Asynchronous on `stream`; degenerate elements as for the other operators.
+ */
+int fe_assemble_general(fe_pattern_h h, const double* q, const void* coef, int32_t coef_kind,
+                        int32_t prec, void* vals, void* stream);
+
+/*
  * fe_assemble_stiff_backward -- gradients of L = u^T S(w) v, S the stiffness
  * matrix of fe_assemble_stiff, without forming any matrix (the paper has no
  * derivatives; these follow from Eq. stiffelemmat and App. C.1). Per element,

@@ -180,9 +180,9 @@ def assemble_boundary(kind: int, q: np.ndarray, facets: np.ndarray, c1=None) -> 
 
 
 def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, kind: int) -> dict:
-    """General operator of Eq. EDP. coef: the d*d + 2d + 1 values A (row-major), b, c, a0,
-    as (nc,) for COEF_SCALAR, (nc, nme) for COEF_P0, (nc, nq) for COEF_P1.
-    Same result dict as assemble()."""
+    """General operator of Eq. EDP. coef: records of the nc = d*d + 2d + 1 values A
+    (row-major), b, c, a0: (nc,) for COEF_SCALAR, (nme, nc) for COEF_P0, (nq, nc) for
+    COEF_P1. Same result dict as assemble()."""
     q = np.ascontiguousarray(q, dtype=np.float64)
     me = np.ascontiguousarray(me, dtype=np.int32)
     cf = np.ascontiguousarray(coef, dtype=np.float64)

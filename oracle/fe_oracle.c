@@ -365,9 +365,9 @@ void orc_free(void* p) { free(p); }
  * c (P1, interpolated) or the element's value for every c (scalar, P0; then sum_c lambda_c = 1
  * gives back the constant), and every integral of a product of barycentric coordinates is
  * taken by the magic formula (Eq. MagicFormula).
- * coef holds the nc = d*d + 2d + 1 values A (row-major), b, c, a0: once (ORC_COEF_SCALAR:
- * coef[j]), per element (ORC_COEF_P0: coef[j * nme + k]) or per vertex (ORC_COEF_P1:
- * coef[j * nq + v]).
+ * coef holds records of nc = d*d + 2d + 1 values A (row-major), b, c, a0: one record
+ * (ORC_COEF_SCALAR: coef[j]), one per element (ORC_COEF_P0: coef[k * nc + j]) or one per
+ * vertex (ORC_COEF_P1: coef[v * nc + j]).
  * The condition scale of an entry is the same sum with every term replaced by its absolute
  * bound: |A(c)|_F |g_a| |g_b|, |b(c)| |g_a|, |c(c)| |g_b|, |a0(c)| under the same integrals.
  */
@@ -399,8 +399,8 @@ int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const 
     for (int c = 0; c < nv; ++c)
       for (int j = 0; j < nc; ++j)
         cf[c][j] = coef_kind == ORC_COEF_SCALAR ? coef[j]
-                 : coef_kind == ORC_COEF_P0     ? coef[(int64_t)j * nme + k]
-                                                : coef[(int64_t)j * nq + vid[c]];
+                 : coef_kind == ORC_COEF_P0     ? coef[k * nc + j]
+                                                : coef[(int64_t)vid[c] * nc + j];
     double gn[4];
     for (int a = 0; a < nv; ++a) {
       double s = 0.0;

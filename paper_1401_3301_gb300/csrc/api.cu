@@ -15,6 +15,8 @@ int fe_launch_boundary(fe_pattern_s* h, int kind, const double* q, const void* w
                        void* vals, cudaStream_t s);
 int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_kind, const void* mu,
                    int mu_kind, int prec, void* vals, cudaStream_t s);
+int fe_launch_general(fe_pattern_s* h, const double* q, const void* coef, int coef_kind, int prec,
+                      void* vals, cudaStream_t s);
 int fe_launch_backward(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* u,
                        const void* v, void* L, void* dLdw, void* dLdq, int prec, cudaStream_t s);
 int fe_launch_vjp(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* grad_vals,
@@ -259,6 +261,16 @@ int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t l
   };
   if (!ok(lam_kind) || !ok(mu_kind)) return FE_ERR_ARG;
   return fe_launch_elas(h, q, lam, lam_kind, mu, mu_kind, prec, vals, (cudaStream_t)stream);
+}
+
+int fe_assemble_general(fe_pattern_h h, const double* q, const void* coef, int32_t coef_kind,
+                        int32_t prec, void* vals, void* stream) {
+  FE_TRY(check_common(h, q, prec, vals));
+  if (h->m != 1 || h->kdim != h->d || !coef) return FE_ERR_ARG;
+  if (coef_kind != FE_COEF_SCALAR && coef_kind != FE_COEF_P0 && coef_kind != FE_COEF_P0_INTERNAL &&
+      coef_kind != FE_COEF_P1)
+    return FE_ERR_ARG;
+  return fe_launch_general(h, q, coef, coef_kind, prec, vals, (cudaStream_t)stream);
 }
 
 int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,

@@ -106,14 +106,13 @@ struct ElemArgs {
   fe_status_word* st;
 };
 
-// values of internal element e, coordinates gathered from global memory
-template <int D, class T, int KIND>
-__device__ __forceinline__ void element_values(const ElemArgs& A, int64_t e, ScalarVals<D, T>& out) {
+// geometry of internal element e (vertex ids in v), coordinates gathered from global
+// memory; a degenerate element is reported and given det B = 1
+template <int D, class T>
+__device__ __forceinline__ void element_geo(const ElemArgs& A, int64_t e, int32_t v[D + 1], Geo<D, T>& g) {
   constexpr int NV = D + 1;
-  int32_t v[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) v[a] = __ldg(A.me + (int64_t)a * A.nme + e);
-  Geo<D, T> g;
   if constexpr (sizeof(T) == 8) {
     double x[NV][D];
     load_x64<D>(A.q, A.nq, v, x);
@@ -127,6 +126,15 @@ __device__ __forceinline__ void element_values(const ElemArgs& A, int64_t e, Sca
     fe_report(A.st, FE_ERR_DEGENERATE, A.order[e]);
     g.det = T(1);
   }
+}
+
+// values of internal element e, coordinates gathered from global memory
+template <int D, class T, int KIND>
+__device__ __forceinline__ void element_values(const ElemArgs& A, int64_t e, ScalarVals<D, T>& out) {
+  constexpr int NV = D + 1;
+  int32_t v[NV];
+  Geo<D, T> g;
+  element_geo<D, T>(A, e, v, g);
   T wv[NV];
   if constexpr (KIND == K_WMASS_P1) {
 #pragma unroll
@@ -180,6 +188,87 @@ struct Acc<float> {
 };
 
 // ---------------------------------------------------------------- FE_REASM_CHUNKED
+// Bulk (TMA) copy of chunk c's plan record into the start of shared memory, on the
+// mbarrier bar; true in every thread once it has landed. On a timeout the block
+// reports FE_ERR_TIMEOUT (element e0), waits once more for the copy in flight and
+// every thread gets false.
+__device__ __forceinline__ bool load_plan_record(unsigned char* smem, uint64_t* bar, const uint8_t* rec,
+                                                 const uint32_t* rec_off16, int64_t c, uint32_t bytes,
+                                                 fe_status_word* st, int64_t e0, uint32_t spin) {
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_copy_g2s(smem, rec + (int64_t)rec_off16[c] * 16, bytes, bar);
+  }
+  __syncthreads();
+  const bool landed = __syncthreads_and(mbar_wait_bounded(bar, 0, spin));
+  if (!landed && threadIdx.x == 0) {
+    fe_report(st, FE_ERR_TIMEOUT, e0);
+    mbar_wait_bounded(bar, 0, spin);  // let the copy in flight finish, if it can
+  }
+  return landed;
+}
+
+// Coordinates of global vertex vid into local slot u of the staged coordinate array
+// sq: FP64 (x, y[, z]) in 16 (2D) or 32 (3D) bytes; FP32 the (hi, lo) float split.
+template <int D, class T>
+__device__ __forceinline__ void stage_vertex(const double* __restrict__ q, int64_t nq, int64_t vid,
+                                             unsigned char* sq, int u) {
+  double x[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = __ldg(q + k * nq + vid);
+  if constexpr (sizeof(T) == 8) {
+    double* xs = (double*)sq + (D == 3 ? 4 : 2) * u;
+    ((double2*)xs)[0] = make_double2(x[0], x[1]);
+    if constexpr (D == 3) xs[2] = x[2];
+  } else {
+    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < D; ++k) split_f64(x[k], h[k], l[k]);
+    float4* xs = (float4*)sq + (D == 3 ? 2 : 1) * u;
+    if constexpr (D == 3) {
+      xs[0] = make_float4(h[0], h[1], h[2], 0.f);
+      xs[1] = make_float4(l[0], l[1], l[2], 0.f);
+    } else {
+      xs[0] = make_float4(h[0], h[1], l[0], l[1]);
+    }
+  }
+}
+
+// Geometry of an element whose corners are the local vertices lv of the staged array sq.
+template <int D, class T>
+__device__ __forceinline__ void staged_geo(const unsigned char* sq, const int lv[D + 1], Geo<D, T>& g) {
+  constexpr int NV = D + 1;
+  if constexpr (sizeof(T) == 8) {
+    double x[NV][D];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const double* xs = (const double*)sq + (D == 3 ? 4 : 2) * lv[a];
+      const double2 xy = ((const double2*)xs)[0];
+      x[a][0] = xy.x;
+      x[a][1] = xy.y;
+      if constexpr (D == 3) x[a][2] = xs[2];
+    }
+    geo_f64<D>(x, g);
+  } else {
+    float xh[NV][D], xl[NV][D];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const float4* xs = (const float4*)sq + (D == 3 ? 2 : 1) * lv[a];
+      const float4 h = xs[0];
+      if constexpr (D == 3) {
+        const float4 l = xs[1];
+        xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
+        xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
+      } else {
+        xh[a][0] = h.x; xh[a][1] = h.y;
+        xl[a][0] = h.z; xl[a][1] = h.w;
+      }
+    }
+    geo_f32<D>(xh, xl, g);
+  }
+}
+
 struct StagedArgs {
   int64_t nme, nq;
   int chunk;
@@ -221,20 +310,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = staged_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, DEFER);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_arrive_expect_tx(&bar, R.total);
-    bulk_copy_g2s(smem, A.rec + (int64_t)A.rec_off16[c] * 16, R.total, &bar);
-  }
-  __syncthreads();
-  const bool landed = __syncthreads_and(mbar_wait_bounded(&bar, 0, kBarrierSpin));
-  if (!landed) {
-    if (threadIdx.x == 0) {
-      fe_report(A.st, FE_ERR_TIMEOUT, e0);
-      mbar_wait_bounded(&bar, 0, kBarrierSpin);  // let the copy in flight finish, if it can
-    }
-    return;
-  }
+  if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
   const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
@@ -251,29 +327,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   // 0. vertex coordinates of the chunk, and the local vertex of every element corner
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
-    double x[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) x[k] = __ldg(A.q + k * A.nq + vid);
-    if constexpr (sizeof(T) == 8) {
-      double* xs = (double*)(smem + S.q) + (D == 3 ? 4 : 2) * u;
-      if constexpr (D == 3) {
-        ((double2*)xs)[0] = make_double2(x[0], x[1]);
-        xs[2] = x[2];
-      } else {
-        ((double2*)xs)[0] = make_double2(x[0], x[1]);
-      }
-    } else {
-      float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < D; ++k) split_f64(x[k], h[k], l[k]);
-      float4* xs = (float4*)(smem + S.q) + (D == 3 ? 2 : 1) * u;
-      if constexpr (D == 3) {
-        xs[0] = make_float4(h[0], h[1], h[2], 0.f);
-        xs[1] = make_float4(l[0], l[1], l[2], 0.f);
-      } else {
-        xs[0] = make_float4(h[0], h[1], l[0], l[1]);
-      }
-    }
+    stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u);
     if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
     for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
@@ -286,34 +340,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     Geo<D, T> g;
-    if constexpr (sizeof(T) == 8) {
-      double x[NV][D];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        const double* xs = (const double*)(smem + S.q) + (D == 3 ? 4 : 2) * lv[a];
-        const double2 xy = ((const double2*)xs)[0];
-        x[a][0] = xy.x;
-        x[a][1] = xy.y;
-        if constexpr (D == 3) x[a][2] = xs[2];
-      }
-      geo_f64<D>(x, g);
-    } else {
-      float xh[NV][D], xl[NV][D];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lv[a];
-        const float4 h = xs[0];
-        if constexpr (D == 3) {
-          const float4 l = xs[1];
-          xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
-          xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
-        } else {
-          xh[a][0] = h.x; xh[a][1] = h.y;
-          xl[a][0] = h.z; xl[a][1] = h.w;
-        }
-      }
-      geo_f32<D>(xh, xl, g);
-    }
+    staged_geo<D, T>(smem + S.q, lv, g);
     if (!det_ok(g.det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       g.det = T(1);

@@ -210,8 +210,6 @@ __global__ void k_vinc_keys(const int32_t* me_int, int64_t nme, int nv, int chun
   vals[i] = (uint32_t)((e % chunk) * nv + a);
 }
 
-// edge incidences: entry i = e * npair + p, key (chunk, vmin, vmax),
-// value ((e_local * npair + p) << 1) | (me(a) > me(b)) for pair p = (a, b), a < b
 // edge incidences: entry i = e * npair + p, key (chunk, nonzero of the edge oriented
 // (vmin, vmax)) taken from the slot map, value ((e_local * npair + p) << 1) |
 // (me(a) > me(b)) for pair p = (a, b), a < b
@@ -611,8 +609,9 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     for (int64_t c = 0; c < h->nchunks; ++c) mlv = vp[c + 1] - vp[c] > mlv ? vp[c + 1] - vp[c] : mlv;
     h->max_lv = mlv;
   }
-  // partial-sum scratch: up to 9 values (elasticity blocks) of 8 bytes per partial
-  const int vals_per_partial = (h->m == 1) ? 1 : h->m * h->m;
+  // partial-sum scratch of 8-byte values: 2 per partial for scalar problems (the
+  // general operator keeps one per edge orientation), m * m for the vector blocks
+  const int vals_per_partial = (h->m == 1) ? 2 : h->m * h->m;
   const size_t pb = (size_t)(npart[0] + npart[1]) * vals_per_partial * 2 * sizeof(float) + 16;
   FE_TRY(fe_malloc(h, &h->partials, pb));
   h->partials_bytes = pb;

@@ -97,14 +97,34 @@ __host__ __device__ __forceinline__ StagedSmem boundary_smem(int D, int sizeT, b
   return L;
 }
 
+// Shared-memory layout of the general (non-symmetric) operator kernel: one diagonal
+// value per corner and two values, one per orientation, per element edge (ko).
+__host__ __device__ __forceinline__ StagedSmem general_smem(int D, int sizeT, uint32_t rec_max,
+                                                            uint32_t max_lv, uint32_t chunk) {
+  const uint32_t nv = D + 1, np = D * (D + 1) / 2;
+  StagedSmem L;
+  uint32_t o = pad16(rec_max);
+  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
+  L.w = o;
+  L.lvid = o; o += pad16(2u * nv * chunk);
+  L.kd = o;   o += pad16(sizeT * nv * chunk);
+  L.ko = o;   o += pad16(2u * sizeT * np * chunk);
+  L.sc = o;
+  L.total = o;
+  return L;
+}
+
 // Largest shared-memory footprint of any chunked kernel for a plan (FP64, with a P1
-// coefficient): the plan build shrinks the chunk until it fits in one block.
+// coefficient, and the general operator): the plan build shrinks the chunk until it
+// fits in one block.
 __host__ __device__ __forceinline__ uint32_t plan_smem_worst(int D, int m, uint32_t rec_max,
                                                              uint32_t max_lv, uint32_t chunk) {
   if (m > 1) return elas_smem(D, 8, rec_max, max_lv, chunk).total;
   const uint32_t a = staged_smem(D, 8, true, rec_max, max_lv, chunk).total;
   const uint32_t b = staged_smem(D, 8, false, rec_max, max_lv, chunk, true).total;
-  return a > b ? a : b;
+  const uint32_t g = general_smem(D, 8, rec_max, max_lv, chunk).total;
+  const uint32_t ab = a > b ? a : b;
+  return ab > g ? ab : g;
 }
 
 }  // namespace fe

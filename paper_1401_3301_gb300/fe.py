@@ -57,6 +57,7 @@ def lib() -> C.CDLL:
         L.fe_assemble_wmass.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_elas.argtypes = [P, P, P, I32, P, I32, I32, P, P]
+        L.fe_assemble_general.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff_vjp.argtypes = [P, P, P, I32, P, P, P, I32, P]
@@ -77,7 +78,7 @@ def lib() -> C.CDLL:
                      "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
                      "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads",
-                     "fe_boundary_pattern"):
+                     "fe_boundary_pattern", "fe_assemble_general"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -305,6 +306,17 @@ def fe_assemble_elas(p: Pattern, q: torch.Tensor, lam: torch.Tensor, lam_kind: i
     _check(lib().fe_assemble_elas(p.handle, _dev(q, torch.float64, "q"), _dev(lam, _vtype(prec), "lam"),
                                   lam_kind, _dev(mu, _vtype(prec), "mu"), mu_kind, prec,
                                   _dev(vals, _vtype(prec), "vals"), _stream(stream)))
+    return vals
+
+
+def fe_assemble_general(p: Pattern, q: torch.Tensor, coef: torch.Tensor, coef_kind: int, prec: int = F64,
+                        vals=None, stream=None):
+    """General operator of Eq. EDP; coef: records of nc = d*d + 2d + 1 values (A row-major,
+    b, c, a0): one (COEF_SCALAR, shape (nc,)), one per element ((nme, nc), COEF_P0 /
+    COEF_P0_INTERNAL) or one per vertex ((nq, nc), COEF_P1)."""
+    vals = _out(p, vals, prec)
+    _check(lib().fe_assemble_general(p.handle, _dev(q, torch.float64, "q"), _dev(coef, _vtype(prec), "coef"),
+                                     coef_kind, prec, _dev(vals, _vtype(prec), "vals"), _stream(stream)))
     return vals
 
 

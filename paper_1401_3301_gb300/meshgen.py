@@ -27,7 +27,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream purposes
-JITTER, ELEM_PERM, VERT_PERM, VERT_WEIGHT, ELEM_WEIGHT, VECTORS, BATCH_SIZES = 1, 2, 3, 4, 5, 6, 7
+JITTER, ELEM_PERM, VERT_PERM, VERT_WEIGHT, ELEM_WEIGHT, VECTORS, BATCH_SIZES, GEN_COEF = 1, 2, 3, 4, 5, 6, 7, 8
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -175,6 +175,20 @@ def vertex_weights(seed: int, nq: int) -> np.ndarray:
 def element_weights(seed: int, nme: int) -> np.ndarray:
     """Per-element lognormal(0, 1) coefficient."""
     return np.exp(normal(stream_key(seed, ELEM_WEIGHT), nme))
+
+
+def general_coefficients(seed: int, d: int, n: int) -> np.ndarray:
+    """n records (rows) of convection-diffusion-reaction coefficients, (n, d*d + 2d + 1):
+    A = exp(g0) I + 0.3 N (a non-symmetric, diffusion-dominated tensor, row-major), b and c
+    with N(0, 1) entries, a0 = exp(g1); g0, g1 and the entries of N iid N(0, 1)."""
+    nc = d * d + 2 * d + 1
+    z = normal(stream_key(seed, GEN_COEF), (nc + 2) * n).reshape(n, nc + 2)
+    out = np.empty((n, nc))
+    out[:, : d * d] = 0.3 * z[:, : d * d]
+    out[:, 0 : d * d : d + 1] += np.exp(z[:, nc : nc + 1])
+    out[:, d * d : nc - 1] = z[:, d * d : nc - 1]
+    out[:, nc - 1] = np.exp(z[:, nc + 1])
+    return out
 
 
 def random_vectors(seed: int, n: int, count: int = 2) -> np.ndarray:

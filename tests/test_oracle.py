@@ -418,10 +418,10 @@ def test_general_operator_per_element_coefficients():
     rng = np.random.default_rng(34)
     cf = general_coef(2, rng.normal(size=(2, 2)), rng.normal(size=2), rng.normal(size=2), 1.3)
     S = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, oracle.COEF_SCALAR))
-    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[:, None], m.nme, 1), oracle.COEF_P0))
+    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[None, :], m.nme, 0), oracle.COEF_P0))
     np.testing.assert_allclose(P, S, atol=1e-14)
-    F = rng.normal(size=(cf.size, m.nme))
-    mask = np.arange(m.nme) % 2 == 0
+    F = rng.normal(size=(m.nme, cf.size))
+    mask = (np.arange(m.nme) % 2 == 0)[:, None]
     Fa, Fb = F * mask, F * ~mask
     T = oracle.to_dense(oracle.assemble_general(m.q, m.me, F, oracle.COEF_P0))
     Ta = oracle.to_dense(oracle.assemble_general(m.q, m.me, Fa, oracle.COEF_P0))
@@ -448,7 +448,7 @@ def test_general_operator_p1_coefficients_by_quadrature(d):
     nc = d * d + 2 * d + 1
     slope, base = rng.normal(size=(nc, d)), rng.normal(size=nc)
     coef_at = lambda x: slope @ x + base[:, None]           # (nc, npoints), linear in x
-    cf = coef_at(m.q)                                        # nodal values (nc, nq)
+    cf = coef_at(m.q).T.copy()                               # nodal records (nq, nc)
     M = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, oracle.COEF_P1))
     al, al0, ga, ga0 = rng.normal(size=d), 0.3, rng.normal(size=d), -0.4
     u, v = al @ m.q + al0, ga @ m.q + ga0
@@ -465,5 +465,5 @@ def test_general_operator_p1_constant_fields_match_scalar():
     m = meshgen.square_mesh(5, seed=37)
     cf = general_coef(2, [[1.0, 0.2], [-0.4, 2.0]], [0.3, -1.0], [0.5, 0.25], 1.5)
     S = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, oracle.COEF_SCALAR))
-    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[:, None], m.nq, 1), oracle.COEF_P1))
+    P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[None, :], m.nq, 0), oracle.COEF_P1))
     np.testing.assert_allclose(P, S, atol=1e-14)
