@@ -37,7 +37,7 @@ SM_COUNT = 152
 FP64_PIPE_PER_SM_CLK = 2.0      # DFMA/DADD/DMUL issue rate per SM per clock on GB300
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["elem.cuh", "plan.cuh", "tma.cuh", "assemble_impl.cuh", "assemble_scalar.inc",
-                  "assemble_f64.cu", "assemble_f32.cu"]
+                  "assemble_f64.cu", "assemble_f32.cu", "assemble_f64x.cu"]
 
 
 def parse():
@@ -309,7 +309,7 @@ def run_gpu(args):
         dom_ms = prof[dom][0] / prof[dom][1]
         abytes = chunk_algorithmic_bytes(p, fe.F64 if prec == fe.F64X else prec, info)
         achieved = abytes / (dom_ms * 1e-3) / 1e9
-        traffic = committed_traffic(prec_name) if prec_name != "f64x" else None
+        traffic = committed_traffic(prec_name)
         roof_hbm = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "traffic": traffic,
                     "algorithmic_bytes_per_launch": abytes, "kernel_ms": dom_ms,
@@ -435,7 +435,6 @@ def run_other(args):
     elif args.workload == "general":
         # convection-diffusion-reaction operator (non-symmetric), per-element and per-vertex
         # coefficient sets of 16 values each
-        import numpy as np
         m = meshgen.kuhn_cube_mesh(args.N, seed=0)
         q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
         p = fe.fe_pattern(q, me)

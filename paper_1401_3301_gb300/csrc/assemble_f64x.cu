@@ -83,20 +83,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   // same footprint as the FP32 form: split coordinates, uint16 corner map, float2 values
   const StagedSmem S = staged_smem(D, 8, false, A.rec_max, A.max_lv, A.chunk);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_arrive_expect_tx(&bar, R.total);
-    bulk_copy_g2s(smem, A.rec + (int64_t)A.rec_off16[c] * 16, R.total, &bar);
-  }
-  __syncthreads();
-  const bool landed = __syncthreads_and(mbar_wait_bounded(&bar, 0, kBarrierSpin));
-  if (!landed) {
-    if (threadIdx.x == 0) {
-      fe_report(A.st, FE_ERR_TIMEOUT, e0);
-      mbar_wait_bounded(&bar, 0, kBarrierSpin);
-    }
-    return;
-  }
+  if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
   const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);

@@ -92,20 +92,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle, true);
   const ElasSmem S = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_arrive_expect_tx(&bar, R.total);
-    bulk_copy_g2s(smem, A.rec + (int64_t)A.rec_off16[c] * 16, R.total, &bar);
-  }
-  __syncthreads();
-  const bool landed = __syncthreads_and(mbar_wait_bounded(&bar, 0, kBarrierSpin));
-  if (!landed) {
-    if (threadIdx.x == 0) {
-      fe_report(A.st, FE_ERR_TIMEOUT, e0);
-      mbar_wait_bounded(&bar, 0, kBarrierSpin);
-    }
-    return;
-  }
+  if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
   const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
@@ -124,25 +111,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   // 0. coordinates (and P1 Lame values) of the chunk's vertices; local vertex of each corner
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
-    double x[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) x[k] = __ldg(A.q + k * A.nq + vid);
-    if constexpr (sizeof(T) == 8) {
-      double* xs = (double*)(smem + S.q) + (D == 3 ? 4 : 2) * u;
-      ((double2*)xs)[0] = make_double2(x[0], x[1]);
-      if constexpr (D == 3) xs[2] = x[2];
-    } else {
-      float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < D; ++k) split_f64(x[k], h[k], l[k]);
-      float4* xs = (float4*)(smem + S.q) + (D == 3 ? 2 : 1) * u;
-      if constexpr (D == 3) {
-        xs[0] = make_float4(h[0], h[1], h[2], 0.f);
-        xs[1] = make_float4(l[0], l[1], l[2], 0.f);
-      } else {
-        xs[0] = make_float4(h[0], h[1], l[0], l[1]);
-      }
-    }
+    stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u);
     if (A.lam_kind == FE_COEF_P1) lam_l[u] = ((const T*)A.lam)[vid];
     if (A.mu_kind == FE_COEF_P1) mu_l[u] = ((const T*)A.mu)[vid];
     for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
@@ -155,34 +124,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     Geo<D, T> g;
-    if constexpr (sizeof(T) == 8) {
-      double x[NV][D];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        const double* xs = (const double*)(smem + S.q) + (D == 3 ? 4 : 2) * lv[a];
-        const double2 xy = ((const double2*)xs)[0];
-        x[a][0] = xy.x;
-        x[a][1] = xy.y;
-        if constexpr (D == 3) x[a][2] = xs[2];
-      }
-      geo_f64<D>(x, g);
-    } else {
-      float xh[NV][D], xl[NV][D];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lv[a];
-        const float4 h = xs[0];
-        if constexpr (D == 3) {
-          const float4 l = xs[1];
-          xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
-          xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
-        } else {
-          xh[a][0] = h.x; xh[a][1] = h.y;
-          xl[a][0] = h.z; xl[a][1] = h.w;
-        }
-      }
-      geo_f32<D>(xh, xl, g);
-    }
+    staged_geo<D, T>(smem + S.q, lv, g);
     if (!det_ok(g.det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       g.det = T(1);
