@@ -11,6 +11,9 @@ from __future__ import annotations
 import ctypes as C
 import os
 import subprocess
+from fractions import Fraction
+from itertools import product
+from math import factorial
 
 import numpy as np
 
@@ -50,6 +53,7 @@ def _load():
         lib.orc_facet.argtypes = [I32, P, P]
         lib.orc_assemble_boundary.argtypes = [I32, I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P]
         lib.orc_assemble_general.argtypes = [I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P]
+        lib.orc_assemble_table.argtypes = [I32, I64, I64, I32, P, P, P, P, P, P, P, P, P, P]
         lib.orc_free.argtypes = [P]
         _lib = lib
     return _lib
@@ -193,6 +197,89 @@ def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, kind: int)
     rc = lib.orc_assemble_general(d, nq, me.shape[1], _ptr(q), _ptr(me), kind,
                                   _ptr(cf), C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
                                   C.byref(sc), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+
+    def take(p, ctype, count, dtype):
+        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
+        out = np.array(arr, dtype=dtype)
+        lib.orc_free(p)
+        return out
+
+    N, NNZ = n.value, nnz.value
+    return dict(n=N, nnz=NNZ, row_ptr=take(rp, C.c_int64, N + 1, np.int64),
+                col_idx=take(ci, C.c_int32, NNZ, np.int32), val=take(va, C.c_double, NNZ, np.float64),
+                scale=take(sc, C.c_double, NNZ, np.float64))
+
+
+def pk_multi_indices(d: int, k: int) -> list:
+    """The P_k nodes of a d-simplex as multi-indices alpha (|alpha| = k, d+1 entries), in
+    the local node order: the d+1 vertices k e_0, ..., k e_d first, then every other alpha
+    in lexicographically decreasing order."""
+    verts = [tuple(k if i == j else 0 for i in range(d + 1)) for j in range(d + 1)]
+    rest = sorted((a for a in product(range(k + 1), repeat=d + 1) if sum(a) == k and a not in verts),
+                  reverse=True)
+    return verts + rest
+
+
+def _pk_basis(alpha, k):
+    """phi_alpha of Eq. Pk:functions as {mu: coefficient} over barycentric monomials."""
+    poly = {tuple(0 for _ in alpha): Fraction(1)}
+    for l, al in enumerate(alpha):
+        for j in range(al):  # times (k lambda_l - j) / (j + 1)
+            nxt = {}
+            for mu, c in poly.items():
+                up = list(mu)
+                up[l] += 1
+                up = tuple(up)
+                nxt[up] = nxt.get(up, 0) + c * Fraction(k, j + 1)
+                nxt[mu] = nxt.get(mu, 0) - c * Fraction(j, j + 1)
+            poly = {m: c for m, c in nxt.items() if c != 0}
+    return poly
+
+
+def pk_mass_table(d: int, k: int) -> list:
+    """Exact (integral of phi_alpha phi_beta) / |K| for all node pairs (list of rows of
+    Fractions, local node order), by the magic formula (Eq. MagicFormula) applied to the
+    monomial expansion of the basis functions."""
+    al = pk_multi_indices(d, k)
+    basis = [_pk_basis(a, k) for a in al]
+
+    def magic(n):  # integral of prod lambda^n over K, divided by |K|
+        num = factorial(d)
+        for x in n:
+            num *= factorial(x)
+        return Fraction(num, factorial(d + sum(n)))
+
+    tab = []
+    for pa in basis:
+        row = []
+        for pb in basis:
+            s = Fraction(0)
+            for mu, ca in pa.items():
+                for nu, cb in pb.items():
+                    s += ca * cb * magic([x + y for x, y in zip(mu, nu)])
+            row.append(s)
+        tab.append(row)
+    return tab
+
+
+def assemble_pk_mass(q: np.ndarray, me: np.ndarray, k: int) -> dict:
+    """P_k mass matrix (App. D, Algorithm 15) of a P_k mesh whose rows of me follow
+    pk_multi_indices. Same result dict as assemble()."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    me = np.ascontiguousarray(me, dtype=np.int32)
+    d, nq = q.shape
+    tab = np.array([[float(x) for x in row] for row in pk_mass_table(d, k)])
+    ndfe = tab.shape[0]
+    assert me.shape[0] == ndfe
+    flat = np.ascontiguousarray(tab.T)  # flat[b * ndfe + a] = entry (a, b)
+    n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
+    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    lib = _load()
+    rc = lib.orc_assemble_table(d, nq, me.shape[1], ndfe, _ptr(q), _ptr(me), _ptr(flat), C.byref(n),
+                                C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va), C.byref(sc),
+                                C.byref(bad))
     if rc:
         raise OracleError(rc, bad.value)
 

@@ -458,6 +458,52 @@ int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const 
 }
 
 /*
+ * P_k mass (App. D, Eq. MatElemMassPk and Algorithm 15): every element contributes
+ * |K| * tab[b * ndfe + a] to entry (me(a), me(b)), where tab = (integral of
+ * phi_alpha phi_beta) / |K| is the same for every element. |K| comes from the element's
+ * first d + 1 nodes, its vertices. The caller supplies tab (computed exactly from the
+ * basis functions of Eq. Pk:functions and the magic formula) and the node order it
+ * belongs to. The condition scale of an entry is the sum of |K| |tab|.
+ */
+int orc_assemble_table(int d, int64_t nq, int64_t nme, int ndfe, const double* q, const int32_t* me,
+                       const double* tab, int64_t* n_out, int64_t* nnz_out, int64_t** row_ptr,
+                       int32_t** col_idx, double** val, double** scale, int64_t* bad_id) {
+  *bad_id = -1;
+  if (d < 2 || d > 3 || ndfe < d + 1) return ORC_ERR_ARG;
+  const int64_t ns = (int64_t)ndfe * ndfe;
+  triplet* t = (triplet*)malloc((size_t)(nme * ns > 0 ? nme * ns : 1) * sizeof(triplet));
+  if (!t) return ORC_ERR_NOMEM;
+  double X[12], G[12], det, vol;
+  int rc = ORC_OK;
+  for (int64_t k = 0; k < nme && rc == ORC_OK; ++k) {
+    for (int a = 0; a < ndfe; ++a) {
+      const int32_t v = me[(int64_t)a * nme + k];
+      if (v < 0 || v >= nq) { *bad_id = k; rc = ORC_ERR_INDEX; break; }
+      if (a <= d)
+        for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
+    }
+    if (rc) break;
+    rc = orc_simplex(d, X, &det, &vol, G);
+    if (rc) { *bad_id = k; break; }
+    for (int b = 0; b < ndfe; ++b)
+      for (int a = 0; a < ndfe; ++a) {
+        triplet* p = &t[k * ns + (int64_t)b * ndfe + a];
+        p->row = me[(int64_t)a * nme + k];
+        p->col = me[(int64_t)b * nme + k];
+        p->k = k;
+        p->slot = b * ndfe + a;
+        p->v = vol * tab[(int64_t)b * ndfe + a];
+        p->s = fabs(p->v);
+      }
+  }
+  if (rc) { free(t); return rc; }
+  rc = triplets_to_csr(t, nme * ns, nq, row_ptr, col_idx, val, scale, nnz_out);
+  free(t);
+  *n_out = nq;
+  return rc;
+}
+
+/*
  * Measure of a (d-1)-simplex in d-space with vertices X (d vertices x d coordinates):
  * sqrt(det(B^T B)) / (d-1)!, B the d x (d-1) matrix of edge vectors q^i - q^0 (the
  * Gram determinant; for a segment its length, for a triangle half the parallelogram).

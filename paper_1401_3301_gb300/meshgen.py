@@ -156,6 +156,62 @@ def kuhn_cube_mesh(N: int, seed: int = 0, jitter: float = 0.15, perm_vertices: b
     return _finish(3, q, me, seed, jitter, interior, 1.0 / N, perm_vertices, perm_elements)
 
 
+def pk_node_order(d: int, k: int) -> list:
+    """Local node order of a P_k simplex (App. D) as multi-indices alpha, |alpha| = k: the
+    d+1 vertices k e_0, ..., k e_d first, then the other multi-indices in lexicographically
+    decreasing order."""
+    verts = [tuple(k if i == j else 0 for i in range(d + 1)) for j in range(d + 1)]
+    out = list(verts)
+    def rec(prefix, left, slots):
+        if slots == 1:
+            yield prefix + (left,)
+            return
+        for x in range(left, -1, -1):
+            yield from rec(prefix + (x,), left - x, slots - 1)
+    out += [a for a in rec((), k, d + 1) if a not in verts]
+    return out
+
+
+def pk_mesh(d: int, N: int, k: int, seed: int = 0, jitter: float | None = None, perm_nodes: bool = False,
+            perm_elements: bool = True) -> Mesh:
+    """P_k mesh (App. D) of the unit square (d=2) or the Kuhn cube (d=3) with N cells per side.
+
+    The simplices are unimodular, so their P_k nodes are exactly the points of the k-times
+    finer lattice: (kN+1)^d nodes, numbered like the coarse vertices on the fine lattice.
+    me is (ndfe, nme), rows in pk_node_order(d, k). Node coordinates are the affine images
+    sum_i alpha_i x_i / k of the jittered coarse vertices, taken from the first element
+    (in generation order) holding the node. k = 1 gives the P1 mesh with the same jitter.
+    """
+    if jitter is None:
+        jitter = 0.2 if d == 2 else 0.15
+    base = (square_mesh if d == 2 else kuhn_cube_mesh)(N, seed=seed, jitter=jitter, perm_vertices=False,
+                                                       perm_elements=False)
+    n1, f1 = N + 1, k * N + 1
+    vid = np.arange(base.nq)
+    ic = np.stack([(vid // n1 ** c) % n1 for c in range(d)])            # coarse integer coordinates
+    alphas = np.array(pk_node_order(d, k), dtype=np.int64)              # (ndfe, d+1)
+    corner = ic[:, base.me]                                             # (d, d+1, nme)
+    fine = np.einsum("ai,cie->ace", alphas, corner)                     # (ndfe, d, nme)
+    ids = np.zeros((alphas.shape[0], base.nme), dtype=np.int64)
+    for c in range(d):
+        ids += fine[:, c, :] * f1 ** c
+    xc = base.q[:, base.me]                                             # (d, d+1, nme)
+    xf = np.einsum("ai,cie->ace", alphas.astype(np.float64), xc) / k    # (ndfe, d, nme)
+    flat_ids = ids.T.ravel()                                            # element-major, first = lowest element
+    _, first = np.unique(flat_ids, return_index=True)
+    q = np.empty((d, f1 ** d))
+    q[:, flat_ids[first]] = xf.transpose(1, 2, 0).reshape(d, -1)[:, first]
+    me = ids
+    if perm_nodes:
+        new_of_old = permutation(stream_key(seed, VERT_PERM), q.shape[1])
+        qn = np.empty_like(q)
+        qn[:, new_of_old] = q
+        q, me = qn, new_of_old[me]
+    if perm_elements:
+        me = me[:, permutation(stream_key(seed, ELEM_PERM), me.shape[1])]
+    return Mesh(d, np.ascontiguousarray(q), np.ascontiguousarray(me, dtype=np.int32))
+
+
 def boundary_facets(mesh: Mesh) -> np.ndarray:
     """Facets (d-1 simplices) that belong to exactly one element: (d, nfacets) int32,
     vertex indices into the same q, in the order of first appearance."""

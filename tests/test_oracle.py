@@ -4,6 +4,7 @@ No GPU. Each check is chosen so that a plausible slip in the oracle (a dropped
 term, a sign, a transposed index, a wrong factorial) fails at least one of them.
 """
 import itertools
+import math
 import os
 from fractions import Fraction
 
@@ -467,3 +468,74 @@ def test_general_operator_p1_constant_fields_match_scalar():
     S = oracle.to_dense(oracle.assemble_general(m.q, m.me, cf, oracle.COEF_SCALAR))
     P = oracle.to_dense(oracle.assemble_general(m.q, m.me, np.repeat(cf[None, :], m.nq, 0), oracle.COEF_P1))
     np.testing.assert_allclose(P, S, atol=1e-14)
+
+
+# ---------------------------------------------------------------- P_k mass (App. D)
+from fractions import Fraction  # noqa: E402
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_pk_table_k1_is_the_p1_mass(d):
+    t = oracle.pk_mass_table(d, 1)
+    base = Fraction(math.factorial(d), math.factorial(d + 2))
+    for a in range(d + 1):
+        for b in range(d + 1):
+            assert t[a][b] == base * (2 if a == b else 1)
+
+
+def test_pk_table_p2_closed_forms():
+    # P2 triangle: |K|/180 [6 on vertex diagonals, -1 vertex-vertex, -4 vertex-opposite edge,
+    # 0 vertex-adjacent edge, 32 edge diagonals, 16 edge-edge]
+    al = oracle.pk_multi_indices(2, 2)
+    t = oracle.pk_mass_table(2, 2)
+    for i, a in enumerate(al):
+        for j, b in enumerate(al):
+            va, vb = max(a) == 2, max(b) == 2
+            if va and vb:
+                want = 6 if i == j else -1
+            elif va or vb:
+                v, e = (a, b) if va else (b, a)
+                want = -4 if all(v[x] == 0 or e[x] == 0 for x in range(3)) else 0
+            else:
+                want = 32 if i == j else 16
+            assert t[i][j] == Fraction(want, 180), (a, b)
+    # P2 tetrahedron: integral of a vertex basis function is -|K|/20, of an edge one |K|/5
+    t3 = oracle.pk_mass_table(3, 2)
+    for a, row in zip(oracle.pk_multi_indices(3, 2), t3):
+        assert sum(row) == (Fraction(-1, 20) if max(a) == 2 else Fraction(1, 5))
+
+
+@pytest.mark.parametrize("d,k", [(2, 2), (2, 3), (2, 4), (3, 2), (3, 3)])
+def test_pk_basis_is_lagrange_on_the_lattice(d, k):
+    al = oracle.pk_multi_indices(d, k)
+    for a in al:
+        poly = oracle._pk_basis(a, k)
+        for b in al:
+            lam = [Fraction(x, k) for x in b]
+            val = sum(c * math.prod(l ** m for l, m in zip(lam, mu)) for mu, c in poly.items())
+            assert val == (1 if a == b else 0)
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (2, 5), (3, 3), (3, 4)])
+def test_pk_table_symmetric_partition_of_unity(d, k):
+    t = oracle.pk_mass_table(d, k)
+    n = math.comb(d + k, k)
+    assert len(t) == n
+    assert sum(sum(r) for r in t) == 1
+    assert all(t[i][j] == t[j][i] for i in range(n) for j in range(n))
+
+
+@pytest.mark.parametrize("d,N,k", [(2, 3, 1), (2, 3, 2), (2, 2, 3), (2, 2, 4), (3, 2, 1), (3, 2, 2), (3, 1, 3)])
+def test_pk_mass_of_polynomials_by_quadrature(d, N, k):
+    # P_k contains every polynomial of degree <= k, so the nodal values of such u, v give
+    # v^T M u = int u v exactly over the unit square / cube; tensor Gauss quadrature with
+    # k + 1 points per direction is exact for the product (degree <= 2k per variable).
+    m = meshgen.pk_mesh(d, N, k, seed=40 + k)
+    rng = np.random.default_rng(41)
+    exps = [e for e in np.ndindex(*([k + 1] * d)) if sum(e) <= k]
+    cu, cv = rng.normal(size=len(exps)), rng.normal(size=len(exps))
+    poly = lambda c, X: sum(ci * np.prod([X[j] ** e[j] for j in range(d)], axis=0) for ci, e in zip(c, exps))
+    M = oracle.to_dense(oracle.assemble_pk_mass(m.q, m.me, k))
+    X, W = _gauss_cube(d, k + 1)
+    exact = W @ (poly(cu, X) * poly(cv, X))
+    assert poly(cv, m.q) @ M @ poly(cu, m.q) == pytest.approx(exact, rel=1e-11, abs=1e-13)
