@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
     ap.add_argument("--workload", default="stiffness",
-                    choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general"],
+                    choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general", "pk"],
                     help="stiffness (default, the headline); the others print one JSON line each "
                          "for the other configurations of the hot path")
     return ap.parse_args()
@@ -222,15 +222,17 @@ def committed_traffic(form):
         return None
 
 
-def chunk_algorithmic_bytes(p, prec, info):
+def chunk_algorithmic_bytes(p, prec, info, points=None):
     """Bytes the chunk kernel must move per launch: its plan records (read once), the
-    FP64 coordinates (each vertex once), the owned CSR values and the partial sums it
-    writes; counts are exact, from the plan."""
-    d, nq = p.d, p.nq
+    FP64 coordinates (each point once: every vertex, or for P_k only the element
+    vertices), the owned CSR values and the partial sums it writes; counts are exact,
+    from the plan."""
+    d = p.d
+    npts = p.nq if points is None else points
     sT = 8 if prec == 0 else 4
     lv, le = info["local_vertices"], info["local_edges"]
     pv, pe = info["partial_vertices"], info["partial_edges"]
-    reads = info["plan_bytes"] + 8 * d * nq
+    reads = info["plan_bytes"] + 8 * d * npts
     writes = (lv - pv) * sT + (le - pe) * 2 * sT + (pv + pe) * 8
     return reads + writes
 
@@ -455,6 +457,38 @@ def run_other(args):
             out["forms"][name] = {"value": res["p0_internal"]["value"], "coefficients": res}
         out.update(metric="3D P1 general operator -div(A grad u) + div(b u) + c.grad u + a0 u (non-symmetric) "
                           "Mtets/s, fixed pattern", unit="Mtets/s", config=workload_config(args.N))
+    elif args.workload == "pk":
+        # 3D P_k mass (App. D) at the largest size of the paper's P_k table, about 10^6 nodes:
+        # k N = 100 cells per side on the fine lattice, (kN+1)^3 nodes, for k = 1..6
+        hbm_peak, _, _ = measured_peaks()
+        for k in range(1, 7):
+            N = {1: 100, 2: 50, 3: 33, 4: 25, 5: 20, 6: 17}[k]
+            m = meshgen.pk_mesh(3, N, k, seed=0)
+            q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p = fe.fe_pk_pattern(q, me, k)
+            pms = (time.perf_counter() - t0) * 1e3
+            info = p.plan_info()
+            res = {"N": N, "nodes": m.nq, "tets": m.nme, "nnz": p.nnz, "chunk": info["chunk"],
+                   "pattern_build_ms": pms}
+            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+                vals = torch.empty(p.nnz, dtype=T, device="cuda")
+                med, mean = _timed(lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals), K, W, flush)
+                p.check()
+                sT = 4 if prec == fe.F32 else 8
+                abytes = chunk_algorithmic_bytes(p, prec, info, points=(N + 1) ** 3)
+                res[name] = {"ms_per_step": mean, "ms_median": med, "Mnodes_per_s": m.nq / (mean * 1e-3) / 1e6,
+                             "Mnnz_per_s": p.nnz / (mean * 1e-3) / 1e6,
+                             "algorithmic_bytes": abytes, "GBps": abytes / (mean * 1e-3) / 1e9,
+                             "hbm_frac": abytes / (mean * 1e-3) / 1e9 / hbm_peak, "value_bytes": p.nnz * sT}
+            out["forms"][f"k{k}"] = res
+            del p, vals, q, me
+        out["forms"]["f64"] = {"value": out["forms"]["k2"]["f64"]["Mnodes_per_s"]}
+        out.update(metric="3D P_k mass (App. D), k = 1..6 at about 10^6 nodes: M nodes/s, fixed pattern "
+                          "(value: k = 2, FP64)", unit="M nodes/s",
+                   config={"workload": "Kuhn cube, P_k lattice nodes, kN ~ 100 (about 1.03e6 nodes), jitter 0.15h, "
+                                       "elements permuted", "hbm_peak_GBps": hbm_peak})
     elif args.workload == "elas":
         N = 80 if args.N == 100 else args.N
         m = meshgen.kuhn_cube_mesh(N, seed=0)

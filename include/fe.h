@@ -145,6 +145,31 @@ int fe_batch_gather_q(fe_pattern_h h, const fe_mesh* meshes, double* q_union, vo
  */
 int fe_boundary_pattern(const fe_mesh* facets, int32_t flags, void* stream, fe_pattern_h* out);
 
+/*
+ * fe_pk_pattern -- pattern of a P_k mesh (App. D): q holds the coordinates of all
+ * P_k nodes (d x nq) and mesh->me has ndfe = (d+k)!/(d! k!) rows, the nodes of each
+ * element in the local order: the d+1 vertices (multi-indices k e_0, ..., k e_d)
+ * first, then the other multi-indices alpha (|alpha| = k) in lexicographically
+ * decreasing order. The element geometry comes from the first d+1 nodes. d = 2 or 3,
+ * 1 <= k <= FE_PK_MAX; k = 1 is fe_pattern. Only fe_assemble_mass accepts a pattern
+ * with k >= 2, which then assembles the P_k mass matrix of Eq. MatElemMassPk
+ * (Algorithm 15): local entry |det B| C_{alpha,beta} = d! |K| C_{alpha,beta}, chunked
+ * reassembly only. The element chunk is bounded by the plan's 16-bit incidence codes
+ * (chunk * ndfe (ndfe - 1) / 2 < 32768), so high k uses small chunks. Other
+ * conventions as fe_pattern (m = 1).
+ */
+#define FE_PK_MAX 6
+int fe_pk_pattern(const fe_mesh* mesh, int32_t k, int32_t flags, void* stream, fe_pattern_h* out);
+
+/*
+ * fe_pk_mass_table -- the constants C_{alpha,beta} of Eq. MatElemMassPk for (d, k),
+ * host only: C[a * ndfe + b] for local nodes a, b in the order of fe_pk_pattern.
+ * Each is summed exactly in integer arithmetic from the basis functions of Eq.
+ * Pk:functions and the magic formula, then rounded once (numerator and denominator
+ * to double, then divided). C must hold ndfe * ndfe doubles.
+ */
+int fe_pk_mass_table(int32_t d, int32_t k, double* C);
+
 /* Borrowed CSR arrays (int32, device): row_ptr[n+1], col_idx[nnz]. */
 int fe_pattern_csr(fe_pattern_h h, int64_t* n, int64_t* nnz, const int32_t** row_ptr,
                    const int32_t** col_idx);

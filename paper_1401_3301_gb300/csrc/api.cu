@@ -17,6 +17,7 @@ int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_ki
                    int mu_kind, int prec, void* vals, cudaStream_t s);
 int fe_launch_general(fe_pattern_s* h, const double* q, const void* coef, int coef_kind, int prec,
                       void* vals, cudaStream_t s);
+int fe_launch_pk_mass(fe_pattern_s* h, const double* q, int prec, void* vals, cudaStream_t s);
 int fe_launch_backward(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* u,
                        const void* v, void* L, void* dLdw, void* dLdq, int prec, cudaStream_t s);
 int fe_launch_vjp(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void* grad_vals,
@@ -49,7 +50,7 @@ void fe_free_all(fe_pattern_s* h) {
                   h->le_dst,  h->sh_ptr,   h->sh_dst,    h->partials,  h->kg,
                   h->qsplit,  h->status, h->rec, h->rec_off16,
                   h->lv_str,  h->le_str,   h->sh_str,    h->vmap_ptr,  h->vmap,
-                  h->bwd_scratch, h->bwd_lpart};
+                  h->bwd_scratch, h->bwd_lpart, h->pk_tab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->m > 1) {
@@ -214,6 +215,11 @@ static int check_common(fe_pattern_h h, const double* q, int32_t prec, const voi
 
 static int scalar_call(fe_pattern_h h, int kind, const double* q, const void* w, int32_t w_kind,
                        int32_t prec, void* vals, void* stream) {
+  if (h && h->pk > 1) {  // P_k patterns: the mass matrix only
+    FE_TRY(check_common(h, q, prec, vals));
+    if (kind != 0) return FE_ERR_ARG;
+    return fe_launch_pk_mass(h, q, prec, vals, (cudaStream_t)stream);
+  }
   if (h && h->kdim != h->d) {  // boundary facets: mass and weighted mass only
     FE_TRY(check_common(h, q, prec, vals));
     if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
@@ -266,7 +272,7 @@ int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t l
 int fe_assemble_general(fe_pattern_h h, const double* q, const void* coef, int32_t coef_kind,
                         int32_t prec, void* vals, void* stream) {
   FE_TRY(check_common(h, q, prec, vals));
-  if (h->m != 1 || h->kdim != h->d || !coef) return FE_ERR_ARG;
+  if (h->m != 1 || h->kdim != h->d || h->pk != 1 || !coef) return FE_ERR_ARG;
   if (coef_kind != FE_COEF_SCALAR && coef_kind != FE_COEF_P0 && coef_kind != FE_COEF_P0_INTERNAL &&
       coef_kind != FE_COEF_P1)
     return FE_ERR_ARG;
@@ -278,7 +284,7 @@ int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, i
                                int32_t prec, void* stream) {
   if (!h || !q || !u || !v) return FE_ERR_ARG;
   if (prec != FE_F64 && prec != FE_F32) return FE_ERR_ARG;
-  if (h->m != 1) return FE_ERR_ARG;
+  if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL)
     return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
@@ -289,7 +295,7 @@ int fe_assemble_stiff_vjp(fe_pattern_h h, const double* q, const void* w, int32_
                           const void* grad_vals, void* dL_dw, void* dL_dq, int32_t prec, void* stream) {
   if (!h || !q || !grad_vals) return FE_ERR_ARG;
   if (prec != FE_F64 && prec != FE_F32) return FE_ERR_ARG;
-  if (h->m != 1) return FE_ERR_ARG;
+  if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL)
     return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;

@@ -42,6 +42,8 @@ struct fe_pattern_s {
   int d = 0, m = 1, nv = 0, npair = 0, flags = 0, strategy = FE_REASM_CHUNKED;
   int threads = 256;                // threads per block of the chunked scalar kernel
   int kdim = 0;                     // element dimension: d (volume) or d - 1 (boundary facets)
+  int pk = 1;                       // polynomial degree of the element nodes (App. D); nv nodes
+  void* pk_tab = nullptr;           // pk > 1: P_k mass table, double[nv + npair] then float[nv + npair]
   int64_t nq = 0, nme = 0, n = 0, nnz_s = 0, nnz = 0;
   int32_t* me_int = nullptr;        // (d+1) x nme, internal element order
   int32_t* order = nullptr;         // internal -> input element id
@@ -111,6 +113,10 @@ int fe_scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tm
 // Device allocation helpers tracked in the handle's byte count.
 int fe_malloc(fe_pattern_s* h, void** p, size_t bytes);
 void fe_free_all(fe_pattern_s* h);
+
+// ---------------------------------------------------------------- pk.cu
+int fe_pk_nodes(int d, int k);                      // (d+k)! / (d! k!)
+int fe_pk_upload_table(fe_pattern_s* h, cudaStream_t s);
 
 // ---------------------------------------------------------------- assemble.cu
 int fe_ensure_scratch(fe_pattern_s* h, int strategy);

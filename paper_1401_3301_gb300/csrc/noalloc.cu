@@ -57,7 +57,7 @@ extern "C" int fe_assemble_stiff_noalloc(fe_pattern_h h, const double* q, const 
                                          int32_t w_kind, int32_t prec, void* vals, void* stream) {
   if (!h || !q || !vals) return FE_ERR_ARG;
   if (prec != FE_F64 && prec != FE_F32) return FE_ERR_ARG;
-  if (h->m != 1) return FE_ERR_ARG;
+  if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
   const size_t need = (size_t)h->nme * h->nv * h->nv * (prec == FE_F64 ? sizeof(double) : sizeof(float));

@@ -683,7 +683,7 @@ int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s) {
 
 namespace {
 int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
-                    const int32_t* group, int group_bits, int kdim);
+                    const int32_t* group, int group_bits, int kdim, int pk = 1);
 }  // namespace
 
 extern "C" int fe_batch_pattern(const fe_mesh* meshes, int32_t count, int32_t m, int32_t flags,
@@ -783,7 +783,7 @@ void free_plan(fe_pattern_s* h) {
 }
 
 int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
-                    const int32_t* group, int group_bits, int kdim);
+                    const int32_t* group, int group_bits, int kdim, int pk);
 }  // namespace
 
 extern "C" int fe_pattern(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
@@ -797,9 +797,14 @@ extern "C" int fe_boundary_pattern(const fe_mesh* facets, int32_t flags, void* s
   return fe_pattern_impl(facets, 1, flags, stream, out, nullptr, 0, facets->d - 1);
 }
 
+extern "C" int fe_pk_pattern(const fe_mesh* mesh, int32_t k, int32_t flags, void* stream, fe_pattern_h* out) {
+  if (!mesh || k < 1 || k > FE_PK_MAX) return FE_ERR_ARG;
+  return fe_pattern_impl(mesh, 1, flags, stream, out, nullptr, 0, mesh->d, k);
+}
+
 namespace {
 int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream, fe_pattern_h* out,
-                    const int32_t* group, int group_bits, int kdim) {
+                    const int32_t* group, int group_bits, int kdim, int pk) {
   if (!mesh || !out) return FE_ERR_ARG;
   *out = nullptr;
   const int d = mesh->d;
@@ -807,15 +812,21 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
   if (m != 1 && m != d) return FE_ERR_ARG;
   if (mesh->nq < 1 || mesh->nme < 1 || !mesh->q || !mesh->me) return FE_ERR_ARG;
   if (kdim != d && !(kdim == d - 1 && m == 1)) return FE_ERR_ARG;
-  const int nv = kdim + 1, S = nv * nv;
+  if (pk > 1 && (kdim != d || m != 1)) return FE_ERR_ARG;
+  const int nv = pk > 1 ? fe_pk_nodes(d, pk) : kdim + 1, S = nv * nv;
   const int64_t nq = mesh->nq, nme = mesh->nme;
   if (nq > INT32_MAX / m || nme > INT32_MAX / S) return FE_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   fe_pattern_s* h = new fe_pattern_s();
   h->d = d; h->m = m; h->nv = nv; h->npair = nv * (nv - 1) / 2; h->flags = flags;
   h->kdim = kdim;
+  h->pk = pk;
   h->nq = nq; h->nme = nme; h->n = (int64_t)m * nq;
   h->chunk = kdim == d ? default_chunk(d, m, flags) : default_chunk(2, 1, flags);
+  if (pk > 1) {  // the plan's uint16 incidence codes: chunk * npair < 2^15, chunk * nv < 2^16
+    const int cmax = 32767 / h->npair < 65535 / nv ? 32767 / h->npair : 65535 / nv;
+    if (h->chunk > cmax) h->chunk = cmax < 1 ? 1 : cmax;
+  }
   int rc = FE_OK;
   dev_tmp tmp;
   do {
@@ -914,16 +925,19 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
     // shrink the chunk until the worst-case block's shared memory fits (227 KB)
     for (;;) {
       if ((rc = build_chunk_plan(h, &sb, tmp, s))) break;
-      const uint32_t need = kdim == d
-          ? fe::plan_smem_worst(d, m, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->chunk)
-          : fe::boundary_smem(d, 8, true, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,
-                              (uint32_t)h->chunk).total;
-      if (need <= 227u * 1024u || h->chunk <= 32) break;
+      const uint32_t need =
+          pk > 1 ? fe::pk_smem((uint32_t)nv, (uint32_t)h->npair, 8, (uint32_t)h->rec_max_bytes, (uint32_t)h->chunk).total
+          : kdim == d
+              ? fe::plan_smem_worst(d, m, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->chunk)
+              : fe::boundary_smem(d, 8, true, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,
+                                  (uint32_t)h->chunk).total;
+      if (need <= 227u * 1024u || h->chunk <= (pk > 1 ? 1 : 32)) break;
       if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
       free_plan(h);
       h->chunk /= 2;
     }
     if (rc) break;
+    if (pk > 1 && (rc = fe_pk_upload_table(h, s))) break;
     if ((rc = fe_ensure_scratch(h, h->strategy))) break;
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
   } while (0);

@@ -114,6 +114,22 @@ __host__ __device__ __forceinline__ StagedSmem general_smem(int D, int sizeT, ui
   return L;
 }
 
+// Shared-memory layout of the P_k mass kernel: local node of each element node (lvid),
+// the |det B| of each element (sc) and the constant table (diagonal, then pairs).
+struct PkSmem {
+  uint32_t lvid, sc, tab, total;
+};
+__host__ __device__ __forceinline__ PkSmem pk_smem(uint32_t nv, uint32_t np, int sizeT, uint32_t rec_max,
+                                                   uint32_t chunk) {
+  PkSmem L;
+  uint32_t o = pad16(rec_max);
+  L.lvid = o; o += pad16(2u * nv * chunk);
+  L.sc = o;   o += pad16(sizeT * chunk);
+  L.tab = o;  o += pad16(sizeT * (nv + np));
+  L.total = o;
+  return L;
+}
+
 // Largest shared-memory footprint of any chunked kernel for a plan (FP64, with a P1
 // coefficient, and the general operator): the plan build shrinks the chunk until it
 // fits in one block.

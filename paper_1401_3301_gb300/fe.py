@@ -58,6 +58,8 @@ def lib() -> C.CDLL:
         L.fe_assemble_stiff.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_elas.argtypes = [P, P, P, I32, P, I32, I32, P, P]
         L.fe_assemble_general.argtypes = [P, P, P, I32, I32, P, P]
+        L.fe_pk_pattern.argtypes = [P, I32, I32, P, P]
+        L.fe_pk_mass_table.argtypes = [I32, I32, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff_vjp.argtypes = [P, P, P, I32, P, P, P, I32, P]
@@ -78,7 +80,7 @@ def lib() -> C.CDLL:
                      "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
                      "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads",
-                     "fe_boundary_pattern", "fe_assemble_general"):
+                     "fe_boundary_pattern", "fe_assemble_general", "fe_pk_pattern", "fe_pk_mass_table"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -239,6 +241,32 @@ def fe_boundary_pattern(q: torch.Tensor, facets: torch.Tensor, flags: int = 0, s
     h = C.c_void_p()
     _check(lib().fe_boundary_pattern(C.byref(mesh), flags, _stream(stream), C.byref(h)))
     return Pattern(h)
+
+
+def fe_pk_pattern(q: torch.Tensor, me: torch.Tensor, k: int, flags: int = 0, stream=None) -> Pattern:
+    """Pattern of a P_k mesh (App. D): me has (d+k)!/(d! k!) rows in the node order of
+    include/fe.h (vertices first); fe_assemble_mass then gives the P_k mass matrix."""
+    d = q.shape[0]
+    ndfe = 1
+    for i in range(1, d + 1):
+        ndfe = ndfe * (k + i) // i
+    if me.dim() != 2 or me.shape[0] != ndfe:
+        raise ValueError(f"me must be ({ndfe}, nme) for P{k} elements in {d}D")
+    mesh = _Mesh(d, q.shape[1], me.shape[1], _dev(q, torch.float64, "q").value, _dev(me, torch.int32, "me").value)
+    h = C.c_void_p()
+    _check(lib().fe_pk_pattern(C.byref(mesh), k, flags, _stream(stream), C.byref(h)))
+    return Pattern(h)
+
+
+def fe_pk_mass_table(d: int, k: int):
+    """The constants C_{alpha,beta} of Eq. MatElemMassPk, (ndfe, ndfe) numpy float64."""
+    import numpy as np
+    n = 1
+    for i in range(1, d + 1):
+        n = n * (k + i) // i
+    out = np.zeros((n, n))
+    _check(lib().fe_pk_mass_table(d, k, out.ctypes.data_as(C.c_void_p)))
+    return out
 
 
 def fe_batch_pattern(qs: list, mes: list, m: int = 1, flags: int = 0, stream=None) -> Pattern:
