@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--N", type=int, default=100, help="cells per cube side (default 100: 6M tets)")
     ap.add_argument("--strategy", default="chunked", choices=["chunked", "gather", "atomic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the default pattern (chunk 512, count-ordered records, 256 threads) for every "
+                         "form instead of the autotuned one")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
     ap.add_argument("--workload", default="stiffness",
                     choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general", "pk"],
@@ -279,10 +282,22 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     hbm_peak, peak_src, sm_max = measured_peaks()
     stream = torch.cuda.current_stream()
+    # per form: the autotuned pattern (chunk size, record layout, threads; untimed, cached)
+    from paper_1401_3301_gb300 import tune
+    pats, tuning = {}, {}
+    for prec_name, prec in (("f64", fe.F64), ("f32", fe.F32), ("f64x", fe.F64X)):
+        if args.strategy == "chunked" and not args.no_tune:
+            best = tune.autotune(q, me, "stiff", prec)
+            pats[prec_name] = tune.tuned_pattern(q, me, "stiff", prec)
+            tuning[prec_name] = {k: best[k] for k in ("chunk", "layout", "threads", "strategy")}
+        else:
+            pats[prec_name] = p
     sampler = ClockSampler(local)
     forms = {}
     sampler.start()
     for prec_name, prec in (("f64", fe.F64), ("f32", fe.F32), ("f64x", fe.F64X)):
+        p = pats[prec_name]
+        info = p.plan_info()
         T = torch.float32 if prec == fe.F32 else torch.float64
         vals = torch.empty(p.nnz, dtype=T, device="cuda")
         for _ in range(args.warmup):
@@ -342,6 +357,8 @@ def run_gpu(args):
 
     # end-to-end through the public API with host buffers (selected form)
     prec = fe.F64 if args.prec == "f64" else fe.F32
+    p = pats[args.prec]
+    info = p.plan_info()
     T = torch.float64 if prec == fe.F64 else torch.float32
     q_host = torch.from_numpy(m.q).pin_memory()
     vals = torch.empty(p.nnz, dtype=T, device="cuda")
@@ -379,6 +396,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": sel["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {**workload_config(args.N), "strategy": args.strategy, "form": args.prec,
+                       "tuning": tuning or "default pattern",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "nnz": p.nnz, "pattern_build_ms": pattern_ms, "plan": info},

@@ -76,6 +76,12 @@ extern "C" {
 /* ---- pattern flags */
 #define FE_PATTERN_KEEP_ORDER 1 /* do not reorder elements internally (default:
                                    Morton order of element centroids) */
+#define FE_PATTERN_ENTITY_ORDER 2 /* keep each chunk's distinct vertices and edges in
+                                     nonzero order (default: by descending number of
+                                     incidences, so that the threads of a warp sum
+                                     lists of similar length; the nonzero order writes
+                                     neighbouring values together). Values are the
+                                     same bit for bit either way. */
 /* elements per chunk of the chunked reassembly, 32..4096 (0: the default, 512 in
    3D and 1024 in 2D for scalar problems, 256 / 512 for elasticity) */
 #define FE_PATTERN_CHUNK(c) ((int32_t)(c) << 8)

@@ -62,6 +62,7 @@ struct X64Args {
   const double* w;
   int w_kind;
   const int32_t* order;
+  const int32_t* me0;  // first row of the internal connectivity: corner 0 of each element
   const int32_t* ch_v_ptr;
   const int32_t* ch_e_ptr;
   const uint8_t* rec;
@@ -95,10 +96,11 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
   float2* Kd = (float2*)(smem + S.kd);
   float2* Ko = (float2*)(smem + S.ko);
 
-  // 0. coordinates relative to the chunk's first vertex (FP64), split into float pairs
+  // 0. coordinates relative to corner 0 of the chunk's first element (FP64), split into
+  //    float pairs; the reference does not depend on the record's vertex order
   double xr[D];
   {
-    const int64_t v0 = lv_vid[0];
+    const int64_t v0 = A.me0[e0];
 #pragma unroll
     for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
   }
@@ -286,6 +288,6 @@ int fe_launch_stiff_f64x(fe_pattern_s* h, const double* q, const void* w, int w_
   using namespace fe;
   if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
   X64Args A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, (const double*)w,
-            w_kind, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
+            w_kind, h->order, h->me_int, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
   return h->d == 3 ? launch<3>(h, A, (double*)vals, s) : launch<2>(h, A, (double*)vals, s);
 }

@@ -365,27 +365,87 @@ __global__ void k_rec_sizes(int64_t nme, int chunk, int nv, int np, int m, int64
   size16[c] = L.total / 16u;
 }
 
-// one block per chunk: copy the chunk's slices of the plan arrays into its record
-__global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, int m, const int32_t* ch_v_ptr,
-                           const int32_t* ch_e_ptr, const uint16_t* inc_v, const uint16_t* inc_e,
-                           const uint16_t* lv_off, const uint16_t* le_off, const int32_t* lv_vid,
-                           const int32_t* lv_dst, const int32_t* le_dst, const uint16_t* lv_str,
-                           const uint16_t* le_str, const uint32_t* off16, uint8_t* rec) {
+// Block-wide exclusive scan of one value per thread (blockDim.x a multiple of 32);
+// *total receives the block sum. ws: 32 words of shared scratch.
+__device__ uint32_t block_exscan(uint32_t v, uint32_t* ws, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < nw ? ws[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) ws[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t base = w ? ws[w - 1] : 0u;
+  *total = ws[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// Order the n local entities of a chunk by descending incidence count, ties in their
+// original order (a stable bucket pass per count value): perm[new] = old, and
+// noff[new] = the entity's first incidence in the new layout. cnt holds the counts.
+__device__ void order_by_count(const uint16_t* cnt, int32_t n, uint16_t* perm, uint16_t* noff, uint32_t* ws) {
+  __shared__ uint32_t mx;
+  if (threadIdx.x == 0) mx = 0;
+  __syncthreads();
+  uint32_t m = 0;
+  for (int32_t u = threadIdx.x; u < n; u += blockDim.x) m = max(m, (uint32_t)cnt[u]);
+  atomicMax(&mx, m);
+  __syncthreads();
+  const int top = (int)mx;
+  uint32_t base = 0;
+  for (int c = top; c >= 1; --c)
+    for (int32_t t0 = 0; t0 < n; t0 += blockDim.x) {
+      const int32_t u = t0 + threadIdx.x;
+      const uint32_t f = (u < n && cnt[u] == c) ? 1u : 0u;
+      uint32_t tot;
+      const uint32_t r = block_exscan(f, ws, &tot);
+      if (f) perm[base + r] = (uint16_t)u;
+      base += tot;
+    }
+  __syncthreads();
+  uint32_t carry = 0;
+  for (int32_t t0 = 0; t0 < n; t0 += blockDim.x) {
+    const int32_t u = t0 + threadIdx.x;
+    const uint32_t v = u < n ? cnt[perm[u]] : 0u;
+    uint32_t tot;
+    const uint32_t r = block_exscan(v, ws, &tot);
+    if (u < n) noff[u] = (uint16_t)(carry + r);
+    carry += tot;
+  }
+  __syncthreads();
+}
+
+// One block per chunk: copy the chunk's slices of the plan arrays into its record. With
+// `ordered`, the chunk's local vertices and edges are laid out by descending incidence
+// count (so that the threads of a warp, which take consecutive entities, loop over
+// similar counts); each entity's incidence list is copied unchanged, so its sum keeps
+// ascending element order. Dynamic shared memory: 6 bytes per entity of the largest
+// list when ordered.
+__global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, int m, bool ordered,
+                           const int32_t* ch_v_ptr, const int32_t* ch_e_ptr, const uint16_t* inc_v,
+                           const uint16_t* inc_e, const uint16_t* lv_off, const uint16_t* le_off,
+                           const int32_t* lv_vid, const int32_t* lv_dst, const int32_t* le_dst,
+                           const uint16_t* lv_str, const uint16_t* le_str, const uint32_t* off16,
+                           uint8_t* rec) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ uint32_t ws[32];
   const int64_t c = blockIdx.x;
   const int64_t ne = min((int64_t)chunk, nme - c * chunk);
   const int32_t vb = ch_v_ptr[c], nlv = ch_v_ptr[c + 1] - vb;
   const int32_t eb = ch_e_ptr[c], nle = ch_e_ptr[c + 1] - eb;
   const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, nlv, nle, m > 1);
   uint8_t* r = rec + (int64_t)off16[c] * 16;
-  if (m > 1) {
-    uint16_t* r_lv_str = (uint16_t*)(r + L.lv_str);
-    uint16_t* r_le_str = (uint16_t*)(r + L.le_str);
-    for (int32_t u = threadIdx.x; u < nlv; u += blockDim.x) r_lv_str[u] = lv_str[vb + u];
-    for (int32_t u = threadIdx.x; u < nle; u += blockDim.x) {
-      r_le_str[2 * u] = le_str[2 * (int64_t)(eb + u)];
-      r_le_str[2 * u + 1] = le_str[2 * (int64_t)(eb + u) + 1];
-    }
-  }
   uint16_t* r_inc_v = (uint16_t*)(r + L.inc_v);
   uint16_t* r_inc_e = (uint16_t*)(r + L.inc_e);
   uint16_t* r_lv_off = (uint16_t*)(r + L.lv_off);
@@ -393,22 +453,48 @@ __global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, int m, const 
   int32_t* r_lv_vid = (int32_t*)(r + L.lv_vid);
   int32_t* r_lv_dst = (int32_t*)(r + L.lv_dst);
   int32_t* r_le_dst = (int32_t*)(r + L.le_dst);
+  uint16_t* r_lv_str = (uint16_t*)(r + L.lv_str);
+  uint16_t* r_le_str = (uint16_t*)(r + L.le_str);
   const int64_t ibv = c * (int64_t)chunk * nv, ibe = c * (int64_t)chunk * np;
-  for (int64_t j = threadIdx.x; j < ne * nv; j += blockDim.x) r_inc_v[j] = inc_v[ibv + j];
-  for (int64_t j = threadIdx.x; j < ne * np; j += blockDim.x) r_inc_e[j] = inc_e[ibe + j];
-  for (int32_t u = threadIdx.x; u < nlv; u += blockDim.x) {
-    r_lv_off[u] = lv_off[vb + u];
-    r_lv_vid[u] = lv_vid[vb + u];
-    r_lv_dst[u] = lv_dst[vb + u];
-  }
-  for (int32_t u = threadIdx.x; u < nle; u += blockDim.x) {
-    r_le_off[u] = le_off[eb + u];
-    r_le_dst[2 * u] = le_dst[2 * (int64_t)(eb + u)];
-    r_le_dst[2 * u + 1] = le_dst[2 * (int64_t)(eb + u) + 1];
-  }
-  if (threadIdx.x == 0) {
-    r_lv_off[nlv] = (uint16_t)(ne * nv);
-    r_le_off[nle] = (uint16_t)(ne * np);
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool edges = pass == 1;
+    const int32_t n = edges ? nle : nlv, b0 = edges ? eb : vb;
+    const uint16_t* off = edges ? le_off : lv_off;
+    const uint16_t* inc = (edges ? inc_e : inc_v) + (edges ? ibe : ibv);
+    uint16_t* r_inc = edges ? r_inc_e : r_inc_v;
+    uint16_t* r_off = edges ? r_le_off : r_lv_off;
+    const uint32_t end = (uint32_t)(ne * (edges ? np : nv));
+    uint16_t* cnt = (uint16_t*)sm;
+    uint16_t* perm = cnt + n;
+    uint16_t* noff = perm + n;
+    if (ordered) {
+      for (int32_t u = threadIdx.x; u < n; u += blockDim.x)
+        cnt[u] = (uint16_t)((u + 1 < n ? off[b0 + u + 1] : end) - off[b0 + u]);
+      __syncthreads();
+      order_by_count(cnt, n, perm, noff, ws);
+    }
+    for (int32_t nu = threadIdx.x; nu < n; nu += blockDim.x) {
+      const int32_t u = ordered ? perm[nu] : nu;
+      const uint32_t o = off[b0 + u];
+      const uint32_t no = ordered ? noff[nu] : o;
+      const uint32_t k = (u + 1 < n ? off[b0 + u + 1] : end) - o;
+      for (uint32_t j = 0; j < k; ++j) r_inc[no + j] = inc[o + j];
+      r_off[nu] = (uint16_t)no;
+      if (!edges) {
+        r_lv_vid[nu] = lv_vid[vb + u];
+        r_lv_dst[nu] = lv_dst[vb + u];
+        if (m > 1) r_lv_str[nu] = lv_str[vb + u];
+      } else {
+        r_le_dst[2 * nu] = le_dst[2 * (int64_t)(eb + u)];
+        r_le_dst[2 * nu + 1] = le_dst[2 * (int64_t)(eb + u) + 1];
+        if (m > 1) {
+          r_le_str[2 * nu] = le_str[2 * (int64_t)(eb + u)];
+          r_le_str[2 * nu + 1] = le_str[2 * (int64_t)(eb + u) + 1];
+        }
+      }
+    }
+    if (threadIdx.x == 0) r_off[n] = (uint16_t)end;
+    __syncthreads();
   }
 }
 
@@ -595,19 +681,41 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     h->rec_bytes = (int64_t)total16 * 16;
     h->plan_bytes = h->rec_bytes + (int64_t)sizeof(int32_t) * 2 * (h->nchunks + 1);
     h->rec_max_bytes = (int64_t)max16 * 16;
-    k_rec_fill<<<(unsigned)h->nchunks, 256, 0, s>>>(nme, C, nv, npair, h->m, h->ch_v_ptr,
-                                                    h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off,
-                                                    h->le_off, h->lv_vid, h->lv_dst, h->le_dst,
-                                                    h->lv_str, h->le_str, h->rec_off16, h->rec);
-    FE_CUDA_TRY(cudaGetLastError());
-    // max local vertices of a chunk (shared-memory coordinate staging)
-    std::vector<int32_t> vp(h->nchunks + 1);
+    // largest local vertex / edge lists of a chunk (shared memory of the kernels)
+    std::vector<int32_t> vp(h->nchunks + 1), ep(h->nchunks + 1);
     FE_CUDA_TRY(cudaMemcpyAsync(vp.data(), h->ch_v_ptr, sizeof(int32_t) * (h->nchunks + 1),
                                 cudaMemcpyDeviceToHost, s));
+    FE_CUDA_TRY(cudaMemcpyAsync(ep.data(), h->ch_e_ptr, sizeof(int32_t) * (h->nchunks + 1),
+                                cudaMemcpyDeviceToHost, s));
     FE_CUDA_TRY(cudaStreamSynchronize(s));
-    int32_t mlv = 0;
-    for (int64_t c = 0; c < h->nchunks; ++c) mlv = vp[c + 1] - vp[c] > mlv ? vp[c + 1] - vp[c] : mlv;
+    int32_t mlv = 0, mle = 0;
+    for (int64_t c = 0; c < h->nchunks; ++c) {
+      mlv = vp[c + 1] - vp[c] > mlv ? vp[c + 1] - vp[c] : mlv;
+      mle = ep[c + 1] - ep[c] > mle ? ep[c + 1] - ep[c] : mle;
+    }
     h->max_lv = mlv;
+    const size_t fill_smem = 6u * (size_t)(mlv > mle ? mlv : mle) + 16u;
+    const bool ordered = fill_smem <= 227u * 1024u && !(h->flags & FE_PATTERN_ENTITY_ORDER);
+    static size_t fill_configured = 0;
+    if (ordered) FE_TRY(fe_smem_limit(k_rec_fill, fill_smem, fill_configured));
+    k_rec_fill<<<(unsigned)h->nchunks, 256, ordered ? fill_smem : 0, s>>>(
+        nme, C, nv, npair, h->m, ordered, h->ch_v_ptr, h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off,
+        h->le_off, h->lv_vid, h->lv_dst, h->le_dst, h->lv_str, h->le_str, h->rec_off16, h->rec);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_CUDA_TRY(cudaStreamSynchronize(s));
+    // the records hold everything the kernels read: release the plan's flat arrays
+    h->bytes -= (int64_t)sizeof(uint16_t) * nme * (nv + npair) + (int64_t)(2 + 4 + 4) * h->nlv +
+                (int64_t)(2 + 8) * h->nle + (h->m > 1 ? (int64_t)2 * h->nlv + (int64_t)4 * h->nle : 0);
+    uint16_t** u16[] = {&h->inc_v, &h->inc_e, &h->lv_off, &h->le_off, &h->lv_str, &h->le_str};
+    for (uint16_t** p : u16) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
+    int32_t** i32[] = {&h->lv_vid, &h->lv_dst, &h->le_dst};
+    for (int32_t** p : i32) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
   }
   // partial-sum scratch of 8-byte values: 2 per partial for scalar problems (the
   // general operator keeps one per edge orientation), m * m for the vector blocks
@@ -924,6 +1032,7 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
     // 5. chunk plan
     // shrink the chunk until the worst-case block's shared memory fits (227 KB)
     for (;;) {
+      const int64_t bytes_before = h->bytes;
       if ((rc = build_chunk_plan(h, &sb, tmp, s))) break;
       const uint32_t need =
           pk > 1 ? fe::pk_smem((uint32_t)nv, (uint32_t)h->npair, 8, (uint32_t)h->rec_max_bytes, (uint32_t)h->chunk).total
@@ -934,6 +1043,7 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
       if (need <= 227u * 1024u || h->chunk <= (pk > 1 ? 1 : 32)) break;
       if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
       free_plan(h);
+      h->bytes = bytes_before;
       h->chunk /= 2;
     }
     if (rc) break;

@@ -1,8 +1,9 @@
 """Autotuner of the fixed-pattern reassembly.
 
 For one mesh and operator it times the chunked kernel over a grid of chunk sizes
-(elements per block, i.e. work per thread) and threads per block, and optionally
-the two-pass gather and atomic strategies, with CUDA events (median of `reps`
+(elements per block, i.e. work per thread), the two layouts of the chunk records
+(distinct vertices and edges by incidence count, or in nonzero order) and threads
+per block, and optionally the two-pass gather and atomic strategies, with CUDA events (median of `reps`
 calls after one warm-up). The winner is cached in a JSON file keyed by GPU name,
 dimension, dofs per vertex, operator, precision and the element count's power of
 two, so later meshes of the same class reuse it without timing.
@@ -20,6 +21,8 @@ from . import build_ext, fe
 
 CHUNKS = (256, 384, 512, 768, 1024)
 THREADS = (128, 256, 512)
+LAYOUTS = (0, fe.PATTERN_ENTITY_ORDER)
+_FORM = {fe.F64: "f64", fe.F32: "f32", fe.F64X: "f64x"}
 
 
 def cache_path() -> str:
@@ -28,7 +31,7 @@ def cache_path() -> str:
 
 def _key(d, m, kind, prec, nme) -> str:
     name = torch.cuda.get_device_name().replace(" ", "_")
-    return f"{name}|d{d}|m{m}|{kind}|{'f64' if prec == fe.F64 else 'f32'}|2^{int(math.log2(max(nme, 1)))}"
+    return f"{name}|d{d}|m{m}|{kind}|{_FORM[prec]}|2^{int(math.log2(max(nme, 1)))}"
 
 
 def _call(p, q, kind, prec, w, w_kind, vals):
@@ -61,9 +64,9 @@ def _load(path):
 
 
 def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int = fe.F64, w=None,
-             w_kind: int | None = None, reps: int = 10, chunks=CHUNKS, threads=THREADS,
+             w_kind: int | None = None, reps: int = 10, chunks=CHUNKS, threads=THREADS, layouts=LAYOUTS,
              deterministic_only: bool = True, use_cache: bool = True) -> dict:
-    """Best {strategy, chunk, threads, ms} for this mesh class, from the cache or by timing."""
+    """Best {strategy, chunk, layout, threads, ms} for this mesh class, from the cache or by timing."""
     if w_kind is None:
         w_kind = fe.COEF_NONE if w is None else fe.COEF_P0
     d, nme = q.shape[0], me.shape[1]
@@ -72,24 +75,25 @@ def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int =
     cache = _load(path)
     if use_cache and key in cache:
         return cache[key]
-    T = torch.float64 if prec == fe.F64 else torch.float32
+    T = torch.float32 if prec == fe.F32 else torch.float64
     results = []
     vals = None
     for c in chunks:
-        p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(c))
-        if vals is None:
-            vals = torch.empty(p.nnz, dtype=T, device=q.device)
-        for t in threads:
-            p.set_threads(t)
-            ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals), reps)
-            results.append({"strategy": "chunked", "chunk": c, "threads": t, "ms": ms})
-        p.destroy()
+        for lay in layouts:
+            p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(c) | lay)
+            if vals is None:
+                vals = torch.empty(p.nnz, dtype=T, device=q.device)
+            for t in threads:
+                p.set_threads(t)
+                ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals), reps)
+                results.append({"strategy": "chunked", "chunk": c, "layout": lay, "threads": t, "ms": ms})
+            p.destroy()
     if not deterministic_only:
         p = fe.fe_pattern(q, me)
         for name, s in (("gather", fe.REASM_GATHER), ("atomic", fe.REASM_ATOMIC)):
             p.set_strategy(s)
             ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals), reps)
-            results.append({"strategy": name, "chunk": 0, "threads": 256, "ms": ms})
+            results.append({"strategy": name, "chunk": 0, "layout": 0, "threads": 256, "ms": ms})
         p.destroy()
     best = dict(min(results, key=lambda r: r["ms"]))
     best["tried"] = len(results)
@@ -107,7 +111,8 @@ def tuned_pattern(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: 
     """A pattern built and configured with the autotuned chunk size, threads and strategy."""
     best = autotune(q, me, kind=kind, prec=prec, **kw)
     strategy = {"chunked": fe.REASM_CHUNKED, "gather": fe.REASM_GATHER, "atomic": fe.REASM_ATOMIC}[best["strategy"]]
-    p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(best["chunk"]) if best["chunk"] else 0)
+    flags = (fe.PATTERN_CHUNK(best["chunk"]) if best["chunk"] else 0) | best.get("layout", 0)
+    p = fe.fe_pattern(q, me, flags=flags)
     p.set_strategy(strategy)
     p.set_threads(best["threads"])
     return p
