@@ -152,6 +152,25 @@ int fe_batch_gather_q(fe_pattern_h h, const fe_mesh* meshes, double* q_union, vo
 int fe_boundary_pattern(const fe_mesh* facets, int32_t flags, void* stream, fe_pattern_h* out);
 
 /*
+ * Vertex renumbering along a Morton curve (a caller-side utility: the library never
+ * renumbers the matrix itself, which keeps the caller's vertex numbering).
+ *
+ * fe_morton_vertex_order -- order[i] = the vertex placed at position i: vertices sorted by
+ * the Morton code of their coordinates (21 bits per axis over the bounding box, bits
+ * interleaved x fastest), ties by vertex id. q: d x nq SoA, device; order: nq int32,
+ * device. Synchronous (allocates and frees scratch).
+ *
+ * fe_apply_vertex_order -- the renumbered mesh: q_out[:, i] = q[:, order[i]] and
+ * me_out = new ids of me (nv x nme, any number of rows, e.g. a P_k or a facet mesh).
+ * All device pointers; q_out and me_out must not alias the inputs. FE_ERR_INDEX if
+ * order has an entry outside [0, nq) or me one outside [0, nq) (those entries are left
+ * unspecified). Synchronous.
+ */
+int fe_morton_vertex_order(int32_t d, int64_t nq, const double* q, int32_t* order, void* stream);
+int fe_apply_vertex_order(int32_t d, int64_t nq, int64_t nme, int32_t nv, const double* q, const int32_t* me,
+                          const int32_t* order, double* q_out, int32_t* me_out, void* stream);
+
+/*
  * fe_pk_pattern -- pattern of a P_k mesh (App. D): q holds the coordinates of all
  * P_k nodes (d x nq) and mesh->me has ndfe = (d+k)!/(d! k!) rows, the nodes of each
  * element in the local order: the d+1 vertices (multi-indices k e_0, ..., k e_d)

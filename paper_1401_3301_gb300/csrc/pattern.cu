@@ -878,6 +878,105 @@ extern "C" int fe_batch_gather_q(fe_pattern_h h, const fe_mesh* meshes, double* 
 }
 
 namespace {
+// Morton code of each vertex: quantised coordinates (qbits per axis, over the bounding
+// box), bits interleaved; value = vertex id (the sort is stable, so ties keep id order).
+__global__ void k_vertex_morton_keys(const double* q, int64_t nq, int d, const double* bbox, int qbits,
+                                     uint64_t* keys, uint32_t* vals) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= nq) return;
+  const double scale = (double)(1u << qbits);
+  uint64_t code = 0;
+  for (int c = 0; c < d; ++c) {
+    const double lo = bbox[c], hi = bbox[d + c];
+    double t = (hi > lo) ? (q[(int64_t)c * nq + v] - lo) / (hi - lo) : 0.0;
+    t = fmin(fmax(t, 0.0), 1.0);
+    uint64_t iq = (uint64_t)(t * scale);
+    if (iq >= (1ull << qbits)) iq = (1ull << qbits) - 1;
+    code |= spread_bits(iq, d) << c;
+  }
+  keys[v] = code;
+  vals[v] = (uint32_t)v;
+}
+
+// inverse permutation; flags an entry of `order` outside [0, n)
+__global__ void k_invert_order(const int32_t* order, int64_t n, int32_t* inv, int32_t* bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t o = order[i];
+  if (o < 0 || o >= n) { atomicExch(bad, 1); return; }
+  inv[o] = (int32_t)i;
+}
+
+__global__ void k_gather_q(const double* q, int64_t nq, int d, const int32_t* order, double* q_out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const int32_t o = order[i];
+  if (o < 0 || o >= nq) return;
+  for (int c = 0; c < d; ++c) q_out[(int64_t)c * nq + i] = q[(int64_t)c * nq + o];
+}
+
+__global__ void k_renumber_me(const int32_t* me, int64_t n, int64_t nq, const int32_t* inv, int32_t* me_out,
+                              int32_t* bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t v = me[i];
+  if (v < 0 || v >= nq) { atomicExch(bad, 2); me_out[i] = -1; return; }
+  me_out[i] = inv[v];
+}
+}  // namespace
+
+extern "C" int fe_morton_vertex_order(int32_t d, int64_t nq, const double* q, int32_t* order, void* stream) {
+  if ((d != 2 && d != 3) || nq < 1 || nq > INT32_MAX || !q || !order) return FE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int T = 256, qbits = 21;
+  dev_tmp tmp;
+  fe_sort_buffers sb;
+  double* bb;
+  FE_TRY(tmp.get(&sb.k0, nq));
+  FE_TRY(tmp.get(&sb.k1, nq));
+  FE_TRY(tmp.get(&sb.v0, nq));
+  FE_TRY(tmp.get(&sb.v1, nq));
+  FE_TRY(tmp.get(&sb.hist, fe_sort_hist_size(nq)));
+  FE_TRY(tmp.get(&sb.scan_tmp, fe_scan_tmp_size((int64_t)fe_sort_hist_size(nq)) + fe_scan_tmp_size(nq)));
+  FE_TRY(tmp.get(&bb, (size_t)256 * 2 * d));
+  k_bbox_partial<<<256, 256, 0, s>>>(q, nq, d, bb);
+  k_bbox_final<<<1, 32, 0, s>>>(bb, 256, d);
+  k_vertex_morton_keys<<<fe_grid(nq, T), T, 0, s>>>(q, nq, d, bb, qbits, sb.k0, sb.v0);
+  FE_CUDA_TRY(cudaGetLastError());
+  uint64_t* keys;
+  uint32_t* vals;
+  FE_TRY(fe_radix_sort(nq, qbits * d, &sb, &keys, &vals, s));
+  FE_CUDA_TRY(cudaMemcpyAsync(order, vals, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, s));
+  FE_CUDA_TRY(cudaStreamSynchronize(s));  // the scratch is released on return
+  return FE_OK;
+}
+
+extern "C" int fe_apply_vertex_order(int32_t d, int64_t nq, int64_t nme, int32_t nv, const double* q,
+                                     const int32_t* me, const int32_t* order, double* q_out,
+                                     int32_t* me_out, void* stream) {
+  if ((d != 2 && d != 3) || nq < 1 || nq > INT32_MAX || nme < 0 || nv < 1 || !q || !me || !order ||
+      !q_out || !me_out)
+    return FE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int T = 256;
+  dev_tmp tmp;
+  int32_t *inv, *bad;
+  FE_TRY(tmp.get(&inv, nq));
+  FE_TRY(tmp.get(&bad, 1));
+  FE_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
+  FE_CUDA_TRY(cudaMemsetAsync(inv, 0xFF, sizeof(int32_t) * nq, s));
+  k_invert_order<<<fe_grid(nq, T), T, 0, s>>>(order, nq, inv, bad);
+  k_gather_q<<<fe_grid(nq, T), T, 0, s>>>(q, nq, d, order, q_out);
+  const int64_t n = nme * nv;
+  if (n > 0) k_renumber_me<<<fe_grid(n, T), T, 0, s>>>(me, n, nq, inv, me_out, bad);
+  FE_CUDA_TRY(cudaGetLastError());
+  int32_t flag = 0;
+  FE_CUDA_TRY(cudaMemcpyAsync(&flag, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FE_CUDA_TRY(cudaStreamSynchronize(s));
+  return flag ? FE_ERR_INDEX : FE_OK;
+}
+
+namespace {
 void free_plan(fe_pattern_s* h) {
   void** ptrs[] = {(void**)&h->ch_v_ptr, (void**)&h->ch_e_ptr, (void**)&h->lv_off, (void**)&h->le_off,
                    (void**)&h->inc_v,    (void**)&h->inc_e,    (void**)&h->lv_dst, (void**)&h->lv_vid,

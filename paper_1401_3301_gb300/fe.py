@@ -61,6 +61,8 @@ def lib() -> C.CDLL:
         L.fe_assemble_general.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_pk_pattern.argtypes = [P, I32, I32, P, P]
         L.fe_pk_mass_table.argtypes = [I32, I32, P]
+        L.fe_morton_vertex_order.argtypes = [I32, I64, P, P, P]
+        L.fe_apply_vertex_order.argtypes = [I32, I64, I64, I32, P, P, P, P, P, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff_vjp.argtypes = [P, P, P, I32, P, P, P, I32, P]
@@ -81,7 +83,8 @@ def lib() -> C.CDLL:
                      "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
                      "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads",
-                     "fe_boundary_pattern", "fe_assemble_general", "fe_pk_pattern", "fe_pk_mass_table"):
+                     "fe_boundary_pattern", "fe_assemble_general", "fe_pk_pattern", "fe_pk_mass_table",
+                     "fe_morton_vertex_order", "fe_apply_vertex_order"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -257,6 +260,27 @@ def fe_pk_pattern(q: torch.Tensor, me: torch.Tensor, k: int, flags: int = 0, str
     h = C.c_void_p()
     _check(lib().fe_pk_pattern(C.byref(mesh), k, flags, _stream(stream), C.byref(h)))
     return Pattern(h)
+
+
+def fe_morton_vertex_order(q: torch.Tensor, stream=None) -> torch.Tensor:
+    """order[i] = the vertex placed at position i along a Morton curve (int32, on q's device)."""
+    d, nq = q.shape
+    order = torch.empty(nq, dtype=torch.int32, device=q.device)
+    _check(lib().fe_morton_vertex_order(d, nq, _dev(q, torch.float64, "q"), _dev(order, torch.int32, "order"),
+                                        _stream(stream)))
+    return order
+
+
+def fe_apply_vertex_order(q: torch.Tensor, me: torch.Tensor, order: torch.Tensor, stream=None):
+    """(q_out, me_out): the mesh with vertex order[i] renumbered i."""
+    d, nq = q.shape
+    q_out = torch.empty_like(q)
+    me_out = torch.empty_like(me)
+    _check(lib().fe_apply_vertex_order(d, nq, me.shape[1], me.shape[0], _dev(q, torch.float64, "q"),
+                                       _dev(me, torch.int32, "me"), _dev(order, torch.int32, "order"),
+                                       _dev(q_out, torch.float64, "q_out"), _dev(me_out, torch.int32, "me_out"),
+                                       _stream(stream)))
+    return q_out, me_out
 
 
 def fe_pk_mass_table(d: int, k: int):
