@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--N", type=int, default=100, help="cells per cube side (default 100: 6M tets)")
     ap.add_argument("--strategy", default="chunked", choices=["chunked", "gather", "atomic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help='per-form pattern configuration as JSON, e.g. \'{"f64": {"chunk": 384, "layout": 0, '
+                         '"threads": 256}}\' (the dict a run prints in config.tuning); forms it names skip the '
+                         'autotuner')
     ap.add_argument("--no-tune", action="store_true",
                     help="use the default pattern (chunk 512, count-ordered records, 256 threads) for every "
                          "form instead of the autotuned one")
@@ -285,8 +289,15 @@ def run_gpu(args):
     # per form: the autotuned pattern (chunk size, record layout, threads; untimed, cached)
     from paper_1401_3301_gb300 import tune
     pats, tuning = {}, {}
+    pinned = json.loads(args.tuning) if args.tuning else {}
     for prec_name, prec in (("f64", fe.F64), ("f32", fe.F32), ("f64x", fe.F64X)):
-        if args.strategy == "chunked" and not args.no_tune:
+        if args.strategy == "chunked" and prec_name in pinned:
+            cfg = pinned[prec_name]
+            pats[prec_name] = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(cfg["chunk"]) | cfg.get("layout", 0))
+            pats[prec_name].set_threads(cfg.get("threads", 256))
+            tuning[prec_name] = {"chunk": cfg["chunk"], "layout": cfg.get("layout", 0),
+                                 "threads": cfg.get("threads", 256), "strategy": "chunked", "pinned": True}
+        elif args.strategy == "chunked" and not args.no_tune:
             best = tune.autotune(q, me, "stiff", prec)
             pats[prec_name] = tune.tuned_pattern(q, me, "stiff", prec)
             tuning[prec_name] = {k: best[k] for k in ("chunk", "layout", "threads", "strategy")}
