@@ -319,6 +319,25 @@ int fe_assemble_general(fe_pattern_h h, const double* q, const void* coef, int32
                         int32_t prec, void* vals, void* stream);
 
 /*
+ * fe_assemble_stiff_host -- fe_assemble_stiff with HOST buffers: q_host (d x nq
+ * doubles, SoA), w_host (nme values of the form's precision, input element order, with
+ * w_kind FE_COEF_P0; or NULL with FE_COEF_NONE) and vals_host (nnz values of the form's
+ * precision) are in host memory, page-locked for the copies to be asynchronous. Forms
+ * FE_F64, FE_F32 and FE_F64X.
+ * The call returns at once; `stream` waits for the result to reach vals_host, so
+ * synchronise it (or an event recorded on it) before reading vals_host. Successive calls
+ * overlap: the pattern owns three streams (upload, assembly, download) and two device
+ * staging slots, so call k's assembly runs beside call k+1's upload and call k-1's
+ * download. The caller must not change q_host / w_host until the call's result is back
+ * (or the next-but-one call on the pattern has started), nor read vals_host before.
+ * The first call allocates the slots (2 x (q + values) on the device; w on demand).
+ * Assemblies on one pattern share its scratch: do not mix this call with device-memory
+ * calls on another stream without ordering them.
+ */
+int fe_assemble_stiff_host(fe_pattern_h h, const double* q_host, const void* w_host, int32_t w_kind,
+                           int32_t prec, void* vals_host, void* stream);
+
+/*
  * fe_assemble_stiff_backward -- gradients of L = u^T S(w) v, S the stiffness
  * matrix of fe_assemble_stiff, without forming any matrix (the paper has no
  * derivatives; these follow from Eq. stiffelemmat and App. C.1). Per element,

@@ -44,6 +44,7 @@ int fe_malloc(fe_pattern_s* h, void** p, size_t bytes) {
 }
 
 void fe_free_all(fe_pattern_s* h) {
+  fe_host_pipe_free(h);  // first: its streams may still hold work on the pattern's buffers
   void* ptrs[] = {h->me_int,  h->order,    h->row_ptr_s, h->col_idx_s, h->slot2nnz,
                   h->nnz_slot_ptr, h->nnz2slot, h->ch_v_ptr, h->ch_e_ptr, h->lv_off,
                   h->le_off,  h->inc_v,    h->inc_e,     h->lv_dst,    h->lv_vid,

@@ -37,6 +37,8 @@ __device__ __forceinline__ void fe_report(fe_status_word* st, int32_t code, long
 // ---------------------------------------------------------------- pattern handle
 struct fe_prof_state;
 void fe_prof_free(struct fe_pattern_s* h);
+struct fe_host_pipe;
+void fe_host_pipe_free(struct fe_pattern_s* h);
 
 struct fe_pattern_s {
   int d = 0, m = 1, nv = 0, npair = 0, flags = 0, strategy = FE_REASM_CHUNKED;
@@ -89,6 +91,7 @@ struct fe_pattern_s {
   void* bwd_lpart = nullptr;        // backward: per-block partial sums of L
   fe_status_word* status = nullptr;
   fe_prof_state* prof = nullptr;    // per-kernel event timing (fe_profile)
+  fe_host_pipe* pipe = nullptr;     // host-buffer calls: streams, events, staging (host.cu)
   std::vector<int64_t> batch_voff, batch_eoff, batch_noff;  // batches: per-mesh offsets
   int64_t bytes = 0;
 };

@@ -62,6 +62,7 @@ def lib() -> C.CDLL:
         L.fe_pk_pattern.argtypes = [P, I32, I32, P, P]
         L.fe_pk_mass_table.argtypes = [I32, I32, P]
         L.fe_morton_vertex_order.argtypes = [I32, I64, P, P, P]
+        L.fe_assemble_stiff_host.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_apply_vertex_order.argtypes = [I32, I64, I64, I32, P, P, P, P, P, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
@@ -84,7 +85,7 @@ def lib() -> C.CDLL:
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
                      "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads",
                      "fe_boundary_pattern", "fe_assemble_general", "fe_pk_pattern", "fe_pk_mass_table",
-                     "fe_morton_vertex_order", "fe_apply_vertex_order"):
+                     "fe_morton_vertex_order", "fe_apply_vertex_order", "fe_assemble_stiff_host"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -351,6 +352,27 @@ def fe_assemble_stiff(p: Pattern, q: torch.Tensor, w: torch.Tensor | None = None
     _check(lib().fe_assemble_stiff(p.handle, _dev(q, torch.float64, "q"), _dev(w, _vtype(prec), "w"),
                                    w_kind, prec, _dev(vals, _vtype(prec), "vals"), _stream(stream)))
     return vals
+
+
+def fe_assemble_stiff_host(p: Pattern, q_host: torch.Tensor, vals_host: torch.Tensor, w_host=None,
+                           prec: int = F64, stream=None):
+    """fe_assemble_stiff from and to host tensors (pin them for overlap); asynchronous on
+    `stream` like the device calls: synchronise before reading vals_host."""
+    def host(t, dtype, name):
+        if t is None:
+            return None
+        if t.device.type != "cpu" or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU tensor of dtype {dtype}")
+        return C.c_void_p(t.data_ptr())
+    T = _vtype(prec)
+    if vals_host.numel() != p.nnz:
+        raise ValueError("vals_host must hold nnz values")
+    if q_host.shape != (p.d, p.nq):
+        raise ValueError("q_host must be (d, nq)")
+    _check(lib().fe_assemble_stiff_host(p.handle, host(q_host, torch.float64, "q_host"), host(w_host, T, "w_host"),
+                                        COEF_NONE if w_host is None else COEF_P0, prec,
+                                        host(vals_host, T, "vals_host"), _stream(stream)))
+    return vals_host
 
 
 def fe_assemble_elas(p: Pattern, q: torch.Tensor, lam: torch.Tensor, lam_kind: int, mu: torch.Tensor,
