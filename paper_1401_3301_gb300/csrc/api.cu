@@ -58,7 +58,6 @@ void fe_free_all(fe_pattern_s* h) {
     if (h->row_ptr) cudaFree(h->row_ptr);
     if (h->col_idx) cudaFree(h->col_idx);
   }
-  if (h->elas_dst) cudaFree(h->elas_dst);
   fe_prof_free(h);
 }
 

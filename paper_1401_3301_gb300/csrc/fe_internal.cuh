@@ -56,7 +56,9 @@ struct fe_pattern_s {
   int32_t* slot2nnz = nullptr;      // nme (d+1)^2
   int32_t* nnz_slot_ptr = nullptr;  // nnz_s + 1
   int32_t* nnz2slot = nullptr;      // nme (d+1)^2
-  // element-chunk plan (FE_REASM_CHUNKED and the vertex sums of the backward pass)
+  // element-chunk plan (FE_REASM_CHUNKED). The flat arrays from lv_off to le_str exist
+  // only while the plan is built: the per-chunk records (rec) hold copies of their
+  // slices, and the flat arrays are released once the records are filled.
   int chunk = 0;
   int64_t nchunks = 0, nlv = 0, nle = 0;
   int32_t* ch_v_ptr = nullptr;      // nchunks + 1: local vertices of chunk c
@@ -84,7 +86,6 @@ struct fe_pattern_s {
   void* partials = nullptr; size_t partials_bytes = 0;
   void* kg = nullptr; size_t kg_bytes = 0;
   void* qsplit = nullptr; size_t qsplit_bytes = 0;
-  int32_t* elas_dst = nullptr;      // unused (kept zero)
   int32_t* vmap_ptr = nullptr;      // nq + 1: vertex -> incidences (backward pass, built on first use)
   int32_t* vmap = nullptr;          // nv nme: e * nv + a, ascending e within each vertex
   void* bwd_scratch = nullptr;      // backward: per-corner gradient contributions
