@@ -59,7 +59,8 @@ def parse():
                          "form instead of the autotuned one")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
     ap.add_argument("--workload", default="stiffness",
-                    choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general", "pk"],
+                    choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general", "pk",
+                             "boundary"],
                     help="stiffness (default, the headline); the others print one JSON line each "
                          "for the other configurations of the hot path")
     return ap.parse_args()
@@ -517,6 +518,30 @@ def run_other(args):
                           "(value: k = 2, FP64)", unit="M nodes/s",
                    config={"workload": "Kuhn cube, P_k lattice nodes, kN ~ 100 (about 1.03e6 nodes), jitter 0.15h, "
                                        "elements permuted", "hbm_peak_GBps": hbm_peak})
+    elif args.workload == "boundary":
+        # facet (boundary) mass and P1-weighted mass on a large triangulated surface in 3D
+        N = 2000 if args.N == 100 else args.N
+        m = meshgen.surface_mesh(N, seed=0)
+        q, f = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = fe.fe_boundary_pattern(q, f)
+        pms = (time.perf_counter() - t0) * 1e3
+        wv = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            w = wv.to(T)
+            res = {}
+            for label, fn in (("mass", lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)),
+                              ("wmass_p1", lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec, vals=vals))):
+                med, mean = _timed(fn, K, W, flush)
+                p.check()
+                res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+            out["forms"][name] = {"value": res["mass"]["value"], "operators": res}
+        out.update(metric="3D surface (facet) mass and P1-weighted mass, Mtris/s, fixed pattern", unit="Mtris/s",
+                   config={"workload": f"height-field surface over the unit square, N={N} ({m.nme:,} triangles, "
+                                       f"{m.nq:,} vertices), jitter 0.2h, vertices and elements permuted",
+                           "nnz": p.nnz, "pattern_build_ms": pms})
     elif args.workload == "elas":
         N = 80 if args.N == 100 else args.N
         m = meshgen.kuhn_cube_mesh(N, seed=0)

@@ -212,6 +212,15 @@ def pk_mesh(d: int, N: int, k: int, seed: int = 0, jitter: float | None = None, 
     return Mesh(d, np.ascontiguousarray(q), np.ascontiguousarray(me, dtype=np.int32))
 
 
+def surface_mesh(N: int, seed: int = 0) -> Mesh:
+    """A triangulated surface in 3D: the jittered, permuted unit-square mesh of
+    square_mesh(N) lifted to the height field z = 0.25 sin(2 pi x) cos(2 pi y). Returns
+    Mesh(d=3, q (3, nq), me (3, ntriangles)), a facet mesh for boundary operators."""
+    m = square_mesh(N, seed=seed)
+    z = 0.25 * np.sin(2.0 * np.pi * m.q[0]) * np.cos(2.0 * np.pi * m.q[1])
+    return Mesh(3, np.ascontiguousarray(np.vstack([m.q, z[None, :]])), m.me)
+
+
 def boundary_facets(mesh: Mesh) -> np.ndarray:
     """Facets (d-1 simplices) that belong to exactly one element: (d, nfacets) int32,
     vertex indices into the same q, in the order of first appearance."""

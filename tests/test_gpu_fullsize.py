@@ -172,3 +172,25 @@ def test_batch_of_256_meshes_sampled_meshes():
         ra, rb = ref["row_ptr"][r], ref["row_ptr"][r + 1]
         np.testing.assert_array_equal(ci[a:e] - base, ref["col_idx"][ra:rb])
         assert normalised_error(s[a:e], ref["val"][ra:rb], ref["scale"][ra:rb]) <= 1e-12
+
+
+def test_surface_n2000_boundary_mass_sampled_rows():
+    # the facet workload of the benchmark: 8,000,000 triangles in 3D
+    fe = fe_or_skip()
+    import torch
+    m = meshgen.surface_mesh(2000, seed=0)
+    q, f = to_cuda(m.q), to_cuda(m.me)
+    p = fe.fe_boundary_pattern(q, f)
+    wv = meshgen.vertex_weights(0, m.nq)
+    rows = np.random.default_rng(5).choice(m.nq, 200, replace=False)
+    keep = sub_mesh_rows(m.me, rows, m.nq)
+    sub = np.ascontiguousarray(m.me[:, keep])
+    rp, ci = (t.cpu().numpy() for t in p.csr())
+    for prec in (0, 1):
+        T = torch.float64 if prec == 0 else torch.float32
+        mass = fe.fe_assemble_mass(p, q, prec=prec).double().cpu().numpy()
+        check_rows(rp, ci, mass, oracle.assemble_boundary(oracle.MASS, m.q, sub), rows, TOL[prec])
+        wm = fe.fe_assemble_wmass(p, q, to_cuda(wv).to(T), fe.COEF_P1, prec=prec).double().cpu().numpy()
+        check_rows(rp, ci, wm, oracle.assemble_boundary(oracle.WMASS, m.q, sub, c1=(oracle.COEF_P1, wv)), rows,
+                   TOL[prec])
+        assert p.status() == (0, -1)
