@@ -83,7 +83,7 @@ extern "C" {
                                      neighbouring values together). Values are the
                                      same bit for bit either way. */
 /* elements per chunk of the chunked reassembly, 32..4096 (0: the default, 512 in
-   3D and 1024 in 2D for scalar problems, 256 / 512 for elasticity) */
+   3D and 1024 in 2D) */
 #define FE_PATTERN_CHUNK(c) ((int32_t)(c) << 8)
 
 typedef struct fe_mesh {

@@ -260,26 +260,25 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   }
 }
 
-// Sum, in chunk order, of the partial blocks of each shared vertex / edge.
+// Sum, in chunk order, of the partial blocks of each shared vertex / edge: one thread per
+// (entity, block entry), so that neighbouring threads read neighbouring words of the
+// partial blocks (partial i of the entity holds its m x m block at i * MM).
 template <int D, class T>
 __global__ void k_fixup_elas(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
                              const int32_t* __restrict__ sh_str, int64_t nsh_v, int64_t nsh,
                              const void* __restrict__ partials, T* __restrict__ vals) {
   constexpr int MM = D * D;
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= nsh) return;
+  const int64_t gk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gk >= nsh * MM) return;
+  const int64_t g = gk / MM;
+  const int k = (int)(gk - g * MM);
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
-  const int32_t dst = sh_dst[2 * g];
-  const int str = sh_str[2 * g];
-#pragma unroll
-  for (int k = 0; k < MM; ++k) {
-    Acc<T> acc = Acc<T>::from_partial(partials, (int64_t)s * MM + k);
-    for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, (int64_t)i * MM + k);
-    const T v = acc.value();
-    const int l = k / D, n = k % D;
-    vals[dst + l * str + n] = v;
-    if (g >= nsh_v) vals[sh_dst[2 * g + 1] + n * sh_str[2 * g + 1] + l] = v;
-  }
+  Acc<T> acc = Acc<T>::from_partial(partials, (int64_t)s * MM + k);
+  for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, (int64_t)i * MM + k);
+  const T v = acc.value();
+  const int l = k / D, n = k % D;
+  vals[sh_dst[2 * g] + l * sh_str[2 * g] + n] = v;
+  if (g >= nsh_v) vals[sh_dst[2 * g + 1] + n * sh_str[2 * g + 1] + l] = v;
 }
 
 template <int D, class T>
@@ -297,8 +296,8 @@ int launch(fe_pattern_s* h, const ElasArgs& A, T* vals, cudaStream_t s) {
   const int64_t nsh = h->nsh_v + h->nsh_e;
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_ELAS_FIXUP, s);
-    k_fixup_elas<D, T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->sh_str, h->nsh_v, nsh,
-                                                         h->partials, vals);
+    k_fixup_elas<D, T><<<fe_grid(nsh * D * D, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->sh_str, h->nsh_v,
+                                                                 nsh, h->partials, vals);
     FE_CUDA_TRY(cudaGetLastError());
     FE_PROF_END(h, FE_K_ELAS_FIXUP, s);
   }

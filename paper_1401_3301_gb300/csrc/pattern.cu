@@ -529,8 +529,7 @@ int default_chunk(int d, int m, int flags) {
     const int c = atoi(env);
     if (c >= 32 && c <= 4096) return c;
   }
-  if (m == 1) return d == 3 ? 512 : 1024;
-  return d == 3 ? 256 : 512;
+  return d == 3 ? 512 : 1024;  // scalar and vector problems alike
 }
 
 // Builds the element-chunk plan. sort buffers sized for max(nv, npair) * nme keys.
