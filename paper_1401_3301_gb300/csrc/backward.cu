@@ -10,7 +10,9 @@
 // the derivative of |det B| / d! and of g_a = B^{-T} g^_a with respect to the
 // columns q^i - q^0 of B (the vertex-0 column is minus the sum of the others, which
 // the same formula gives because sum_a g_a = 0). With cofactor vectors c_a = det B g_a
-// everything is a polynomial in c scaled by 1/(d! |det B|) (and a sign for dq).
+// everything is a polynomial in c scaled by 1/(d! |det B|) (and a sign for dq). The
+// kernel evaluates it through the D x D matrix W = C^T (G^ + G^T) C: t = tr(W) / 2 and
+// sum_x g_x (G^s Gamma)_xc = W c_c / det^2, so dL/dq^c = w / (d! det |det|) (t I - W) c_c.
 // Two sources of G^:
 //   rank one, G^_ab = u(me(a)) v(me(b)):  L = u^T S(w) v without forming any matrix;
 //   general, G^_ab = dL/dS at the nonzero of slot (a, b) (a vector-Jacobian product
@@ -70,41 +72,75 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem(BwdArgs A) {
       g.det = T(1);
     }
     form_c0<D, T>(g);
-    T Gh[NV][NV];
+    // W = C^T (G^ + G^T) C (D x D, C the NV x D matrix of cofactor vectors): then
+    // t = sum_ab G^_ab c_a . c_b = tr(W) / 2, and the bracket of dL/dq^c is
+    // t c_c - sum_x c_x (G^s Gamma)_xc = (t I - W) c_c.
+    T W[D][D];
     if constexpr (RANK1) {
+      // G^ = u v^T: W = ub vb^T + vb ub^T with ub = sum_a u_a c_a, vb = sum_a v_a c_a
       const T* u = (const T*)A.u;
       const T* v = (const T*)A.v;
-      T uu[NV], vw[NV];
+      T ub[D], vb[D];
+      {
+        const T u0 = u[vv[0]], v0 = v[vv[0]];
 #pragma unroll
-      for (int a = 0; a < NV; ++a) { uu[a] = u[vv[a]]; vw[a] = v[vv[a]]; }
+        for (int k = 0; k < D; ++k) {
+          ub[k] = u0 * g.c[0][k];
+          vb[k] = v0 * g.c[0][k];
+        }
+      }
 #pragma unroll
-      for (int a = 0; a < NV; ++a)
+      for (int a = 1; a < NV; ++a) {
+        const T ua = u[vv[a]], va = v[vv[a]];
 #pragma unroll
-        for (int b = 0; b < NV; ++b) Gh[a][b] = uu[a] * vw[b];
+        for (int k = 0; k < D; ++k) {
+          ub[k] += ua * g.c[a][k];
+          vb[k] += va * g.c[a][k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int j = k; j < D; ++j) {
+          W[k][j] = ub[k] * vb[j] + vb[k] * ub[j];
+          W[j][k] = W[k][j];
+        }
     } else {
       const T* gv = (const T*)A.grad_vals;
       const int32_t* m = A.slot2nnz + e * NV * NV;
+      T Gs[NV][NV];  // G^ + G^T, G^_ab = dL/dS at the nonzero of slot (row a, column b)
 #pragma unroll
       for (int a = 0; a < NV; ++a)
 #pragma unroll
-        for (int b = 0; b < NV; ++b) Gh[a][b] = gv[m[b * NV + a]];
+        for (int b = a; b < NV; ++b) {
+          Gs[a][b] = gv[m[b * NV + a]] + gv[m[a * NV + b]];
+          Gs[b][a] = Gs[a][b];
+        }
+      T Pc[NV][D];  // (G^ + G^T) C
+#pragma unroll
+      for (int x = 0; x < NV; ++x)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          T p = Gs[x][0] * g.c[0][j];
+#pragma unroll
+          for (int y = 1; y < NV; ++y) p += Gs[x][y] * g.c[y][j];
+          Pc[x][j] = p;
+        }
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int j = k; j < D; ++j) {
+          T w = g.c[0][k] * Pc[0][j];
+#pragma unroll
+          for (int x = 1; x < NV; ++x) w += g.c[x][k] * Pc[x][j];
+          W[k][j] = w;
+          W[j][k] = w;
+        }
     }
-    T Gam[NV][NV];
+    T t = W[0][0];
 #pragma unroll
-    for (int a = 0; a < NV; ++a)
-#pragma unroll
-      for (int b = a; b < NV; ++b) {
-        T s = g.c[a][0] * g.c[b][0];
-#pragma unroll
-        for (int k = 1; k < D; ++k) s += g.c[a][k] * g.c[b][k];
-        Gam[a][b] = s;
-        Gam[b][a] = s;
-      }
-    T t = T(0);
-#pragma unroll
-    for (int a = 0; a < NV; ++a)
-#pragma unroll
-      for (int b = 0; b < NV; ++b) t += Gh[a][b] * Gam[a][b];
+    for (int k = 1; k < D; ++k) t += W[k][k];
+    t *= T(0.5);
     const T adet = tabs(g.det);
     const T inv = recip<T>(T(factorial(D)) * adet);   // |K| / det^2 = 1 / (d! |det|)
     const bool has_w = A.w_kind != FE_COEF_NONE;
@@ -113,26 +149,21 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem(BwdArgs A) {
     if (A.dLdw) ((T*)A.dLdw)[A.dLdw_internal ? e : A.order[e]] = dw;
     Le = w * dw;
     const T s = w * inv * recip<T>(g.det);            // w |K| / det^3 = w / (d! det |det|)
+    T Z[D][D];  // s (t I - W)
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int j = 0; j < D; ++j) Z[k][j] = s * ((k == j ? t : T(0)) - W[k][j]);
     T* out = (T*)A.corner + e * NV * D;
 #pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      // M_xc = sum_y (G^_xy + G^_yx) Gamma_yc
-      T Mx[NV];
-#pragma unroll
-      for (int x = 0; x < NV; ++x) {
-        T m = (Gh[x][0] + Gh[0][x]) * Gam[0][c];
-#pragma unroll
-        for (int y = 1; y < NV; ++y) m += (Gh[x][y] + Gh[y][x]) * Gam[y][c];
-        Mx[x] = m;
-      }
+    for (int c = 0; c < NV; ++c)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        T acc = t * g.c[c][k];
+        T o = Z[k][0] * g.c[c][0];
 #pragma unroll
-        for (int x = 0; x < NV; ++x) acc -= g.c[x][k] * Mx[x];
-        out[c * D + k] = s * acc;
+        for (int j = 1; j < D; ++j) o += Z[k][j] * g.c[c][j];
+        out[c * D + k] = o;
       }
-    }
   }
   if (A.lpart) {  // fixed-order block reduction of L
     red[threadIdx.x] = Le;
