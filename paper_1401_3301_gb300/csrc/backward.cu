@@ -183,16 +183,25 @@ __global__ void k_bwd_vertex(const int32_t* __restrict__ ptr, const int32_t* __r
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= nq) return;
   const int32_t s = ptr[v], t = ptr[v + 1];
+  if (s == t) {  // a vertex no element uses
 #pragma unroll
-  for (int k = 0; k < D; ++k) {
-    T acc = T(0);
-    if (s < t) {
-      Acc<T> a(corner[(int64_t)inc[s] * D + k]);
-      for (int32_t j = s + 1; j < t; ++j) a.add(corner[(int64_t)inc[j] * D + k]);
-      acc = a.value();
-    }
-    dLdq[k * nq + v] = acc;
+    for (int k = 0; k < D; ++k) dLdq[k * nq + v] = T(0);
+    return;
   }
+  // one pass over the incidences, all D components of each corner together
+  Acc<T> a[D];
+  {
+    const T* c0 = corner + (int64_t)inc[s] * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) a[k] = Acc<T>(c0[k]);
+  }
+  for (int32_t j = s + 1; j < t; ++j) {
+    const T* cj = corner + (int64_t)inc[j] * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) a[k].add(cj[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) dLdq[k * nq + v] = a[k].value();
 }
 
 // L = sum of the block partials, in block order (one block)
