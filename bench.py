@@ -519,29 +519,41 @@ def run_other(args):
                    config={"workload": "Kuhn cube, P_k lattice nodes, kN ~ 100 (about 1.03e6 nodes), jitter 0.15h, "
                                        "elements permuted", "hbm_peak_GBps": hbm_peak})
     elif args.workload == "boundary":
-        # facet (boundary) mass and P1-weighted mass on a large triangulated surface in 3D
+        # facet (boundary) mass and P1-weighted mass on a large triangulated surface in 3D,
+        # as generated (random vertex numbering) and after fe_morton_vertex_order
         N = 2000 if args.N == 100 else args.N
         m = meshgen.surface_mesh(N, seed=0)
-        q, f = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        p = fe.fe_boundary_pattern(q, f)
-        pms = (time.perf_counter() - t0) * 1e3
-        wv = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
-            vals = torch.empty(p.nnz, dtype=T, device="cuda")
-            w = wv.to(T)
-            res = {}
-            for label, fn in (("mass", lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)),
-                              ("wmass_p1", lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec, vals=vals))):
-                med, mean = _timed(fn, K, W, flush)
-                p.check()
-                res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
-            out["forms"][name] = {"value": res["mass"]["value"], "operators": res}
-        out.update(metric="3D surface (facet) mass and P1-weighted mass, Mtris/s, fixed pattern", unit="Mtris/s",
+        q0, f0 = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        wv0 = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
+        order = fe.fe_morton_vertex_order(q0)
+        q1, f1 = fe.fe_apply_vertex_order(q0, f0, order)
+        numberings = {"as_generated": (q0, f0, wv0), "morton": (q1, f1, wv0[order.long()])}
+        pms = {}
+        for label_n, (q, f, wv) in numberings.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p = fe.fe_boundary_pattern(q, f)
+            pms[label_n] = (time.perf_counter() - t0) * 1e3
+            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+                vals = torch.empty(p.nnz, dtype=T, device="cuda")
+                w = wv.to(T)
+                res = {}
+                for label, fn in (("mass", lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)),
+                                  ("wmass_p1", lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec,
+                                                                            vals=vals))):
+                    med, mean = _timed(fn, K, W, flush)
+                    p.check()
+                    res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+                out["forms"].setdefault(name, {"value": None, "numbering": {}})["numbering"][label_n] = res
+            nnz = p.nnz
+            del p
+        for name in ("f64", "f32"):
+            out["forms"][name]["value"] = out["forms"][name]["numbering"]["morton"]["mass"]["value"]
+        out.update(metric="3D surface (facet) mass and P1-weighted mass, Mtris/s, fixed pattern (value: Morton "
+                          "vertex numbering, mass)", unit="Mtris/s",
                    config={"workload": f"height-field surface over the unit square, N={N} ({m.nme:,} triangles, "
                                        f"{m.nq:,} vertices), jitter 0.2h, vertices and elements permuted",
-                           "nnz": p.nnz, "pattern_build_ms": pms})
+                           "nnz": nnz, "pattern_build_ms": pms})
     elif args.workload == "elas":
         N = 80 if args.N == 100 else args.N
         m = meshgen.kuhn_cube_mesh(N, seed=0)
