@@ -631,7 +631,9 @@ def run_other(args):
             torch.cuda.manual_seed(0)
 
             def step():
-                w.copy_(torch.randn(w.shape, device="cuda", dtype=T).exp_())
+                # fresh lognormal(0, 1) weights, drawn in FP32 (input data: an FP64 normal
+                # generator would cost more FP64 work than the assembly) and widened to the form
+                w.copy_(torch.randn(w.shape, device="cuda", dtype=torch.float32).exp_())
                 fe.fe_assemble_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=s)
                 fe.fe_assemble_wmass(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=mm_)
             step()
