@@ -4,8 +4,11 @@
  * The library computes the P1 Lagrange finite element matrices of a simplicial
  * mesh (Cuvelier, Japhet, Scarella, "An efficient way to assemble finite element
  * matrices in vector languages"): mass, weighted mass, stiffness and linear
- * elasticity, and assembles them into CSR form with duplicate contributions
- * summed, which is the `sparse(Ig, Jg, Kg, m, n)` constructor of Section 3.
+ * elasticity, the general second-order operator of Eq. EDP, boundary (facet) mass
+ * and P_k mass (App. D), and assembles them into CSR form with duplicate
+ * contributions summed, which is the `sparse(Ig, Jg, Kg, m, n)` constructor of
+ * Section 3; also the gradients of L = u^T S(w) v (and general vector-Jacobian
+ * products) of the stiffness matrix.
  *
  * Conventions shared by every call
  *   - Mesh (Section 2, Table 1): q is d x nq (coordinate c of vertex v at
@@ -41,7 +44,8 @@ extern "C" {
 #define FE_ERR_DEGENERATE 3 /* an element has det B = 0 or a non-finite det B */
 #define FE_ERR_OVERFLOW 4   /* a size does not fit the library's 32-bit indices */
 #define FE_ERR_CUDA 5       /* a CUDA runtime call failed */
-#define FE_ERR_TIMEOUT 6    /* reserved: a bounded device-side wait gave up */
+#define FE_ERR_TIMEOUT 6    /* a bounded device-side wait for a chunk's plan record
+                               gave up; that chunk's values are missing */
 #define FE_ERR_NOMEM 7      /* device allocation failed */
 #define FE_ERR_SCRATCH_LIMIT 8 /* the mesh needs more scratch than fe_assemble_stiff_noalloc has */
 
@@ -247,6 +251,7 @@ int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices
                          int64_t* local_edges, int64_t* partial_vertices, int64_t* partial_edges,
                          int64_t* shared_vertices, int64_t* shared_edges, int64_t* plan_bytes);
 
+/* Release everything the handle owns (synchronises the device first). */
 int fe_pattern_destroy(fe_pattern_h h);
 
 /*
