@@ -251,6 +251,15 @@ int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices
                          int64_t* local_edges, int64_t* partial_vertices, int64_t* partial_edges,
                          int64_t* shared_vertices, int64_t* shared_edges, int64_t* plan_bytes);
 
+/*
+ * fe_selftest_wait_timeout -- exercises the failure path of the kernels' bounded
+ * waits without any fault: a one-block kernel waits on an mbarrier for 16 bytes that
+ * no copy will bring, gives up after a short bound and records FE_ERR_TIMEOUT in a
+ * status word, which is returned in *code (FE_ERR_TIMEOUT when the path works). The
+ * CUDA context stays usable. Synchronous. The paper has no counterpart.
+ */
+int fe_selftest_wait_timeout(int32_t* code, void* stream);
+
 /* Release everything the handle owns (synchronises the device first). */
 int fe_pattern_destroy(fe_pattern_h h);
 

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include "fe_internal.cuh"
+#include "tma.cuh"
 
 int fe_launch_scalar_f64(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind,
                          void* vals, cudaStream_t s);
@@ -303,3 +304,40 @@ int fe_assemble_stiff_vjp(fe_pattern_h h, const double* q, const void* w, int32_
 }
 
 }  // extern "C"
+
+namespace {
+// Self-test of the bounded wait: an mbarrier expects 16 bytes that no copy will bring,
+// so the bounded wait runs out; the block reports FE_ERR_TIMEOUT and returns. Nothing
+// is in flight when it returns (no copy was issued).
+__global__ void k_selftest_wait(uint32_t max_iter, fe_status_word* st) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    fe::mbar_init(&bar, 1);
+    fe::mbar_arrive_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  const bool landed = __syncthreads_and(fe::mbar_wait_bounded(&bar, 0, max_iter));
+  if (!landed && threadIdx.x == 0) fe_report(st, FE_ERR_TIMEOUT, 0);
+}
+}  // namespace
+
+extern "C" int fe_selftest_wait_timeout(int32_t* code, void* stream) {
+  if (!code) return FE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  fe_status_word* st = nullptr;
+  FE_CUDA_TRY(cudaMalloc(&st, sizeof(fe_status_word)));
+  fe_status_word init = {0, 0, ~0ull}, out;
+  int rc = FE_OK;
+  if (cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = FE_ERR_CUDA;
+  if (!rc) {
+    k_selftest_wait<<<1, 32, 0, s>>>(1u << 12, st);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&out, st, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = FE_ERR_CUDA;
+    else
+      *code = out.code;
+  }
+  cudaFree(st);
+  return rc;
+}

@@ -63,6 +63,7 @@ def lib() -> C.CDLL:
         L.fe_pk_mass_table.argtypes = [I32, I32, P]
         L.fe_morton_vertex_order.argtypes = [I32, I64, P, P, P]
         L.fe_assemble_stiff_host.argtypes = [P, P, P, I32, I32, P, P]
+        L.fe_selftest_wait_timeout.argtypes = [P, P]
         L.fe_apply_vertex_order.argtypes = [I32, I64, I64, I32, P, P, P, P, P, P]
         L.fe_assemble_stiff_backward.argtypes = [P, P, P, I32, P, P, P, P, P, I32, P]
         L.fe_assemble_stiff_noalloc.argtypes = [P, P, P, I32, I32, P, P]
@@ -85,7 +86,8 @@ def lib() -> C.CDLL:
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
                      "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads",
                      "fe_boundary_pattern", "fe_assemble_general", "fe_pk_pattern", "fe_pk_mass_table",
-                     "fe_morton_vertex_order", "fe_apply_vertex_order", "fe_assemble_stiff_host"):
+                     "fe_morton_vertex_order", "fe_apply_vertex_order", "fe_assemble_stiff_host",
+                     "fe_selftest_wait_timeout"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -423,6 +425,14 @@ def fe_assemble_stiff_noalloc(p: Pattern, q: torch.Tensor, vals: torch.Tensor, w
     _check(lib().fe_assemble_stiff_noalloc(p.handle, _dev(q, torch.float64, "q"), _dev(w, _vtype(prec), "w"),
                                            w_kind, prec, _dev(vals, _vtype(prec), "vals"), _stream(stream)))
     return vals
+
+
+def fe_selftest_wait_timeout(stream=None) -> int:
+    """Status code of a bounded wait that is made to run out (FE_ERR_TIMEOUT = 6 when the
+    failure path works); see include/fe.h."""
+    code = C.c_int32(-1)
+    _check(lib().fe_selftest_wait_timeout(C.byref(code), _stream(stream)))
+    return code.value
 
 
 def fe_version() -> str:
