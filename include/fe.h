@@ -48,6 +48,8 @@ extern "C" {
                                gave up; that chunk's values are missing */
 #define FE_ERR_NOMEM 7      /* device allocation failed */
 #define FE_ERR_SCRATCH_LIMIT 8 /* the mesh needs more scratch than fe_assemble_stiff_noalloc has */
+#define FE_ERR_BOUNDS 9     /* bounds-checked builds only (FE_CHECKED): an index fell outside its
+                               buffer; the access was skipped, *id is the element chunk */
 
 /* ---- precision forms of the element and value kernels */
 #define FE_F64 0 /* FP64 arithmetic, FP64 values */
@@ -390,8 +392,9 @@ int fe_assemble_stiff_vjp(fe_pattern_h h, const double* q, const void* w, int32_
 
 /*
  * Per-kernel timing. fe_profile(h, 1) makes every later kernel launch of h be
- * bracketed by a CUDA event pair on its stream (fe_profile(h, 0) stops and frees
- * them). fe_profile_read synchronises on the recorded events and returns, per
+ * bracketed by a CUDA event pair on its stream and by an NVTX range named after the
+ * kernel (visible to a timeline profiler; a no-op without one). fe_profile(h, 0) stops
+ * and frees them. fe_profile_read synchronises on the recorded events and returns, per
  * kernel kind launched since the last read, its name (32-byte slots in `names`),
  * total milliseconds and launch count; *count receives the number of kinds
  * (entries beyond max_kernels are dropped). Host pointers.
@@ -426,7 +429,8 @@ int fe_profile_read(fe_pattern_h h, int32_t max_kernels, char* names, double* ms
 int fe_assemble_stiff_noalloc(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
                               int32_t prec, void* vals, void* stream);
 
-/* Library version string (host pointer, static). */
+/* Library version string (host pointer, static); the bounds-checked build (compiled
+ * with FE_CHECKED) says "bounds-checked" in it. */
 const char* fe_version(void);
 
 /* Text of the last CUDA runtime error seen by the library (host pointer, static;

@@ -77,7 +77,13 @@ int fe_ensure_scratch(fe_pattern_s* h, int strategy) {
 
 extern "C" {
 
-const char* fe_version(void) { return "fe_gb300 0.1 (sm_103a)"; }
+const char* fe_version(void) {
+#ifdef FE_CHECKED
+  return "fe_gb300 0.1 (sm_103a, bounds-checked)";
+#else
+  return "fe_gb300 0.1 (sm_103a)";
+#endif
+}
 
 const char* fe_last_cuda_error(void) { return g_last_cuda_error; }
 

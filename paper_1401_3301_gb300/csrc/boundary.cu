@@ -171,7 +171,7 @@ int launch(fe_pattern_s* h, const StagedArgs& A, T* vals, cudaStream_t s) {
   const int64_t nsh = h->nsh_v + h->nsh_e;
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_FIXUP, s);
-    k_fixup_scalar<T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->partials, vals);
+    k_fixup_scalar<T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->partials, vals, h->nnz_s, h->npart, h->status);
     FE_CUDA_TRY(cudaGetLastError());
     FE_PROF_END(h, FE_K_FIXUP, s);
   }
@@ -198,7 +198,7 @@ int fe_launch_boundary(fe_pattern_s* h, int kind, const double* q, const void* w
   using namespace fe;
   if (h->strategy != FE_REASM_CHUNKED || kind == K_STIFF) return FE_ERR_ARG;
   StagedArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, w, w_kind,
-               h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
+               h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status, h->nnz_s, h->npart};
   if (prec == FE_F64) return dispatch<double>(h, kind, A, (double*)vals, s);
   return dispatch<float>(h, kind, A, (float*)vals, s);
 }

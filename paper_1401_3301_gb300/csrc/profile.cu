@@ -1,4 +1,7 @@
-// Per-kernel CUDA-event timing of a pattern handle (see profile.cuh).
+// Per-kernel CUDA-event timing of a pattern handle (see profile.cuh), and an NVTX range
+// named after the kernel around every launch (header-only NVTX 3: a no-op unless a
+// profiling tool is attached).
+#include <nvtx3/nvToolsExt.h>
 #include <string.h>
 
 #include <vector>
@@ -32,7 +35,7 @@ static int next_event(fe_prof_state::slot_events& se, cudaEvent_t* e) {
   return FE_OK;
 }
 
-int fe_prof_begin(fe_pattern_s* h, int slot, cudaStream_t s) {
+static int record(fe_pattern_s* h, int slot, cudaStream_t s) {
   if (!h->prof) return FE_OK;
   cudaEvent_t e;
   FE_TRY(next_event(h->prof->slots[slot], &e));
@@ -40,7 +43,15 @@ int fe_prof_begin(fe_pattern_s* h, int slot, cudaStream_t s) {
   return FE_OK;
 }
 
-int fe_prof_end(fe_pattern_s* h, int slot, cudaStream_t s) { return fe_prof_begin(h, slot, s); }
+int fe_prof_begin(fe_pattern_s* h, int slot, cudaStream_t s) {
+  nvtxRangePushA(kNames[slot]);
+  return record(h, slot, s);
+}
+
+int fe_prof_end(fe_pattern_s* h, int slot, cudaStream_t s) {
+  nvtxRangePop();
+  return record(h, slot, s);
+}
 
 void fe_prof_free(fe_pattern_s* h) {
   delete h->prof;

@@ -24,7 +24,7 @@ def PATTERN_CHUNK(c: int) -> int:
     """Pattern flag: elements per chunk of the chunked reassembly (32..4096)."""
     return int(c) << 8
 ERRORS = {1: "FE_ERR_ARG", 2: "FE_ERR_INDEX", 3: "FE_ERR_DEGENERATE", 4: "FE_ERR_OVERFLOW",
-          5: "FE_ERR_CUDA", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NOMEM", 8: "FE_ERR_SCRATCH_LIMIT"}
+          5: "FE_ERR_CUDA", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NOMEM", 8: "FE_ERR_SCRATCH_LIMIT", 9: "FE_ERR_BOUNDS"}
 
 _lib = None
 
@@ -36,10 +36,11 @@ class FEError(RuntimeError):
 
 
 def lib() -> C.CDLL:
-    """The loaded libfe_gb300.so (raises if it has not been built)."""
+    """The loaded libfe_gb300.so (raises if it has not been built). With the environment
+    variable FE_GB300_CHECKED=1 the bounds-checked build is loaded instead."""
     global _lib
     if _lib is None:
-        path = build_ext.LIB
+        path = build_ext.LIB_CHECKED if os.environ.get("FE_GB300_CHECKED") == "1" else build_ext.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libfe_gb300.so is missing ({path}); build it with "
                                "paper_1401_3301_gb300.build_ext.build()")

@@ -102,3 +102,17 @@ def test_values_do_not_depend_on_threads_per_block(prec):
         p.set_threads(t)
         out.append(fe.fe_assemble_stiff(p, q, prec=prec))
     assert torch.equal(out[0], out[1]) and torch.equal(out[1], out[2])
+
+
+def test_nan_coordinate_is_reported_as_degenerate():
+    fe = fe_or_skip()
+    m = meshgen.kuhn_cube_mesh(4, seed=15)
+    qb = m.q.copy()
+    v = m.me[2, 20]
+    qb[1, v] = np.nan
+    q, me = to_cuda(qb), to_cuda(m.me)
+    p = fe.fe_pattern(q, me)  # the pattern does not read coordinates' values for its indices
+    for prec in (fe.F64, fe.F32, fe.F64X):
+        fe.fe_assemble_stiff(p, q, prec=prec)
+        code, eid = p.status()
+        assert code == 3 and v in m.me[:, eid], prec
