@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "3D P1 stiffness Mtets/s and % HBM roofline, FP32 vs FP64 form, fixed pattern"
 UNIT = "Mtets/s"
 SM_COUNT = 152
-FP64_PIPE_PER_SM_CLK = 2.0      # DFMA/DADD/DMUL issue rate per SM per clock on GB300
+FP64_PIPE_PER_SM_CLK = 2.0      # nominal FP64 issue rate per SM per clock on GB300
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["elem.cuh", "plan.cuh", "tma.cuh", "assemble_impl.cuh", "assemble_scalar.inc",
                   "assemble_f64.cu", "assemble_f32.cu", "assemble_f64x.cu"]
@@ -246,19 +246,32 @@ def chunk_algorithmic_bytes(p, prec, info, points=None):
 
 
 def fp64_instr_per_tet():
-    """FP64-pipe instructions (DADD + DMUL + DFMA) per tet of the FP64 chunk kernel:
-    ncu-counted when the committed profile matches the current kernel sources, else
-    the count from the source (edges 9, cofactors 18, det 3, 1/(6|det|) 5, Gram 18,
-    scaling 6, row sums 8, about 8 incidence sums)."""
+    """FP64-pipe instructions (DADD + DMUL + DFMA) per tet of the FP64 chunk kernel and
+    their mix: ncu-counted when the committed profile matches the current kernel sources,
+    else the count from the source (edges 9, cofactors 18, det 3, 1/(6|det|) 5, Gram 18,
+    scaling 6, row sums 8, about 8 incidence sums) and no mix."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             ent = json.load(f)["f64"]
         if ent.get("source_hash") == kernel_source_hash() and "fp64_instr_per_tet" in ent:
-            return float(ent["fp64_instr_per_tet"]), "ncu (profiles/traffic.json)"
+            return (float(ent["fp64_instr_per_tet"]), "ncu (profiles/traffic.json)",
+                    ent.get("fp64_instr_mix_per_tet"))
     except Exception:
         pass
-    return 75.0, "from source"
+    return 75.0, "from source", None
+
+
+# FP64 issue rates measured on this GB300 with 8 independent dependency chains per
+# thread (G instr/s at 2070 MHz): DFMA reaches 2 per SM per clock, DADD and DMUL only
+# about 1.6, so a kernel's attainable FP64 rate depends on its instruction mix.
+FP64_MEASURED_RATE = {"dfma": 599.0, "dadd": 505.0, "dmul": 505.0}
+
+
+def fp64_mix_peak(mix):
+    """Attainable FP64 instructions/s (G/s) for an instruction mix {op: per tet}."""
+    total = sum(mix.values())
+    return total / sum(n / FP64_MEASURED_RATE[k] for k, n in mix.items())
 
 
 def run_gpu(args):
@@ -356,15 +369,22 @@ def run_gpu(args):
         forms[prec_name]["path_effective"]["frac"] = forms[prec_name]["path_effective"]["GBps"] / hbm_peak
         if prec == fe.F64:
             clock = sm_max
-            ipt, counted = fp64_instr_per_tet()
+            ipt, counted, mix = fp64_instr_per_tet()
             instr = ipt * p.nme
             peak_ops = FP64_PIPE_PER_SM_CLK * SM_COUNT * clock * 1e6 / 1e9
+            achieved_ops = instr / (dom_ms * 1e-3) / 1e9
             forms[prec_name]["roofline_alu"] = {
-                "bound": "alu", "kernel": dom, "achieved": instr / (dom_ms * 1e-3) / 1e9,
+                "bound": "alu", "kernel": dom, "achieved": achieved_ops,
                 "peak": peak_ops, "unit": "G FP64 instr/s",
-                "frac": instr / (dom_ms * 1e-3) / 1e9 / peak_ops,
+                "frac": achieved_ops / peak_ops, "traffic": traffic,
                 "instr_per_tet": ipt, "counted": counted,
                 "peak_source": f"{FP64_PIPE_PER_SM_CLK:.0f} FP64 instr/SM/clk x {SM_COUNT} SMs x {clock:.0f} MHz"}
+            if mix:
+                mp = fp64_mix_peak(mix)
+                forms[prec_name]["roofline_alu"]["mix"] = {
+                    "per_tet": mix, "attainable": mp, "frac": achieved_ops / mp,
+                    "rates": FP64_MEASURED_RATE,
+                    "source": "issue-rate microbenchmark (8 independent chains per thread)"}
     clocks = sampler.stop()
 
     # end-to-end through the public API with host buffers (selected form)

@@ -253,6 +253,13 @@ int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices
                          int64_t* local_edges, int64_t* partial_vertices, int64_t* partial_edges,
                          int64_t* shared_vertices, int64_t* shared_edges, int64_t* plan_bytes);
 
+/* Device address and size in bytes of the plan record of element chunk c (the
+ * layout is in csrc/plan.cuh; it starts with the uint16 vertex incidence codes
+ * e_local * nv + a). Borrowed: owned by the handle, valid until fe_pattern_destroy,
+ * read by every chunked assembly. Synchronises the device to read the offsets.
+ * FE_ERR_ARG for c outside [0, nchunks) or a handle without a chunk plan. */
+int fe_pattern_plan_record(fe_pattern_h h, int64_t c, const void** rec, int64_t* bytes);
+
 /*
  * fe_selftest_wait_timeout -- exercises the failure path of the kernels' bounded
  * waits without any fault: a one-block kernel waits on an mbarrier for 16 bytes that

@@ -3,7 +3,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "fe_internal.cuh"
+#include "plan.cuh"
 #include "tma.cuh"
 
 int fe_launch_scalar_f64(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind,
@@ -189,6 +192,22 @@ int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices
   if (shared_vertices) *shared_vertices = h->nsh_v;
   if (shared_edges) *shared_edges = h->nsh_e;
   if (plan_bytes) *plan_bytes = h->plan_bytes;
+  return FE_OK;
+}
+
+int fe_pattern_plan_record(fe_pattern_h h, int64_t c, const void** rec, int64_t* bytes) {
+  if (!h || !rec || !bytes || !h->rec || c < 0 || c >= h->nchunks) return FE_ERR_ARG;
+  int32_t v[2], e[2];
+  uint32_t off16;
+  FE_CUDA_TRY(cudaDeviceSynchronize());
+  FE_CUDA_TRY(cudaMemcpy(v, h->ch_v_ptr + c, sizeof(v), cudaMemcpyDeviceToHost));
+  FE_CUDA_TRY(cudaMemcpy(e, h->ch_e_ptr + c, sizeof(e), cudaMemcpyDeviceToHost));
+  FE_CUDA_TRY(cudaMemcpy(&off16, h->rec_off16 + c, sizeof(off16), cudaMemcpyDeviceToHost));
+  const int64_t ne = std::min<int64_t>(h->chunk, h->nme - c * h->chunk);
+  const fe::RecLayout R = fe::rec_layout((uint32_t)ne, (uint32_t)h->nv, (uint32_t)h->npair,
+                                         (uint32_t)(v[1] - v[0]), (uint32_t)(e[1] - e[0]), h->m > 1);
+  *rec = h->rec + (int64_t)off16 * 16;
+  *bytes = R.total;
   return FE_OK;
 }
 

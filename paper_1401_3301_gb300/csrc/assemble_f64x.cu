@@ -68,6 +68,7 @@ struct X64Args {
   const uint8_t* rec;
   const uint32_t* rec_off16;
   fe_status_word* st;
+  int64_t nnz, npart;  // sizes of vals and of the partial sums (bounds-checked builds)
 };
 
 template <int D, int THREADS>
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   // same footprint as the FP32 form: split coordinates, uint16 corner map, float2 values
   const StagedSmem S = staged_smem(D, 8, false, A.rec_max, A.max_lv, A.chunk);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
   uint16_t* lvid = (uint16_t*)(smem + S.lvid);
   float2* Kd = (float2*)(smem + S.kd);
   float2* Ko = (float2*)(smem + S.ko);
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   // 0. coordinates relative to corner 0 of the chunk's first element (FP64), split into
   //    float pairs; the reference does not depend on the record's vertex order
@@ -242,10 +245,11 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
 
 __global__ void k_fixup_f64x(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
                              int64_t nsh_v, int64_t nsh, const float2* __restrict__ partials,
-                             double* __restrict__ vals) {
+                             double* __restrict__ vals, int64_t nnz, int64_t npart, fe_status_word* st) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nsh) return;
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
+  if (!FE_FIXUP_VALID(s, t, npart, sh_dst[2 * g], sh_dst[2 * g + 1], g >= nsh_v, nnz, st, g)) return;
   float2 v = partials[s];
   df acc{v.x, v.y};
   for (int32_t i = s + 1; i < t; ++i) {
@@ -273,7 +277,8 @@ int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_FIXUP, s);
     k_fixup_f64x<<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
-                                                   (const float2*)h->partials, vals);
+                                                   (const float2*)h->partials, vals, h->nnz_s, h->npart,
+                                                   h->status);
     FE_CUDA_TRY(cudaGetLastError());
     FE_PROF_END(h, FE_K_FIXUP, s);
   }
@@ -288,6 +293,7 @@ int fe_launch_stiff_f64x(fe_pattern_s* h, const double* q, const void* w, int w_
   using namespace fe;
   if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
   X64Args A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, (const double*)w,
-            w_kind, h->order, h->me_int, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
+            w_kind, h->order, h->me_int, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status,
+            h->nnz_s, h->npart};
   return h->d == 3 ? launch<3>(h, A, (double*)vals, s) : launch<2>(h, A, (double*)vals, s);
 }

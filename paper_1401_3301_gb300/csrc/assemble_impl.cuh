@@ -2,6 +2,7 @@
 // reassembly strategies. Included by one translation unit per precision form.
 #pragma once
 
+#include "check.cuh"
 #include "elem.cuh"
 #include "fe_internal.cuh"
 #include "plan.cuh"
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = staged_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, DEFER);
-  if (!FE_IN_BOUNDS(A.st, R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, c)) return;
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -325,15 +326,14 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   T* Ko = (T*)(smem + S.ko);
   T* wl = (T*)(smem + S.w);
   T* Sc = (T*)(smem + S.sc);
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   // 0. vertex coordinates of the chunk, and the local vertex of every element corner
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
-    if (!FE_IN_BOUNDS(A.st, vid >= 0 && vid < A.nq && lv_off[u + 1] <= ne * NV, c)) continue;
     stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u);
     if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j)
-      if (FE_IN_BOUNDS(A.st, inc_v[j] < ne * NV, c)) lvid[inc_v[j]] = (uint16_t)u;
+    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -342,10 +342,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   for (int el = threadIdx.x; el < ne; el += THREADS) {
     int lv[NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      lv[a] = lvid[el * NV + a];
-      if (!FE_IN_BOUNDS(A.st, lv[a] < nlv, c)) lv[a] = 0;
-    }
+    for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     Geo<D, T> g;
     staged_geo<D, T>(smem + S.q, lv, g);
     if (!det_ok(g.det)) {
@@ -371,30 +368,17 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   // 2. sums over the incidences of each distinct vertex and edge, in element order
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int s = lv_off[u], t = lv_off[u + 1];
-#ifdef FE_CHECKED
-    bool ok = s < t && t <= ne * NV;
-    for (int j = s; ok && j < t; ++j) ok = inc_v[j] < ne * NV;
-    if (!FE_IN_BOUNDS(A.st, ok, c)) continue;
-#endif
     Acc<T> acc = DEFER ? Acc<T>(Kd[inc_v[s]] * Sc[inc_v[s] / NV]) : Acc<T>(Kd[inc_v[s]]);
     for (int j = s + 1; j < t; ++j) {
       if constexpr (DEFER) acc.add_scaled(Kd[inc_v[j]], Sc[inc_v[j] / NV]);
       else acc.add(Kd[inc_v[j]]);
     }
     const int32_t dst = lv_dst[u];
-    if (dst >= 0) {
-      if (FE_IN_BOUNDS(A.st, dst < A.nnz, c)) vals[dst] = acc.value();
-    } else if (FE_IN_BOUNDS(A.st, -1 - (int64_t)dst < A.npart, c)) {
-      acc.store_partial(partials, -1 - (int64_t)dst);
-    }
+    if (dst >= 0) vals[dst] = acc.value();
+    else acc.store_partial(partials, -1 - (int64_t)dst);
   }
   for (int u = threadIdx.x; u < nle; u += THREADS) {
     const int s = le_off[u], t = le_off[u + 1];
-#ifdef FE_CHECKED
-    bool ok = s < t && t <= ne * NP;
-    for (int j = s; ok && j < t; ++j) ok = (inc_e[j] >> 1) < ne * NP;
-    if (!FE_IN_BOUNDS(A.st, ok, c)) continue;
-#endif
     const int i0 = inc_e[s] >> 1;
     Acc<T> acc = DEFER ? Acc<T>(Ko[i0] * Sc[i0 / NP]) : Acc<T>(Ko[i0]);
     for (int j = s + 1; j < t; ++j) {
@@ -405,11 +389,9 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
     const int32_t dst = le_dst[2 * u];
     if (dst >= 0) {
       const T val = acc.value();
-      if (FE_IN_BOUNDS(A.st, dst < A.nnz && le_dst[2 * u + 1] >= 0 && le_dst[2 * u + 1] < A.nnz, c)) {
-        vals[dst] = val;
-        vals[le_dst[2 * u + 1]] = val;
-      }
-    } else if (FE_IN_BOUNDS(A.st, -1 - (int64_t)dst < A.npart, c)) {
+      vals[dst] = val;
+      vals[le_dst[2 * u + 1]] = val;
+    } else {
       acc.store_partial(partials, -1 - (int64_t)dst);
     }
   }
@@ -424,11 +406,7 @@ __global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t
   if (g >= nsh) return;
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
   const int32_t d0 = sh_dst[2 * g], d1 = sh_dst[2 * g + 1];
-#ifdef FE_CHECKED
-  if (!FE_IN_BOUNDS(st, s >= 0 && s < t && t <= npart && d0 >= 0 && d0 < nnz &&
-                            (g < nsh_v || (d1 >= 0 && d1 < nnz)), g))
-    return;
-#endif
+  if (!FE_FIXUP_VALID(s, t, npart, d0, d1, g >= nsh_v, nnz, st, g)) return;
   Acc<T> acc = Acc<T>::from_partial(partials, s);
   int32_t i = s + 1;
   for (; i + 2 < t; i += 3) {  // three independent loads in flight, summed in order

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary(StagedArgs A, T* __r
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = boundary_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -39,6 +40,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary(StagedArgs A, T* __r
   T* Kd = (T*)(smem + S.kd);
   T* Ko = (T*)(smem + S.ko);
   T* wl = (T*)(smem + S.w);
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];

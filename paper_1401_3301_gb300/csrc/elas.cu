@@ -32,6 +32,7 @@ struct ElasArgs {
   const uint8_t* rec;
   const uint32_t* rec_off16;
   fe_status_word* st;
+  int64_t nnz, npart;  // sizes of vals and of the partial blocks (bounds-checked builds)
 };
 
 // sum over the element's vertices of a coefficient's P1 values (lambda^s, mu^s)
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle, true);
   const ElasSmem S = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   T* mu_l = lam_l + A.max_lv;
   T* Cg = (T*)(smem + S.cg);   // [e][a][i]
   T* LM = (T*)(smem + S.lm);   // [e][2]
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   // 0. coordinates (and P1 Lame values) of the chunk's vertices; local vertex of each corner
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
@@ -266,13 +269,17 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
 template <int D, class T>
 __global__ void k_fixup_elas(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
                              const int32_t* __restrict__ sh_str, int64_t nsh_v, int64_t nsh,
-                             const void* __restrict__ partials, T* __restrict__ vals) {
+                             const void* __restrict__ partials, T* __restrict__ vals, int64_t nnz,
+                             int64_t npart, fe_status_word* st) {
   constexpr int MM = D * D;
   const int64_t gk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gk >= nsh * MM) return;
   const int64_t g = gk / MM;
   const int k = (int)(gk - g * MM);
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
+  if (!FE_FIXUP_VALID(s, t, npart, (int64_t)sh_dst[2 * g] + (k / D) * sh_str[2 * g] + k % D,
+                      (int64_t)sh_dst[2 * g + 1] + (k % D) * sh_str[2 * g + 1] + k / D, g >= nsh_v, nnz, st, g))
+    return;
   Acc<T> acc = Acc<T>::from_partial(partials, (int64_t)s * MM + k);
   for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, (int64_t)i * MM + k);
   const T v = acc.value();
@@ -297,7 +304,8 @@ int launch(fe_pattern_s* h, const ElasArgs& A, T* vals, cudaStream_t s) {
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_ELAS_FIXUP, s);
     k_fixup_elas<D, T><<<fe_grid(nsh * D * D, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->sh_str, h->nsh_v,
-                                                                 nsh, h->partials, vals);
+                                                                 nsh, h->partials, vals, h->nnz, h->npart,
+                                                                 h->status);
     FE_CUDA_TRY(cudaGetLastError());
     FE_PROF_END(h, FE_K_ELAS_FIXUP, s);
   }
@@ -312,7 +320,8 @@ int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_ki
   using namespace fe;
   if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;  // vector problems: chunked only
   ElasArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, lam, lam_kind,
-             mu, mu_kind, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status};
+             mu, mu_kind, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status, h->nnz,
+             h->npart};
   if (prec == FE_F64)
     return h->d == 3 ? launch<3, double>(h, A, (double*)vals, s) : launch<2, double>(h, A, (double*)vals, s);
   return h->d == 3 ? launch<3, float>(h, A, (float*)vals, s) : launch<2, float>(h, A, (float*)vals, s);

@@ -34,19 +34,6 @@ __device__ __forceinline__ void fe_report(fe_status_word* st, int32_t code, long
   atomicMin(&st->id, (unsigned long long)id);
 }
 
-// Bounds checks of the FE_CHECKED build: fe_in_bounds(st, ok, where) records
-// FE_ERR_BOUNDS (with `where`) when ok is false and returns ok, so the caller skips the
-// access. In the normal build FE_IN_BOUNDS is the constant true and costs nothing.
-#ifdef FE_CHECKED
-__device__ __forceinline__ bool fe_in_bounds(fe_status_word* st, bool ok, long long where) {
-  if (!ok) fe_report(st, FE_ERR_BOUNDS, where);
-  return ok;
-}
-#define FE_IN_BOUNDS(st, ok, where) fe_in_bounds((st), (ok), (where))
-#else
-#define FE_IN_BOUNDS(st, ok, where) true
-#endif
-
 // ---------------------------------------------------------------- pattern handle
 struct fe_prof_state;
 void fe_prof_free(struct fe_pattern_s* h);

@@ -264,6 +264,7 @@ struct GeneralArgs {
   const uint32_t* rec_off16;
   int64_t npart;  // the second orientation of edge partial i is at npart + i
   fe_status_word* st;
+  int64_t nnz;    // size of vals (bounds-checked builds)
 };
 
 // One block per chunk, as the symmetric staged kernel: plan record by one bulk copy,
@@ -283,6 +284,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = general_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
   uint16_t* lvid = (uint16_t*)(smem + S.lvid);
   T* Kd = (T*)(smem + S.kd);
   T2* Ko = (T2*)(smem + S.ko);
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     stage_vertex<D, T>(A.q, A.nq, lv_vid[u], smem + S.q, u);
@@ -367,10 +370,12 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
 template <class T>
 __global__ void k_fixup_general(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
                                 int64_t nsh_v, int64_t nsh, int64_t npart,
-                                const void* __restrict__ partials, T* __restrict__ vals) {
+                                const void* __restrict__ partials, T* __restrict__ vals, int64_t nnz,
+                                fe_status_word* st) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nsh) return;
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
+  if (!FE_FIXUP_VALID(s, t, npart, sh_dst[2 * g], sh_dst[2 * g + 1], g >= nsh_v, nnz, st, g)) return;
   Acc<T> acc = Acc<T>::from_partial(partials, s);
   for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, i);
   vals[sh_dst[2 * g]] = acc.value();
@@ -442,7 +447,8 @@ int launch_general(fe_pattern_s* h, const ElemArgs& E, T* vals, cudaStream_t s) 
                                       (uint32_t)h->chunk);
     if (L.total > 227u * 1024u) return FE_ERR_ARG;
     GeneralArgs G{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, E.q, E.w,
-                  E.w_kind, vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status};
+                  E.w_kind, vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status,
+                  h->nnz_s};
     auto kern = k_chunk_general<D, T, THREADS, P1>;
     static size_t configured = 0;
     FE_TRY(fe_smem_limit(kern, L.total, configured));
@@ -454,7 +460,7 @@ int launch_general(fe_pattern_s* h, const ElemArgs& E, T* vals, cudaStream_t s) 
     if (nsh > 0) {
       FE_PROF_BEGIN(h, FE_K_FIXUP, s);
       k_fixup_general<T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->npart,
-                                                          h->partials, vals);
+                                                          h->partials, vals, h->nnz_s, h->status);
       FE_CUDA_TRY(cudaGetLastError());
       FE_PROF_END(h, FE_K_FIXUP, s);
     }

@@ -169,6 +169,7 @@ struct PkArgs {
   const uint8_t* rec;
   const uint32_t* rec_off16;
   fe_status_word* st;
+  int64_t nnz, npart;  // sizes of vals and of the partial sums (bounds-checked builds)
 };
 
 // One block per chunk: the plan record by one bulk copy, the table and the element
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const PkSmem S = pk_smem(NV, NP, (int)sizeof(T), A.rec_max, (uint32_t)A.chunk);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
   uint16_t* lvid = (uint16_t*)(smem + S.lvid);
   T* Sc = (T*)(smem + S.sc);
   T* tab = (T*)(smem + S.tab);
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   for (int i = threadIdx.x; i < NV + NP; i += THREADS) tab[i] = ((const T*)A.tab)[i];
   for (int u = threadIdx.x; u < nlv; u += THREADS)
@@ -271,7 +274,7 @@ int launch_pk(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   const void* tab = sizeof(T) == 8 ? h->pk_tab : (const void*)((const double*)h->pk_tab + NV + NP);
   PkArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, q, tab, h->order, h->ch_v_ptr, h->ch_e_ptr,
-           h->rec, h->rec_off16, h->status};
+           h->rec, h->rec_off16, h->status, h->nnz_s, h->npart};
   auto kern = k_chunk_pk<D, K, T, THREADS>;
   static size_t configured = 0;
   FE_TRY(fe_smem_limit(kern, L.total, configured));

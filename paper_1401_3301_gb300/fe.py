@@ -53,6 +53,7 @@ def lib() -> C.CDLL:
         L.fe_pattern_set_strategy.argtypes = [P, I32]
         L.fe_pattern_memory.argtypes = [P, P]
         L.fe_pattern_plan_info.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.fe_pattern_plan_record.argtypes = [P, I64, P, P]
         L.fe_pattern_destroy.argtypes = [P]
         L.fe_status.argtypes = [P, P, P, P]
         L.fe_assemble_mass.argtypes = [P, P, I32, P, P]
@@ -81,7 +82,8 @@ def lib() -> C.CDLL:
         L.fe_last_cuda_error.restype = C.c_char_p
         for name in ("fe_pattern", "fe_pattern_copy_csr", "fe_pattern_copy_slot_map", "fe_pattern_dims",
                      "fe_pattern_set_strategy", "fe_pattern_memory", "fe_pattern_plan_info",
-                     "fe_pattern_destroy", "fe_status", "fe_assemble_mass", "fe_assemble_wmass",
+                     "fe_pattern_destroy", "fe_pattern_plan_record", "fe_status", "fe_assemble_mass",
+                     "fe_assemble_wmass",
                      "fe_assemble_stiff", "fe_assemble_elas", "fe_assemble_stiff_backward",
                      "fe_profile", "fe_profile_read", "fe_assemble_stiff_noalloc",
                      "fe_assemble_stiff_vjp", "fe_batch_pattern", "fe_batch_offsets",
@@ -188,6 +190,12 @@ class Pattern:
         v = [C.c_int64() for _ in keys]
         _check(lib().fe_pattern_plan_info(self.handle, *[C.byref(x) for x in v]))
         return dict(zip(keys, (x.value for x in v)))
+
+    def plan_record(self, c: int) -> tuple[int, int]:
+        """(device address, bytes) of element chunk c's plan record (borrowed)."""
+        ptr, nb = C.c_void_p(), C.c_int64()
+        _check(lib().fe_pattern_plan_record(self.handle, c, C.byref(ptr), C.byref(nb)))
+        return ptr.value, nb.value
 
     def profile(self, enable: bool = True):
         _check(lib().fe_profile(self.handle, 1 if enable else 0))

@@ -49,8 +49,69 @@ def run(fe) -> dict:
     lam = torch.tensor([1.5], dtype=torch.float64, device="cuda")
     mu = torch.tensor([0.7], dtype=torch.float64, device="cuda")
     record("3d/elas", pe, fe.fe_assemble_elas(pe, q3, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR))
+    record("3d/elas/f32", pe, fe.fe_assemble_elas(pe, q3, lam.float(), fe.COEF_SCALAR, mu.float(),
+                                                  fe.COEF_SCALAR, prec=fe.F32))
     pb = fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3)))
     record("3d/boundary_mass", pb, fe.fe_assemble_mass(pb, q3))
+    record("3d/boundary_wmass", pb, fe.fe_assemble_wmass(pb, q3, w3.float(), fe.COEF_P1, prec=fe.F32))
+    p = fe.fe_pattern(q3, me3)
+    coef = cuda(meshgen.general_coefficients(4, 3, m3.nme))
+    record("3d/general/p0", p, fe.fe_assemble_general(p, q3, coef, fe.COEF_P0))
+    coef1 = cuda(meshgen.general_coefficients(5, 3, m3.nq))
+    record("3d/general/p1", p, fe.fe_assemble_general(p, q3, coef1.float(), fe.COEF_P1, prec=fe.F32))
+    mk = meshgen.pk_mesh(3, 4, 2, seed=6)
+    pk = fe.fe_pk_pattern(cuda(mk.q), cuda(mk.me), 2)
+    record("3d/pk2_mass", pk, fe.fe_assemble_mass(pk, cuda(mk.q)))
+    return out
+
+
+class _DeviceInt16:
+    """A borrowed device buffer seen as int16 through the CUDA array interface."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i2", "data": (ptr, False), "version": 3}
+
+
+def corrupted(fe) -> dict:
+    """Bounds-checked build only: corrupt the first vertex incidence code of chunk 1's
+    plan record (a duplicate of the second, or an out-of-range code) and assemble with
+    every chunked kernel. Each must report FE_ERR_BOUNDS for chunk 1 and skip it."""
+    import torch
+    from paper_1401_3301_gb300 import meshgen
+    assert "bounds-checked" in fe.fe_version()  # the normal build would read out of bounds
+    cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    m3 = meshgen.kuhn_cube_mesh(13, seed=4)
+    q3, me3 = cuda(m3.q), cuda(m3.me)
+    mk = meshgen.pk_mesh(3, 6, 2, seed=6)
+    qk = cuda(mk.q)
+    lam = torch.tensor([1.5], dtype=torch.float64, device="cuda")
+    coef = cuda(meshgen.general_coefficients(4, 3, m3.nme))
+    cases = {
+        "stiff/f64": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_stiff(p, q3)),
+        "stiff/f32": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_stiff(p, q3, prec=fe.F32)),
+        "stiff/f64x": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_stiff(p, q3, prec=fe.F64X)),
+        "general": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_general(p, q3, coef, fe.COEF_P0)),
+        "elas": (lambda: fe.fe_pattern(q3, me3, m=3),
+                 lambda p: fe.fe_assemble_elas(p, q3, lam, fe.COEF_SCALAR, lam, fe.COEF_SCALAR)),
+        "boundary": (lambda: fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3))),
+                     lambda p: fe.fe_assemble_mass(p, q3)),
+        "pk2": (lambda: fe.fe_pk_pattern(qk, cuda(mk.me), 2), lambda p: fe.fe_assemble_mass(p, qk)),
+    }
+    out = {}
+    for name, (make, assemble) in cases.items():
+        for how in ("duplicate", "range"):
+            p = make()
+            assert p.nme > p.plan_info()["chunk"], name  # chunk 1 exists
+            ptr, nbytes = p.plan_record(1)
+            rec = torch.as_tensor(_DeviceInt16(ptr, nbytes // 2), device="cuda")
+            if how == "duplicate":
+                rec[0] = rec[1]
+            else:
+                rec[0] = -1  # 0xFFFF
+            torch.cuda.synchronize()
+            assemble(p)
+            out[f"{name}/{how}"] = p.status()
+            p.destroy()
     return out
 
 
@@ -58,6 +119,8 @@ def main(path: str) -> None:
     from paper_1401_3301_gb300 import fe
     out = run(fe)
     out["version"] = np.array(fe.fe_version())
+    for name, st in corrupted(fe).items():
+        out["corrupted:" + name] = np.array(st, dtype=np.int64)
     np.savez(path, **out)
 
 

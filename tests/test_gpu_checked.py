@@ -1,10 +1,11 @@
 """The bounds-checked build (compiled with FE_CHECKED) against the normal build.
 
-Every index the scalar chunk kernel and its fixup take from the plan records is checked
-there against the size of the buffer it addresses (FE_ERR_BOUNDS and a skipped access on
-failure). Running the same assemblies through both builds and finding clean status words
-and bit-identical values shows that no checked index leaves its buffer on these meshes,
-and that the checks change no arithmetic.
+There every chunked kernel validates its plan record in shared memory before using any
+index in it, and every fixup kernel its partial ranges and destinations (FE_ERR_BOUNDS
+and a skipped chunk or entity on failure). Running the same assemblies through both
+builds and finding clean status words and bit-identical values shows that no index
+leaves its buffer on these meshes and that the checks change no arithmetic; a record
+corrupted on purpose, in the checked build only, shows that the checks are live.
 """
 import os
 import subprocess
@@ -33,6 +34,11 @@ def test_checked_build_matches_normal_build(tmp_path):
     got = dict(np.load(path))
     assert "bounds-checked" in str(got.pop("version"))
     assert "bounds-checked" not in fe.fe_version()
+    # a corrupted plan record is reported (FE_ERR_BOUNDS, chunk 1) by every chunked kernel
+    bad = {k: tuple(got.pop(k)) for k in list(got) if k.startswith("corrupted:")}
+    assert len(bad) == 14, sorted(bad)
+    for name, st in bad.items():
+        assert st == (9, 1), (name, st)
 
     import checked_cases
     ref = checked_cases.run(fe)
