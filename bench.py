@@ -71,9 +71,9 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload_config(N):
+def workload_config(N, operator="stiffness"):
     nq, nme = (N + 1) ** 3, 6 * N ** 3
-    return {"workload": f"3D P1 stiffness, fixed-pattern reassembly, Kuhn cube N={N} "
+    return {"workload": f"3D P1 {operator}, fixed-pattern reassembly, Kuhn cube N={N} "
                         f"({nme:,} tets, {nq:,} vertices), jitter 0.15h, elements permuted",
             "mesh": "kuhn_cube", "N": N, "tets": nme, "vertices": nq}
 
@@ -472,7 +472,8 @@ def run_other(args):
         q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
         p = fe.fe_pattern(q, me)
         wv = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                              ("f64x", fe.F64X, torch.float64)):
             vals = torch.empty(p.nnz, dtype=T, device="cuda")
             w = wv.to(T)
             fn = (lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)) if args.workload == "mass" else \
@@ -482,7 +483,8 @@ def run_other(args):
             out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
         out.update(metric=f"3D P1 {'mass' if args.workload == 'mass' else 'weighted mass (P1 vertex weight)'} "
                           "Mtets/s, fixed pattern", unit="Mtets/s",
-                   config=workload_config(args.N))
+                   config=workload_config(args.N, "mass" if args.workload == "mass"
+                                          else "weighted mass (P1 vertex weight)"))
     elif args.workload == "general":
         # convection-diffusion-reaction operator (non-symmetric), per-element and per-vertex
         # coefficient sets of 16 values each
@@ -505,7 +507,8 @@ def run_other(args):
                 res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
             out["forms"][name] = {"value": res["p0_internal"]["value"], "coefficients": res}
         out.update(metric="3D P1 general operator -div(A grad u) + div(b u) + c.grad u + a0 u (non-symmetric) "
-                          "Mtets/s, fixed pattern", unit="Mtets/s", config=workload_config(args.N))
+                          "Mtets/s, fixed pattern", unit="Mtets/s",
+                   config=workload_config(args.N, "general operator (Eq. EDP)"))
     elif args.workload == "pk":
         # 3D P_k mass (App. D) at the largest size of the paper's P_k table, about 10^6 nodes:
         # k N = 100 cells per side on the fine lattice, (kN+1)^3 nodes, for k = 1..6
@@ -609,7 +612,8 @@ def run_other(args):
             out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6,
                                   "rigid_mode_residual": res}
         out.update(metric="3D P1 linear elasticity (12x12 element blocks) Mtets/s, fixed pattern", unit="Mtets/s",
-                   config={**workload_config(N), "E": 1.0, "nu": 0.3, "nnz": p.nnz, "pattern_build_ms": pms})
+                   config={**workload_config(N, "linear elasticity"), "E": 1.0, "nu": 0.3, "nnz": p.nnz,
+                           "pattern_build_ms": pms})
     elif args.workload == "2d":
         m = meshgen.square_mesh(100, seed=0)
         q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
@@ -689,7 +693,7 @@ def run_other(args):
             p.check()
             out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
         out.update(metric="3D stiffness K(w) forward + backward (L = u^T K v, dL/dw, dL/dq) Mtets/s",
-                   unit="Mtets/s", config={**workload_config(N)})
+                   unit="Mtets/s", config={**workload_config(N, "stiffness forward + backward")})
     out["value"] = out["forms"]["f64"]["value"]
     out["dtype"] = "f64"
     print(json.dumps(out), flush=True)

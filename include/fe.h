@@ -55,11 +55,12 @@ extern "C" {
 #define FE_F64 0 /* FP64 arithmetic, FP64 values */
 #define FE_F32 1 /* FP32 values; det B and |K| from FP64-accurate coordinates
                     differences in double-float arithmetic; compensated sums */
-#define FE_F64X 2 /* fe_assemble_stiff only: FP64 values of FP64-class accuracy
+#define FE_F64X 2 /* fe_assemble_mass, fe_assemble_wmass and fe_assemble_stiff on
+                    volume patterns (m = 1, P1): FP64 values of FP64-class accuracy
                     computed in double-float (pairs of floats, about 48 bits) on the
                     FP32 pipe; native FP64 only for coordinates relative to a vertex of
                     each element chunk and for converting sums to double. Coefficients
-                    are double, as for FE_F64. */
+                    are double, as for FE_F64. Other operators and patterns: FE_ERR_ARG. */
 
 /* ---- coefficient kinds (coefficient arrays use the precision of the form:
  *      double for FE_F64, float for FE_F32) */

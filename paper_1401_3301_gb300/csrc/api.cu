@@ -13,8 +13,8 @@ int fe_launch_scalar_f64(fe_pattern_s* h, int kind, const double* q, const void*
                          void* vals, cudaStream_t s);
 int fe_launch_scalar_f32(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind,
                          void* vals, cudaStream_t s);
-int fe_launch_stiff_f64x(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals,
-                         cudaStream_t s);
+int fe_launch_f64x(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, void* vals,
+                   cudaStream_t s);
 int fe_launch_boundary(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, int prec,
                        void* vals, cudaStream_t s);
 int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_kind, const void* mu,
@@ -251,10 +251,10 @@ static int scalar_call(fe_pattern_h h, int kind, const double* q, const void* w,
     if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
     return fe_launch_boundary(h, kind, q, w, w_kind, prec, vals, (cudaStream_t)stream);
   }
-  if (prec == FE_F64X && kind == 3) {  // stiffness only
+  if (prec == FE_F64X) {  // volume patterns, scalar operators
     if (!h || !q || !vals || h->m != 1) return FE_ERR_ARG;
     if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
-    return fe_launch_stiff_f64x(h, q, w, w_kind, vals, (cudaStream_t)stream);
+    return fe_launch_f64x(h, kind, q, w, w_kind, vals, (cudaStream_t)stream);
   }
   FE_TRY(check_common(h, q, prec, vals));
   if (h->m != 1) return FE_ERR_ARG;

@@ -1,15 +1,18 @@
-// FE_F64X form of the stiffness assembly: FP64 inputs and outputs, FP64-class
-// accuracy, arithmetic in double-float (unevaluated sums of two floats, about 48
-// significant bits) on the FP32 pipe, which on this part issues 64 times as many
-// operations per clock as the FP64 pipe. Native FP64 is used only to take each
-// chunk vertex's coordinates relative to a reference vertex of the chunk (so that
-// large coordinate offsets cannot cost accuracy) and to convert each final sum to
-// double.
+// FE_F64X form of the scalar volume operators (mass, weighted mass, stiffness): FP64
+// inputs and outputs, FP64-class accuracy, arithmetic in double-float (unevaluated
+// sums of two floats, about 48 significant bits) on the FP32 pipe, which on this part
+// issues 64 times as many operations per clock as the FP64 pipe. Native FP64 is used
+// only to take each chunk vertex's coordinates relative to a reference vertex of the
+// chunk (so that large coordinate offsets cannot cost accuracy) and to convert each
+// final sum to double; coefficients are split into float pairs without FP64 arithmetic.
 //
-// Local stiffness (Eq. stiffelemmat): S_ab = w (c_a . c_b) / (d! |det B|) with the
-// cofactor vectors c_a of B = [q^1 - q^0, ...]; the row of vertex 0 follows from
-// sum_a c_a = 0. Sums over the incidences of each chunk vertex / edge run in
-// ascending element order, then over chunks in chunk order (as in the other forms).
+// Local matrices, with the cofactor vectors c_a of B = [q^1 - q^0, ...] (the row of
+// vertex 0 follows from sum_a c_a = 0):
+//   stiffness (Eq. stiffelemmat): S_ab = w (c_a . c_b) / (d! |det B|);
+//   mass (Section 4.1): |det B| / (d+2)! (1 + delta_ab), times w for a P0 weight;
+//   P1-weighted mass (Eq. MatElemMassWP1): |det B| / (d+3)! (1 + delta_ab)(w^s + w_a + w_b).
+// Sums over the incidences of each chunk vertex / edge run in ascending element
+// order, then over chunks in chunk order (as in the other forms).
 #include "assemble_impl.cuh"
 #include "profile.cuh"
 
@@ -33,6 +36,19 @@ __device__ __forceinline__ df df_recip(df a) {  // one Newton step from the floa
   return df_add(df{r, 0.f}, df_mul_full(df{r, 0.f}, e));
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// double-float of a double constant, rounded at compile time
+struct DfConst {
+  float hi, lo;
+};
+constexpr DfConst df_const(double x) { return {(float)x, (float)(x - (double)(float)x)}; }
+__device__ __forceinline__ df df_of(DfConst c) { return df{c.hi, c.lo}; }
+__device__ __forceinline__ df df_twice(df a) { return df{2.f * a.hi, 2.f * a.lo}; }  // exact
+__device__ __forceinline__ df df_split(double x) {
+  float h, l;
+  split_f64(x, h, l);
+  return df{h, l};
+}
 
 // a*b - c*d for double-float operands: exact double-float of the high parts plus the
 // first-order terms of the low parts
@@ -71,9 +87,9 @@ struct X64Args {
   int64_t nnz, npart;  // sizes of vals and of the partial sums (bounds-checked builds)
 };
 
-template <int D, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double* __restrict__ vals,
-                                                              float2* __restrict__ partials) {
+template <int D, int KIND, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __restrict__ vals,
+                                                        float2* __restrict__ partials) {
   constexpr int NV = D + 1, NP = Pairs<D>::n;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
@@ -84,7 +100,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   // same footprint as the FP32 form: split coordinates, uint16 corner map, float2 values
-  const StagedSmem S = staged_smem(D, 8, false, A.rec_max, A.max_lv, A.chunk);
+  const StagedSmem S = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
@@ -97,6 +113,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
   uint16_t* lvid = (uint16_t*)(smem + S.lvid);
   float2* Kd = (float2*)(smem + S.kd);
   float2* Ko = (float2*)(smem + S.ko);
+  float2* wl = (float2*)(smem + S.w);  // P1 weight of each chunk vertex
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   // 0. coordinates relative to corner 0 of the chunk's first element (FP64), split into
@@ -119,6 +136,10 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
     } else {
       xs[0] = make_float4(h[0], h[1], l[0], l[1]);
     }
+    if constexpr (KIND == K_WMASS_P1) {
+      const df wv = df_split(A.w[vid]);
+      wl[u] = make_float2(wv.hi, wv.lo);
+    }
     for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
@@ -126,9 +147,11 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
   // 1. element entries in double-float
   for (int el = threadIdx.x; el < ne; el += THREADS) {
     float xh[NV][D], xl[NV][D];
+    int lv[NV];
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-      const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lvid[el * NV + a];
+      lv[a] = lvid[el * NV + a];
+      const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lv[a];
       const float4 h = xs[0];
       if constexpr (D == 3) {
         const float4 l = xs[1];
@@ -173,13 +196,44 @@ __global__ void __launch_bounds__(THREADS) k_chunk_stiff_f64x(X64Args A, double*
       det = df{1.f, 0.f};
     }
     if (det.hi < 0.f) det = df_neg(det);
-    df inv = df_recip(df_mul_full(det, df{(float)factorial(D), 0.f}));
-    if (A.w_kind != FE_COEF_NONE) {
-      const double wv = elem_coef<double>(A.w, A.w_kind, A.order, e0 + el);
-      float wh, wl;
-      split_f64(wv, wh, wl);
-      inv = df_mul_full(inv, df{wh, wl});
+    if constexpr (KIND != K_STIFF) {
+      df dv[NV], ov[NP];
+      if constexpr (KIND == K_WMASS_P1) {
+        constexpr DfConst kC = df_const(1.0 / factorial(D + 3));
+        const df base = df_mul_full(det, df_of(kC));
+        df w[NV];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+          const float2 x = wl[lv[a]];
+          w[a] = df{x.x, x.y};
+        }
+        df ws = w[0];
+#pragma unroll
+        for (int a = 1; a < NV; ++a) ws = df_add(ws, w[a]);
+#pragma unroll
+        for (int a = 0; a < NV; ++a) dv[a] = df_twice(df_mul_full(base, df_add(ws, df_twice(w[a]))));
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+          ov[p] = df_mul_full(base, df_add(ws, df_add(w[Pairs<D>::a(p)], w[Pairs<D>::b(p)])));
+      } else {
+        constexpr DfConst kC = df_const(1.0 / factorial(D + 2));
+        df m = df_mul_full(det, df_of(kC));
+        if (A.w_kind != FE_COEF_NONE)
+          m = df_mul_full(m, df_split(elem_coef<double>(A.w, A.w_kind, A.order, e0 + el)));
+#pragma unroll
+        for (int a = 0; a < NV; ++a) dv[a] = df_twice(m);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) ov[p] = m;
+      }
+#pragma unroll
+      for (int a = 0; a < NV; ++a) Kd[el * NV + a] = make_float2(dv[a].hi, dv[a].lo);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) Ko[el * NP + p] = make_float2(ov[p].hi, ov[p].lo);
+      continue;
     }
+    df inv = df_recip(df_mul_full(det, df{(float)factorial(D), 0.f}));
+    if (A.w_kind != FE_COEF_NONE)
+      inv = df_mul_full(inv, df_split(elem_coef<double>(A.w, A.w_kind, A.order, e0 + el)));
     df G[D][D];
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -261,12 +315,12 @@ __global__ void k_fixup_f64x(const int32_t* __restrict__ sh_ptr, const int32_t* 
   if (g >= nsh_v) vals[sh_dst[2 * g + 1]] = val;
 }
 
-template <int D>
+template <int D, int KIND>
 int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
-  const StagedSmem L = staged_smem(D, 8, false, A.rec_max, A.max_lv, A.chunk);
+  const StagedSmem L = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
-  auto kern = k_chunk_stiff_f64x<D, THREADS>;
+  auto kern = k_chunk_f64x<D, KIND, THREADS>;
   static size_t configured = 0;
   FE_TRY(fe_smem_limit(kern, L.total, configured));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
@@ -285,15 +339,26 @@ int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   return FE_OK;
 }
 
+template <int D>
+int launch_kind(fe_pattern_s* h, int kind, const X64Args& A, double* vals, cudaStream_t s) {
+  switch (kind) {
+    case K_MASS: return launch<D, K_MASS>(h, A, vals, s);
+    case K_WMASS_P1: return launch<D, K_WMASS_P1>(h, A, vals, s);
+    case K_WMASS_P0: return launch<D, K_WMASS_P0>(h, A, vals, s);
+    default: return launch<D, K_STIFF>(h, A, vals, s);
+  }
+}
+
 }  // namespace
 }  // namespace fe
 
-int fe_launch_stiff_f64x(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals,
-                         cudaStream_t s) {
+int fe_launch_f64x(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, void* vals,
+                   cudaStream_t s) {
   using namespace fe;
   if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
   X64Args A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, (const double*)w,
             w_kind, h->order, h->me_int, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status,
             h->nnz_s, h->npart};
-  return h->d == 3 ? launch<3>(h, A, (double*)vals, s) : launch<2>(h, A, (double*)vals, s);
+  if (h->d == 3) return launch_kind<3>(h, kind, A, (double*)vals, s);
+  return launch_kind<2>(h, kind, A, (double*)vals, s);
 }

@@ -1,5 +1,6 @@
-"""FE_F64X stiffness: FP64 results of FP64-class accuracy from double-float arithmetic.
-Same gate as the FP64 form (1e-12 normalised error vs the FP64 oracle)."""
+"""FE_F64X form of mass, weighted mass and stiffness: FP64 results of FP64-class accuracy
+from double-float arithmetic. Same gate as the FP64 form (1e-12 normalised error vs the
+FP64 oracle)."""
 import numpy as np
 import pytest
 
@@ -30,14 +31,53 @@ def test_f64x_matches_oracle_to_fp64_tolerance(d, N, offset):
         assert bool((again == vals).all())
 
 
+@pytest.mark.parametrize("d,N,offset", [(2, 37, 0.0), (3, 9, 0.0), (3, 8, 1000.0), (2, 25, -3000.5)])
+def test_f64x_mass_and_weighted_mass_match_oracle(d, N, offset):
+    fe = fe_or_skip()
+    import torch
+    m = meshgen.square_mesh(N, seed=N) if d == 2 else meshgen.kuhn_cube_mesh(N, seed=N)
+    qn = m.q + offset
+    q, me = to_cuda(qn), to_cuda(m.me)
+    p = fe.fe_pattern(q, me)
+    wv = meshgen.vertex_weights(N, m.nq)
+    we = meshgen.element_weights(N, m.nme)
+    cases = [
+        (lambda: fe.fe_assemble_mass(p, q, prec=fe.F64X), oracle.assemble(oracle.MASS, qn, m.me)),
+        (lambda: fe.fe_assemble_wmass(p, q, to_cuda(wv), fe.COEF_P1, prec=fe.F64X),
+         oracle.assemble(oracle.WMASS, qn, m.me, c1=(oracle.COEF_P1, wv))),
+        (lambda: fe.fe_assemble_wmass(p, q, to_cuda(we), fe.COEF_P0, prec=fe.F64X),
+         oracle.assemble(oracle.WMASS, qn, m.me, c1=(oracle.COEF_P0, we))),
+    ]
+    for k, (run, ref) in enumerate(cases):
+        vals = run()
+        assert vals.dtype == torch.float64
+        assert p.status() == (0, -1)
+        err = normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"])
+        assert err <= 1e-12, (k, err)
+        assert bool((run() == vals).all())
+
+
 def test_f64x_reports_degenerate_elements_and_rejects_other_operators():
     fe = fe_or_skip()
+    import torch
     m = meshgen.square_mesh(6, seed=3)
     qb = m.q.copy()
     a, b, c = m.me[:, 4]
     qb[:, c] = qb[:, a]
     p = fe.fe_pattern(to_cuda(m.q), to_cuda(m.me))
-    fe.fe_assemble_stiff(p, to_cuda(qb), prec=fe.F64X)
-    assert p.status()[0] == 3
+    bad = [e for e in range(m.nme) if a in m.me[:, e] and c in m.me[:, e]]
+    for run in (lambda: fe.fe_assemble_stiff(p, to_cuda(qb), prec=fe.F64X),
+                lambda: fe.fe_assemble_mass(p, to_cuda(qb), prec=fe.F64X)):
+        run()
+        assert p.status() == (3, min(bad))
+    # F64X is a form of the scalar volume operators only
+    coef = torch.ones((m.nme, 9), dtype=torch.float64, device="cuda")
     with pytest.raises(fe.FEError):
-        fe.fe_assemble_mass(p, to_cuda(m.q), prec=fe.F64X)
+        fe.fe_assemble_general(p, to_cuda(m.q), coef, fe.COEF_P0, prec=fe.F64X)
+    pe = fe.fe_pattern(to_cuda(m.q), to_cuda(m.me), m=2)
+    one = torch.ones(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(fe.FEError):
+        fe.fe_assemble_elas(pe, to_cuda(m.q), one, fe.COEF_SCALAR, one, fe.COEF_SCALAR, prec=fe.F64X)
+    pb = fe.fe_boundary_pattern(to_cuda(m.q), to_cuda(meshgen.boundary_facets(m)))
+    with pytest.raises(fe.FEError):
+        fe.fe_assemble_mass(pb, to_cuda(m.q), prec=fe.F64X)
