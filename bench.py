@@ -648,7 +648,8 @@ def run_other(args):
         fe.fe_batch_gather_q(p, qs, mes, qu)
         del qs, mes
         ntri = int(eo[-1])
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                              ("f64x", fe.F64X, torch.float64)):
             w = torch.ones(ntri, dtype=T, device="cuda")
             s = torch.empty(p.nnz, dtype=T, device="cuda")
             mm_ = torch.empty(p.nnz, dtype=T, device="cuda")
