@@ -585,7 +585,8 @@ def run_other(args):
         p = fe.fe_pattern(q, me, m=3)
         pms = (time.perf_counter() - t0) * 1e3
         lam0, mu0 = meshgen.lame_from_young(1.0, 0.3)
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                              ("f64x", fe.F64X, torch.float64)):
             vals = torch.empty(p.nnz, dtype=T, device="cuda")
             lam = torch.tensor([lam0], dtype=T, device="cuda")
             mu = torch.tensor([mu0], dtype=T, device="cuda")

@@ -55,8 +55,8 @@ extern "C" {
 #define FE_F64 0 /* FP64 arithmetic, FP64 values */
 #define FE_F32 1 /* FP32 values; det B and |K| from FP64-accurate coordinates
                     differences in double-float arithmetic; compensated sums */
-#define FE_F64X 2 /* fe_assemble_mass, fe_assemble_wmass and fe_assemble_stiff on
-                    volume patterns (m = 1, P1): FP64 values of FP64-class accuracy
+#define FE_F64X 2 /* fe_assemble_mass, fe_assemble_wmass, fe_assemble_stiff and
+                    fe_assemble_elas on volume P1 patterns: FP64 values of FP64-class accuracy
                     computed in double-float (pairs of floats, about 48 bits) on the
                     FP32 pipe; native FP64 only for coordinates relative to a vertex of
                     each element chunk and for converting sums to double. Coefficients
@@ -313,6 +313,8 @@ int fe_assemble_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_
  * lem:VecLocalElas, App. B), lambda^s and mu^s the sums of the vertex values of
  * the P1 interpolants (a P0 or scalar coefficient counts as d+1 equal values).
  * lam_kind / mu_kind: FE_COEF_SCALAR, FE_COEF_P0, FE_COEF_P0_INTERNAL or FE_COEF_P1.
+ * prec: FE_F64, FE_F32 or FE_F64X (double coefficients and values, double-float
+ * arithmetic). Chunked strategy only.
  */
 int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t lam_kind,
                      const void* mu, int32_t mu_kind, int32_t prec, void* vals, void* stream);

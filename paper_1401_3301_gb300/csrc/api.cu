@@ -286,7 +286,8 @@ int fe_assemble_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_
 
 int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t lam_kind,
                      const void* mu, int32_t mu_kind, int32_t prec, void* vals, void* stream) {
-  FE_TRY(check_common(h, q, prec, vals));
+  if (prec == FE_F64X) FE_TRY(check_common(h, q, FE_F64, vals));  // F64X: FP64 values and coefficients
+  else FE_TRY(check_common(h, q, prec, vals));
   if (h->m != h->d || !lam || !mu) return FE_ERR_ARG;
   auto ok = [](int k) {
     return k == FE_COEF_SCALAR || k == FE_COEF_P0 || k == FE_COEF_P0_INTERNAL || k == FE_COEF_P1;

@@ -14,61 +14,11 @@
 // Sums over the incidences of each chunk vertex / edge run in ascending element
 // order, then over chunks in chunk order (as in the other forms).
 #include "assemble_impl.cuh"
+#include "dfloat.cuh"
 #include "profile.cuh"
 
 namespace fe {
 namespace {
-
-// double-float helpers on top of elem.cuh: products with the low parts, reciprocal
-__device__ __forceinline__ df df_mul_full(df a, df b) {  // relative error ~2^-47
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
-__device__ __forceinline__ df df_recip(df a) {  // one Newton step from the float reciprocal
-  const float r = __frcp_rn(a.hi);
-  // e = 1 - a r in double-float, then r (1 + e)
-  const df ar = df_mul_full(a, df{r, 0.f});
-  const df e = df_add(df{1.f, 0.f}, df_neg(ar));
-  return df_add(df{r, 0.f}, df_mul_full(df{r, 0.f}, e));
-}
-__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
-
-// double-float of a double constant, rounded at compile time
-struct DfConst {
-  float hi, lo;
-};
-constexpr DfConst df_const(double x) { return {(float)x, (float)(x - (double)(float)x)}; }
-__device__ __forceinline__ df df_of(DfConst c) { return df{c.hi, c.lo}; }
-__device__ __forceinline__ df df_twice(df a) { return df{2.f * a.hi, 2.f * a.lo}; }  // exact
-__device__ __forceinline__ df df_split(double x) {
-  float h, l;
-  split_f64(x, h, l);
-  return df{h, l};
-}
-
-// a*b - c*d for double-float operands: exact double-float of the high parts plus the
-// first-order terms of the low parts
-__device__ __forceinline__ df df_cross_term(df a, df b, df c, df d) {
-  const df h = diff_of_products(a.hi, b.hi, c.hi, d.hi);
-  float lo = h.lo;
-  lo = __fmaf_rn(a.lo, b.hi, lo);
-  lo = __fmaf_rn(a.hi, b.lo, lo);
-  lo = __fmaf_rn(-c.lo, d.hi, lo);
-  lo = __fmaf_rn(-c.hi, d.lo, lo);
-  return fast_two_sum(h.hi, lo);
-}
-
-template <int D>
-__device__ __forceinline__ df df_dot(const df* x, const df* y) {
-  df s = df_mul_full(x[0], y[0]);
-#pragma unroll
-  for (int k = 1; k < D; ++k) s = df_add(s, df_mul_full(x[k], y[k]));
-  return s;
-}
 
 struct X64Args {
   int64_t nme, nq;
@@ -126,16 +76,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __res
   }
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
-    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < D; ++k) split_f64(__ldg(A.q + k * A.nq + vid) - xr[k], h[k], l[k]);
-    float4* xs = (float4*)(smem + S.q) + (D == 3 ? 2 : 1) * u;
-    if constexpr (D == 3) {
-      xs[0] = make_float4(h[0], h[1], h[2], 0.f);
-      xs[1] = make_float4(l[0], l[1], l[2], 0.f);
-    } else {
-      xs[0] = make_float4(h[0], h[1], l[0], l[1]);
-    }
+    x64_stage_vertex<D>(A.q, A.nq, vid, xr, smem + S.q, u);
     if constexpr (KIND == K_WMASS_P1) {
       const df wv = df_split(A.w[vid]);
       wl[u] = make_float2(wv.hi, wv.lo);
@@ -146,52 +87,12 @@ __global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __res
 
   // 1. element entries in double-float
   for (int el = threadIdx.x; el < ne; el += THREADS) {
-    float xh[NV][D], xl[NV][D];
     int lv[NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      lv[a] = lvid[el * NV + a];
-      const float4* xs = (const float4*)(smem + S.q) + (D == 3 ? 2 : 1) * lv[a];
-      const float4 h = xs[0];
-      if constexpr (D == 3) {
-        const float4 l = xs[1];
-        xh[a][0] = h.x; xh[a][1] = h.y; xh[a][2] = h.z;
-        xl[a][0] = l.x; xl[a][1] = l.y; xl[a][2] = l.z;
-      } else {
-        xh[a][0] = h.x; xh[a][1] = h.y;
-        xl[a][0] = h.z; xl[a][1] = h.w;
-      }
-    }
-    df e[D][D];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const df s = two_sum(xh[i + 1][k], -xh[0][k]);
-        e[i][k] = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][k], xl[0][k])));
-      }
+    for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     df cf[D][D];  // cofactor vectors c_1..c_D
-    df det;
-    if constexpr (D == 3) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const df* u1 = e[(i + 1) % 3];
-        const df* u2 = e[(i + 2) % 3];
-        cf[i][0] = df_cross_term(u1[1], u2[2], u1[2], u2[1]);
-        cf[i][1] = df_cross_term(u1[2], u2[0], u1[0], u2[2]);
-        cf[i][2] = df_cross_term(u1[0], u2[1], u1[1], u2[0]);
-      }
-      det = df_dot<3>(e[0], cf[0]);
-    } else {
-      cf[0][0] = e[1][1];
-      cf[0][1] = df_neg(e[1][0]);
-      cf[1][0] = df_neg(e[0][1]);
-      cf[1][1] = e[0][0];
-      det = df_cross_term(e[0][0], e[1][1], e[0][1], e[1][0]);
-    }
-    const float dh = __fadd_rn(det.hi, det.lo);
-    const unsigned int ex = (__float_as_uint(dh) >> 23) & 0xFFu;
-    if (ex == 0u || ex == 0xFFu) {
+    df det = x64_geometry<D>(smem + S.q, lv, cf);
+    if (df_degenerate(det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       det = df{1.f, 0.f};
     }

@@ -12,6 +12,7 @@
 // vertices (diagonal blocks) and edges (off-diagonal blocks, written at (i,j) and,
 // transposed, at (j,i)), in ascending element order.
 #include "assemble_impl.cuh"
+#include "dfloat.cuh"
 #include "profile.cuh"
 
 namespace fe {
@@ -33,6 +34,7 @@ struct ElasArgs {
   const uint32_t* rec_off16;
   fe_status_word* st;
   int64_t nnz, npart;  // sizes of vals and of the partial blocks (bounds-checked builds)
+  const int32_t* me0;  // F64X form: corner 0 of each internal element (chunk reference vertex)
 };
 
 // sum over the element's vertices of a coefficient's P1 values (lambda^s, mu^s)
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
 // Sum, in chunk order, of the partial blocks of each shared vertex / edge: one thread per
 // (entity, block entry), so that neighbouring threads read neighbouring words of the
 // partial blocks (partial i of the entity holds its m x m block at i * MM).
-template <int D, class T>
+template <int D, class T, class AccT = Acc<T>>
 __global__ void k_fixup_elas(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
                              const int32_t* __restrict__ sh_str, int64_t nsh_v, int64_t nsh,
                              const void* __restrict__ partials, T* __restrict__ vals, int64_t nnz,
@@ -280,7 +282,7 @@ __global__ void k_fixup_elas(const int32_t* __restrict__ sh_ptr, const int32_t* 
   if (!FE_FIXUP_VALID(s, t, npart, (int64_t)sh_dst[2 * g] + (k / D) * sh_str[2 * g] + k % D,
                       (int64_t)sh_dst[2 * g + 1] + (k % D) * sh_str[2 * g + 1] + k / D, g >= nsh_v, nnz, st, g))
     return;
-  Acc<T> acc = Acc<T>::from_partial(partials, (int64_t)s * MM + k);
+  AccT acc = AccT::from_partial(partials, (int64_t)s * MM + k);
   for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, (int64_t)i * MM + k);
   const T v = acc.value();
   const int l = k / D, n = k % D;
@@ -312,6 +314,239 @@ int launch(fe_pattern_s* h, const ElasArgs& A, T* vals, cudaStream_t s) {
   return FE_OK;
 }
 
+
+// ---------------------------------------------------------------- FE_F64X form
+// The same element blocks and fixed-order sums in double-float on the FP32 pipe: the
+// coordinates relative to the chunk's reference vertex are split into float pairs
+// (as for the F64X scalar operators), the cofactor vectors and scaled Lame sums are
+// kept as float pairs in shared memory, and every block entry is formed and summed in
+// double-float. Coefficient arrays are double.
+
+// lambda^s (or mu^s) of one element in double-float
+template <int D>
+__device__ __forceinline__ df coef_sum_x(const void* c, int kind, const int32_t* order, int64_t e,
+                                         const float2* local_p1, const int lv[D + 1]) {
+  if (kind == FE_COEF_P1) {
+    float2 v = local_p1[lv[0]];
+    df s{v.x, v.y};
+#pragma unroll
+    for (int a = 1; a <= D; ++a) {
+      v = local_p1[lv[a]];
+      s = df_add(s, df{v.x, v.y});
+    }
+    return s;
+  }
+  const double* cp = (const double*)c;
+  const double v = kind == FE_COEF_SCALAR ? cp[0] : (kind == FE_COEF_P0 ? cp[order[e]] : cp[e]);
+  return df_mul_full(df_split(v), df{(float)(D + 1), 0.f});
+}
+
+__device__ __forceinline__ df ld_df(const float2* p) {
+  const float2 v = *p;
+  return df{v.x, v.y};
+}
+
+template <int D, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __restrict__ vals,
+                                                          float2* __restrict__ partials) {
+  constexpr int NV = D + 1, NP = Pairs<D>::n, MM = D * D;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t c = blockIdx.x;
+  const int64_t e0 = c * A.chunk;
+  const int ne = (int)min((int64_t)A.chunk, A.nme - e0);
+  const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
+  const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
+  const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle, true);
+  const ElasSmem S = elas_smem(D, 8, A.rec_max, A.max_lv, A.chunk);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
+  const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
+  const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
+  const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
+  const uint16_t* le_off = (const uint16_t*)(smem + R.le_off);
+  const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
+  const uint16_t* lv_str = (const uint16_t*)(smem + R.lv_str);
+  const uint16_t* le_str = (const uint16_t*)(smem + R.le_str);
+  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  float2* lam_l = (float2*)(smem + S.coef);
+  float2* mu_l = lam_l + A.max_lv;
+  float2* Cg = (float2*)(smem + S.cg);  // [e][a][i]
+  float2* LM = (float2*)(smem + S.lm);  // [e][2]
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+
+  // 0. coordinates relative to corner 0 of the chunk's first element, split into float
+  //    pairs; P1 Lame values; local vertex of each corner
+  double xr[D];
+  {
+    const int64_t v0 = A.me0[e0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
+  }
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int64_t vid = lv_vid[u];
+    x64_stage_vertex<D>(A.q, A.nq, vid, xr, smem + S.q, u);
+    if (A.lam_kind == FE_COEF_P1) {
+      const df v = df_split(((const double*)A.lam)[vid]);
+      lam_l[u] = make_float2(v.hi, v.lo);
+    }
+    if (A.mu_kind == FE_COEF_P1) {
+      const df v = df_split(((const double*)A.mu)[vid]);
+      mu_l[u] = make_float2(v.hi, v.lo);
+    }
+    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
+  }
+  __syncthreads();
+
+  // 1. cofactor vectors (c_0 = -sum c_a) and scaled Lame sums of every element
+  for (int el = threadIdx.x; el < ne; el += THREADS) {
+    int lv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
+    df cf[D][D];
+    df det = x64_geometry<D>(smem + S.q, lv, cf);
+    if (df_degenerate(det)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+      det = df{1.f, 0.f};
+    }
+    if (det.hi < 0.f) det = df_neg(det);
+    const df scale = df_recip(df_mul_full(det, df{(float)(factorial(D) * (D + 1)), 0.f}));
+    const df ls = coef_sum_x<D>(A.lam, A.lam_kind, A.order, e0 + el, lam_l, lv);
+    const df ms = coef_sum_x<D>(A.mu, A.mu_kind, A.order, e0 + el, mu_l, lv);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      df s = cf[0][i];
+#pragma unroll
+      for (int a = 1; a < D; ++a) s = df_add(s, cf[a][i]);
+      Cg[(el * NV) * D + i] = make_float2(-s.hi, -s.lo);
+#pragma unroll
+      for (int a = 1; a < NV; ++a) Cg[(el * NV + a) * D + i] = make_float2(cf[a - 1][i].hi, cf[a - 1][i].lo);
+    }
+    const df lp = df_mul_full(ls, scale), mp = df_mul_full(ms, scale);
+    LM[2 * el] = make_float2(lp.hi, lp.lo);
+    LM[2 * el + 1] = make_float2(mp.hi, mp.lo);
+  }
+  __syncthreads();
+
+  // 2a. diagonal blocks (lp + mp) x x^T + mp |x|^2 I over the (element, corner)
+  //     incidences of each vertex, in element order
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int s = lv_off[u], t = lv_off[u + 1];
+    AccX acc[MM];
+    for (int j = s; j < t; ++j) {
+      const int inc = inc_v[j];
+      const int el = inc / NV;
+      df x[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) x[i] = ld_df(Cg + inc * D + i);
+      const df lp = ld_df(LM + 2 * el), mp = ld_df(LM + 2 * el + 1);
+      const df lm = df_add(lp, mp);
+      const df mxx = df_mul_full(mp, df_dot<D>(x, x));
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        const df lx = df_mul_full(lm, x[l]);
+#pragma unroll
+        for (int n = 0; n < D; ++n) {
+          const df v = df_mul_full(lx, x[n]);
+          if (j == s) acc[l * D + n] = AccX(v);
+          else acc[l * D + n].add(v);
+        }
+        acc[l * D + l].add(mxx);
+      }
+    }
+    const int32_t dst = lv_dst[u];
+    if (dst >= 0) {
+      const int str = lv_str[u];
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+#pragma unroll
+        for (int n = 0; n < D; ++n) vals[dst + l * str + n] = acc[l * D + n].value();
+    } else {
+      const int64_t pi = (-1 - (int64_t)dst) * MM;
+#pragma unroll
+      for (int k = 0; k < MM; ++k) acc[k].store_partial(partials, pi + k);
+    }
+  }
+  // 2b. off-diagonal blocks lp x y^T + mp (y x^T + (x . y) I) over the (element, pair)
+  //     incidences of each edge, oriented (vmin, vmax), in element order
+  for (int u = threadIdx.x; u < nle; u += THREADS) {
+    const int s = le_off[u], t = le_off[u + 1];
+    AccX acc[MM];
+    for (int j = s; j < t; ++j) {
+      const int code = inc_e[j];
+      const int ep = code >> 1;
+      const int el = ep / NP, p = ep - el * NP;
+      int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
+      if (code & 1) {  // me(a) > me(b): the (vmin, vmax) block is block (b, a)
+        const int t2 = a; a = b; b = t2;
+      }
+      df x[D], y[D], px[D], qy[D];
+      const df lp = ld_df(LM + 2 * el), mp = ld_df(LM + 2 * el + 1);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        x[i] = ld_df(Cg + (el * NV + a) * D + i);
+        y[i] = ld_df(Cg + (el * NV + b) * D + i);
+        px[i] = df_mul_full(lp, x[i]);
+        qy[i] = df_mul_full(mp, y[i]);
+      }
+      const df mxy = df_dot<D>(qy, x);
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+#pragma unroll
+        for (int n = 0; n < D; ++n) {
+          const df v = df_mul_full(px[l], y[n]);
+          if (j == s) acc[l * D + n] = AccX(v);
+          else acc[l * D + n].add(v);
+          acc[l * D + n].add(df_mul_full(qy[l], x[n]));
+        }
+        acc[l * D + l].add(mxy);
+      }
+    }
+    const int32_t dst = le_dst[2 * u];
+    if (dst >= 0) {
+      const int32_t dst_t = le_dst[2 * u + 1];
+      const int str = le_str[2 * u], str_t = le_str[2 * u + 1];
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+#pragma unroll
+        for (int n = 0; n < D; ++n) {
+          const double v = acc[l * D + n].value();
+          vals[dst + l * str + n] = v;
+          vals[dst_t + n * str_t + l] = v;
+        }
+    } else {
+      const int64_t pi = (-1 - (int64_t)dst) * MM;
+#pragma unroll
+      for (int k = 0; k < MM; ++k) acc[k].store_partial(partials, pi + k);
+    }
+  }
+}
+
+template <int D>
+int launch_x(fe_pattern_s* h, const ElasArgs& A, double* vals, cudaStream_t s) {
+  constexpr int THREADS = 256;
+  const ElasSmem L = elas_smem(D, 8, A.rec_max, A.max_lv, A.chunk);
+  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  auto kern = k_chunk_elas_x<D, THREADS>;
+  static size_t configured = 0;
+  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_PROF_BEGIN(h, FE_K_ELAS_CHUNK, s);
+  kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, (float2*)h->partials);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_PROF_END(h, FE_K_ELAS_CHUNK, s);
+  const int64_t nsh = h->nsh_v + h->nsh_e;
+  if (nsh > 0) {
+    FE_PROF_BEGIN(h, FE_K_ELAS_FIXUP, s);
+    k_fixup_elas<D, double, AccX><<<fe_grid(nsh * D * D, 256), 256, 0, s>>>(
+        h->sh_ptr, h->sh_dst, h->sh_str, h->nsh_v, nsh, h->partials, vals, h->nnz, h->npart, h->status);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_PROF_END(h, FE_K_ELAS_FIXUP, s);
+  }
+  return FE_OK;
+}
+
 }  // namespace
 }  // namespace fe
 
@@ -321,7 +556,9 @@ int fe_launch_elas(fe_pattern_s* h, const double* q, const void* lam, int lam_ki
   if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;  // vector problems: chunked only
   ElasArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, lam, lam_kind,
              mu, mu_kind, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status, h->nnz,
-             h->npart};
+             h->npart, h->me_int};
+  if (prec == FE_F64X)
+    return h->d == 3 ? launch_x<3>(h, A, (double*)vals, s) : launch_x<2>(h, A, (double*)vals, s);
   if (prec == FE_F64)
     return h->d == 3 ? launch<3, double>(h, A, (double*)vals, s) : launch<2, double>(h, A, (double*)vals, s);
   return h->d == 3 ? launch<3, float>(h, A, (float*)vals, s) : launch<2, float>(h, A, (float*)vals, s);

@@ -49,6 +49,7 @@ def run(fe) -> dict:
     lam = torch.tensor([1.5], dtype=torch.float64, device="cuda")
     mu = torch.tensor([0.7], dtype=torch.float64, device="cuda")
     record("3d/elas", pe, fe.fe_assemble_elas(pe, q3, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR))
+    record("3d/elas/f64x", pe, fe.fe_assemble_elas(pe, q3, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR, prec=fe.F64X))
     record("3d/elas/f32", pe, fe.fe_assemble_elas(pe, q3, lam.float(), fe.COEF_SCALAR, mu.float(),
                                                   fe.COEF_SCALAR, prec=fe.F32))
     pb = fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3)))
@@ -93,6 +94,9 @@ def corrupted(fe) -> dict:
         "general": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_general(p, q3, coef, fe.COEF_P0)),
         "elas": (lambda: fe.fe_pattern(q3, me3, m=3),
                  lambda p: fe.fe_assemble_elas(p, q3, lam, fe.COEF_SCALAR, lam, fe.COEF_SCALAR)),
+        "elas/f64x": (lambda: fe.fe_pattern(q3, me3, m=3),
+                      lambda p: fe.fe_assemble_elas(p, q3, lam, fe.COEF_SCALAR, lam, fe.COEF_SCALAR,
+                                                    prec=fe.F64X)),
         "boundary": (lambda: fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3))),
                      lambda p: fe.fe_assemble_mass(p, q3)),
         "pk2": (lambda: fe.fe_pk_pattern(qk, cuda(mk.me), 2), lambda p: fe.fe_assemble_mass(p, qk)),

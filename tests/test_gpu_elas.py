@@ -8,7 +8,7 @@ from helpers import assert_pattern_equal, fe_or_skip, normalised_error, to_cuda
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5}
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
 
 
 def mesh(d, N, seed):
@@ -30,11 +30,11 @@ def coef(kind, m, seed, base):
 
 @pytest.mark.parametrize("d,N", [(2, 13), (3, 5), (3, 9)])
 @pytest.mark.parametrize("kind", ["scalar", "p0", "p1"])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_elasticity_parity(d, N, kind, prec):
     fe = fe_or_skip()
     import torch
-    T = torch.float64 if prec == 0 else torch.float32
+    T = torch.float32 if prec == 1 else torch.float64
     m = mesh(d, N, seed=50 + N)
     lam0, mu0 = meshgen.lame_from_young(1.0, 0.3)
     lo, ld, lk = coef(kind, m, 1, lam0)
@@ -50,8 +50,9 @@ def test_elasticity_parity(d, N, kind, prec):
     assert err <= TOL[prec], err
 
 
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("d", [2, 3])
-def test_elasticity_rigid_modes_gpu_and_bit_identity(d):
+def test_elasticity_rigid_modes_gpu_and_bit_identity(d, prec):
     fe = fe_or_skip()
     import torch
     m = mesh(d, 24 if d == 2 else 8, seed=60)
@@ -60,8 +61,8 @@ def test_elasticity_rigid_modes_gpu_and_bit_identity(d):
     p = fe.fe_pattern(q, me, m=d)
     lam = torch.tensor([lam0], dtype=torch.float64, device="cuda")
     mu = torch.tensor([mu0], dtype=torch.float64, device="cuda")
-    vals = fe.fe_assemble_elas(p, q, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR)
-    again = fe.fe_assemble_elas(p, q, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR)
+    vals = fe.fe_assemble_elas(p, q, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR, prec=prec)
+    again = fe.fe_assemble_elas(p, q, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR, prec=prec)
     assert bool((vals == again).all())
     rp, ci = (t.cpu().numpy() for t in p.csr())
     v = vals.cpu().numpy()
