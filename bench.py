@@ -681,7 +681,8 @@ def run_other(args):
         p = fe.fe_pattern(q, me)
         w64 = torch.from_numpy(meshgen.element_weights(0, m.nme)).cuda()
         u64, v64 = (torch.from_numpy(x).cuda() for x in meshgen.random_vectors(0, m.nq))
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                              ("f64x", fe.F64X, torch.float64)):
             w, u, v = w64.to(T), u64.to(T), v64.to(T)
             vals = torch.empty(p.nnz, dtype=T, device="cuda")
             L = torch.empty(1, dtype=T, device="cuda")

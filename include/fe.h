@@ -55,8 +55,9 @@ extern "C" {
 #define FE_F64 0 /* FP64 arithmetic, FP64 values */
 #define FE_F32 1 /* FP32 values; det B and |K| from FP64-accurate coordinates
                     differences in double-float arithmetic; compensated sums */
-#define FE_F64X 2 /* fe_assemble_mass, fe_assemble_wmass, fe_assemble_stiff and
-                    fe_assemble_elas on volume P1 patterns: FP64 values of FP64-class accuracy
+#define FE_F64X 2 /* fe_assemble_mass, fe_assemble_wmass, fe_assemble_stiff (and its
+                    backward and VJP) and fe_assemble_elas on volume P1 patterns: FP64
+                    values of FP64-class accuracy
                     computed in double-float (pairs of floats, about 48 bits) on the
                     FP32 pipe; native FP64 only for coordinates relative to a vertex of
                     each element chunk and for converting sums to double. Coefficients
@@ -377,7 +378,8 @@ int fe_assemble_stiff_host(fe_pattern_h h, const double* q_host, const void* w_h
  *   dL_dw       nme values (input element order, or internal for
  *               FE_COEF_P0_INTERNAL), or NULL
  *   dL_dq       d x nq like q, or NULL
- * All of u, v, L, dL_dw, dL_dq (and w) use the precision of the form. Sums over
+ * All of u, v, L, dL_dw, dL_dq (and w) use the precision of the form (double for
+ * FE_F64 and FE_F64X, whose gradients are evaluated in double-float). Sums over
  * the elements of a vertex, and the sum of L, are taken in a fixed order
  * (bit-identical run to run). The first backward call on a handle allocates its
  * scratch (d (d+1) values per element) and builds the vertex -> element lists,

@@ -34,7 +34,7 @@ class StiffnessValues(torch.autograd.Function):
     def backward(ctx, grad_vals):
         saved = ctx.saved_tensors
         w, q = (saved[0], saved[1]) if ctx.has_w else (None, saved[0])
-        T = torch.float64 if ctx.prec == fe.F64 else torch.float32
+        T = torch.float32 if ctx.prec == fe.F32 else torch.float64
         p = ctx.pattern
         dw = torch.empty(p.nme, dtype=T, device=q.device) if (ctx.has_w and ctx.needs_input_grad[0]) else None
         dq = torch.empty((p.d, p.nq), dtype=T, device=q.device) if ctx.needs_input_grad[1] else None
@@ -46,7 +46,7 @@ class StiffnessValues(torch.autograd.Function):
 class StiffnessBilinear(torch.autograd.Function):
     @staticmethod
     def forward(ctx, w, q, u, v, pattern, prec):
-        T = torch.float64 if prec == fe.F64 else torch.float32
+        T = torch.float32 if prec == fe.F32 else torch.float64
         wt, kind = _w_args(w)
         L = torch.empty(1, dtype=T, device=q.device)
         dw = torch.empty(pattern.nme, dtype=T, device=q.device) if w is not None else None

@@ -310,7 +310,7 @@ int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, i
                                const void* u, const void* v, void* L, void* dL_dw, void* dL_dq,
                                int32_t prec, void* stream) {
   if (!h || !q || !u || !v) return FE_ERR_ARG;
-  if (prec != FE_F64 && prec != FE_F32) return FE_ERR_ARG;
+  if (prec != FE_F64 && prec != FE_F32 && prec != FE_F64X) return FE_ERR_ARG;
   if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL)
     return FE_ERR_ARG;
@@ -321,7 +321,7 @@ int fe_assemble_stiff_backward(fe_pattern_h h, const double* q, const void* w, i
 int fe_assemble_stiff_vjp(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
                           const void* grad_vals, void* dL_dw, void* dL_dq, int32_t prec, void* stream) {
   if (!h || !q || !grad_vals) return FE_ERR_ARG;
-  if (prec != FE_F64 && prec != FE_F32) return FE_ERR_ARG;
+  if (prec != FE_F64 && prec != FE_F32 && prec != FE_F64X) return FE_ERR_ARG;
   if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL)
     return FE_ERR_ARG;

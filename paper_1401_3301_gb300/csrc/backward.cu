@@ -19,8 +19,10 @@
 //   for any loss of the assembled values).
 // Pass 1 (one thread per element) writes dL/dw and each corner's contribution to
 // dL/dq; pass 2 (one thread per vertex) sums the contributions of its incidences in
-// ascending element order, so the result is bit-identical run to run.
+// ascending element order, so the result is bit-identical run to run. The FE_F64X form
+// evaluates the same formulas in double-float on the FP32 pipe.
 #include "assemble_impl.cuh"
+#include "dfloat.cuh"
 #include "profile.cuh"
 
 namespace fe {
@@ -241,6 +243,184 @@ int launch(fe_pattern_s* h, BwdArgs& A, bool rank1, void* L, void* dLdq, cudaStr
   return FE_OK;
 }
 
+// ---------------------------------------------------------------- FE_F64X form
+// Pass 1 in double-float: edge vectors from an FP64 subtraction of the corner
+// coordinates, split into float pairs; cofactors, W, t and the corner contributions in
+// double-float; dL/dw and L in double, the corner contributions as float2 pairs.
+template <int D, bool RANK1>
+__global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
+  constexpr int NV = D + 1;
+  __shared__ double red[BWD_THREADS];
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double Le = 0.0;
+  if (e < A.nme) {
+    int32_t vv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) vv[a] = __ldg(A.me + (int64_t)a * A.nme + e);
+    double x[NV][D];
+    load_x64<D>(A.q, A.nq, vv, x);
+    df ed[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) ed[i][k] = df_split(x[i + 1][k] - x[0][k]);
+    df c[NV][D];
+    df det = x64_cofactors<D>(ed, &c[1]);
+    if (df_degenerate(det)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e]);
+      det = df{1.f, 0.f};
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      df s = c[1][k];
+#pragma unroll
+      for (int a = 2; a < NV; ++a) s = df_add(s, c[a][k]);
+      c[0][k] = df_neg(s);
+    }
+    df W[D][D];  // C^T (G^ + G^T) C
+    if constexpr (RANK1) {
+      const double* u = (const double*)A.u;
+      const double* v = (const double*)A.v;
+      df ub[D], vb[D];
+      {
+        const df u0 = df_split(u[vv[0]]), v0 = df_split(v[vv[0]]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          ub[k] = df_mul_full(u0, c[0][k]);
+          vb[k] = df_mul_full(v0, c[0][k]);
+        }
+      }
+#pragma unroll
+      for (int a = 1; a < NV; ++a) {
+        const df ua = df_split(u[vv[a]]), va = df_split(v[vv[a]]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          ub[k] = df_add(ub[k], df_mul_full(ua, c[a][k]));
+          vb[k] = df_add(vb[k], df_mul_full(va, c[a][k]));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int j = k; j < D; ++j) {
+          W[k][j] = df_add(df_mul_full(ub[k], vb[j]), df_mul_full(vb[k], ub[j]));
+          W[j][k] = W[k][j];
+        }
+    } else {
+      const double* gv = (const double*)A.grad_vals;
+      const int32_t* m = A.slot2nnz + e * NV * NV;
+      df Gs[NV][NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int b = a; b < NV; ++b) {
+          Gs[a][b] = df_add(df_split(gv[m[b * NV + a]]), df_split(gv[m[a * NV + b]]));
+          Gs[b][a] = Gs[a][b];
+        }
+      df Pc[NV][D];
+#pragma unroll
+      for (int xx = 0; xx < NV; ++xx)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          df p = df_mul_full(Gs[xx][0], c[0][j]);
+#pragma unroll
+          for (int y = 1; y < NV; ++y) p = df_add(p, df_mul_full(Gs[xx][y], c[y][j]));
+          Pc[xx][j] = p;
+        }
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int j = k; j < D; ++j) {
+          df w = df_mul_full(c[0][k], Pc[0][j]);
+#pragma unroll
+          for (int xx = 1; xx < NV; ++xx) w = df_add(w, df_mul_full(c[xx][k], Pc[xx][j]));
+          W[k][j] = w;
+          W[j][k] = w;
+        }
+    }
+    df t = W[0][0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) t = df_add(t, W[k][k]);
+    t = df{0.5f * t.hi, 0.5f * t.lo};  // exact
+    const df adet = det.hi < 0.f ? df_neg(det) : det;
+    const df inv = df_recip(df_mul_full(adet, df{(float)factorial(D), 0.f}));  // 1 / (d! |det|)
+    const bool has_w = A.w_kind != FE_COEF_NONE;
+    const df w = has_w ? df_split(elem_coef<double>(A.w, A.w_kind, A.order, e)) : df{1.f, 0.f};
+    const df dw = df_mul_full(t, inv);
+    if (A.dLdw) ((double*)A.dLdw)[A.dLdw_internal ? e : A.order[e]] = df_to_double(dw);
+    Le = df_to_double(df_mul_full(w, dw));
+    const df s = df_mul_full(df_mul_full(w, inv), df_recip(det));  // w / (d! det |det|)
+    df Z[D][D];  // s (t I - W)
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int j = 0; j < D; ++j) Z[k][j] = df_mul_full(s, k == j ? df_add(t, df_neg(W[k][j])) : df_neg(W[k][j]));
+    float2* out = (float2*)A.corner + e * NV * D;
+#pragma unroll
+    for (int cc = 0; cc < NV; ++cc)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        df o = df_mul_full(Z[k][0], c[cc][0]);
+#pragma unroll
+        for (int j = 1; j < D; ++j) o = df_add(o, df_mul_full(Z[k][j], c[cc][j]));
+        out[cc * D + k] = make_float2(o.hi, o.lo);
+      }
+  }
+  if (A.lpart) {  // fixed-order block reduction of L
+    red[threadIdx.x] = Le;
+    __syncthreads();
+    for (int o = BWD_THREADS / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) ((double*)A.lpart)[blockIdx.x] = red[0];
+  }
+}
+
+// pass 2 of the F64X form: double-float sums of the float2 corner contributions
+template <int D>
+__global__ void k_bwd_vertex_x(const int32_t* __restrict__ ptr, const int32_t* __restrict__ inc,
+                               int64_t nq, const float2* __restrict__ corner, double* __restrict__ dLdq) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= nq) return;
+  const int32_t s = ptr[v], t = ptr[v + 1];
+  if (s == t) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) dLdq[k * nq + v] = 0.0;
+    return;
+  }
+  AccX a[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) a[k] = AccX::from_partial(corner, (int64_t)inc[s] * D + k);
+  for (int32_t j = s + 1; j < t; ++j)
+#pragma unroll
+    for (int k = 0; k < D; ++k) a[k].add_partial(corner, (int64_t)inc[j] * D + k);
+#pragma unroll
+  for (int k = 0; k < D; ++k) dLdq[k * nq + v] = a[k].value();
+}
+
+template <int D>
+int launch_x(fe_pattern_s* h, BwdArgs& A, bool rank1, void* L, void* dLdq, cudaStream_t s) {
+  const int nblk = fe_grid(h->nme, BWD_THREADS);
+  FE_PROF_BEGIN(h, FE_K_BWD_CHUNK, s);
+  if (rank1) k_bwd_elem_x<D, true><<<nblk, BWD_THREADS, 0, s>>>(A);
+  else k_bwd_elem_x<D, false><<<nblk, BWD_THREADS, 0, s>>>(A);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_PROF_END(h, FE_K_BWD_CHUNK, s);
+  if (dLdq) {
+    FE_PROF_BEGIN(h, FE_K_BWD_REDUCE, s);
+    k_bwd_vertex_x<D><<<fe_grid(h->nq, 256), 256, 0, s>>>(h->vmap_ptr, h->vmap, h->nq, (const float2*)A.corner,
+                                                         (double*)dLdq);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_PROF_END(h, FE_K_BWD_REDUCE, s);
+  }
+  if (L && A.lpart) {
+    k_bwd_lsum<double><<<1, 256, 0, s>>>((const double*)A.lpart, nblk, (double*)L);
+    FE_CUDA_TRY(cudaGetLastError());
+  }
+  return FE_OK;
+}
+
 int prepare(fe_pattern_s* h, cudaStream_t s) {
   if (!h->vmap_ptr) FE_TRY(fe_build_vertex_map(h, s));
   if (!h->bwd_scratch) {
@@ -256,6 +436,7 @@ int run(fe_pattern_s* h, const double* q, const void* w, int w_kind, const void*
   BwdArgs A{h->me_int, h->nme, h->nq, q, nullptr, w, w_kind, h->order, u, v, grad_vals, h->slot2nnz,
             dLdw, w_kind == FE_COEF_P0_INTERNAL, h->bwd_scratch, L ? h->bwd_lpart : nullptr, h->status};
   const bool rank1 = grad_vals == nullptr;
+  if (prec == FE_F64X) return h->d == 3 ? launch_x<3>(h, A, rank1, L, dLdq, s) : launch_x<2>(h, A, rank1, L, dLdq, s);
   if (prec == FE_F32) {
     float4* qs = (float4*)h->qsplit;
     if (h->d == 3) k_split_q<3><<<fe_grid(h->nq, 256), 256, 0, s>>>(q, h->nq, qs);

@@ -80,6 +80,29 @@ __device__ __forceinline__ void x64_stage_vertex(const double* __restrict__ q, i
   }
 }
 
+// Cofactor vectors cf[i] = c_{i+1} (i < D) of B from its double-float edge vectors
+// e[i] = x^{i+1} - x^0, and the signed det B (returned).
+template <int D>
+__device__ __forceinline__ df x64_cofactors(const df e[D][D], df cf[D][D]) {
+  if constexpr (D == 3) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const df* u1 = e[(i + 1) % 3];
+      const df* u2 = e[(i + 2) % 3];
+      cf[i][0] = df_cross_term(u1[1], u2[2], u1[2], u2[1]);
+      cf[i][1] = df_cross_term(u1[2], u2[0], u1[0], u2[2]);
+      cf[i][2] = df_cross_term(u1[0], u2[1], u1[1], u2[0]);
+    }
+    return df_dot<3>(e[0], cf[0]);
+  } else {
+    cf[0][0] = e[1][1];
+    cf[0][1] = df_neg(e[1][0]);
+    cf[1][0] = df_neg(e[0][1]);
+    cf[1][1] = e[0][0];
+    return df_cross_term(e[0][0], e[1][1], e[0][1], e[1][0]);
+  }
+}
+
 // Double-float geometry of the element whose corners are the staged local vertices
 // lv: the cofactor vectors cf[i] = c_{i+1} (i < D) of B = [x^1 - x^0, ...] and the
 // signed det B (returned). Edge vectors are exact double-float differences.
@@ -108,23 +131,7 @@ __device__ __forceinline__ df x64_geometry(const unsigned char* sq, const int lv
       const df s = two_sum(xh[i + 1][k], -xh[0][k]);
       e[i][k] = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][k], xl[0][k])));
     }
-  if constexpr (D == 3) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const df* u1 = e[(i + 1) % 3];
-      const df* u2 = e[(i + 2) % 3];
-      cf[i][0] = df_cross_term(u1[1], u2[2], u1[2], u2[1]);
-      cf[i][1] = df_cross_term(u1[2], u2[0], u1[0], u2[2]);
-      cf[i][2] = df_cross_term(u1[0], u2[1], u1[1], u2[0]);
-    }
-    return df_dot<3>(e[0], cf[0]);
-  } else {
-    cf[0][0] = e[1][1];
-    cf[0][1] = df_neg(e[1][0]);
-    cf[1][0] = df_neg(e[0][1]);
-    cf[1][1] = e[0][0];
-    return df_cross_term(e[0][0], e[1][1], e[0][1], e[1][0]);
-  }
+  return x64_cofactors<D>(e, cf);
 }
 
 // det B is zero or not finite (tested on its float rounding)

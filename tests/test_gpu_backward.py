@@ -26,11 +26,11 @@ def setup(d, N, seed):
 
 
 @pytest.mark.parametrize("d,N", [(2, 17), (3, 7)])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_rank_one_backward_matches_oracle(d, N, prec):
     fe = fe_or_skip()
     import torch
-    T = torch.float64 if prec == 0 else torch.float32
+    T = torch.float32 if prec == 1 else torch.float64
     m, w, u, v = setup(d, N, 70 + N)
     Lr, dwr, dqr = oracle.stiff_loss(m.q, m.me, w, u, v)
     q, me = to_cuda(m.q), to_cuda(m.me)
@@ -41,7 +41,7 @@ def test_rank_one_backward_matches_oracle(d, N, prec):
     fe.fe_assemble_stiff_backward(p, q, to_cuda(w).to(T), fe.COEF_P0, to_cuda(u).to(T), to_cuda(v).to(T),
                                   L, dw, dq, prec=prec)
     assert p.status() == (0, -1)
-    tol = 1e-12 if prec == 0 else 2e-4
+    tol = 2e-4 if prec == 1 else 1e-12
     assert normwise(dw.cpu().numpy(), dwr) <= tol
     assert normwise(dq.cpu().numpy(), dqr) <= tol
     assert abs(L.item() - Lr) <= tol * np.abs(dwr * w).sum()
@@ -52,8 +52,10 @@ def test_rank_one_backward_matches_oracle(d, N, prec):
     assert bool((dq2 == dq).all())
 
 
-def test_gradients_against_central_differences_fp64():
+@pytest.mark.parametrize("form", ["f64", "f64x"])
+def test_gradients_against_central_differences_fp64(form):
     fe = fe_or_skip()
+    prec = fe.F64 if form == "f64" else fe.F64X
     import torch
     from paper_1401_3301_gb300.autograd import StiffnessBilinear
     m, w, u, v = setup(3, 8, 81)
@@ -62,12 +64,12 @@ def test_gradients_against_central_differences_fp64():
     wt, ut, vt = to_cuda(w), to_cuda(u), to_cuda(v)
     qg = q.clone().requires_grad_(True)
     wg = wt.clone().requires_grad_(True)
-    L = StiffnessBilinear.apply(wg, qg, ut, vt, p, fe.F64)
+    L = StiffnessBilinear.apply(wg, qg, ut, vt, p, prec)
     L.backward()
     gq, gw = qg.grad.cpu().numpy(), wg.grad.cpu().numpy()
 
     def loss(qq, ww):
-        return StiffnessBilinear.apply(ww, qq, ut, vt, p, fe.F64).item()
+        return StiffnessBilinear.apply(ww, qq, ut, vt, p, prec).item()
 
     rng = np.random.default_rng(3)
     h = 1e-6 / 8
@@ -92,12 +94,12 @@ def test_gradients_against_central_differences_fp64():
     assert normwise(an_w, fd_w) <= 1e-6
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_vjp_through_autograd_matches_rank_one(prec):
     fe = fe_or_skip()
     import torch
     from paper_1401_3301_gb300.autograd import StiffnessValues
-    T = torch.float64 if prec == 0 else torch.float32
+    T = torch.float32 if prec == 1 else torch.float64
     m, w, u, v = setup(3, 6, 91)
     q, me = to_cuda(m.q), to_cuda(m.me)
     p = fe.fe_pattern(q, me)
@@ -110,7 +112,7 @@ def test_vjp_through_autograd_matches_rank_one(prec):
     L = (ut[rows] * vals * vt[ci.long()]).sum()     # u^T S v from the CSR values
     L.backward()
     _, dwr, dqr = oracle.stiff_loss(m.q, m.me, w, u, v)
-    tol = 1e-12 if prec == 0 else 2e-4
+    tol = 2e-4 if prec == 1 else 1e-12
     assert normwise(wg.grad.cpu().numpy(), dwr) <= tol
     assert normwise(qg.grad.cpu().numpy(), dqr) <= tol
 
