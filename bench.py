@@ -495,7 +495,8 @@ def run_other(args):
         c1 = meshgen.general_coefficients(1, 3, m.nq)
         order = p.element_order().long().cpu().numpy()
         c0i = np.ascontiguousarray(c0[order])
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                              ("f64x", fe.F64X, torch.float64)):
             vals = torch.empty(p.nnz, dtype=T, device="cuda")
             res = {}
             for label, arr, kind in (("p0_internal", c0i, fe.COEF_P0_INTERNAL), ("p0", c0, fe.COEF_P0),

@@ -56,8 +56,8 @@ extern "C" {
 #define FE_F32 1 /* FP32 values; det B and |K| from FP64-accurate coordinates
                     differences in double-float arithmetic; compensated sums */
 #define FE_F64X 2 /* fe_assemble_mass, fe_assemble_wmass, fe_assemble_stiff (and its
-                    backward and VJP) and fe_assemble_elas on volume P1 patterns: FP64
-                    values of FP64-class accuracy
+                    backward and VJP), fe_assemble_elas and fe_assemble_general on
+                    volume P1 patterns: FP64 values of FP64-class accuracy
                     computed in double-float (pairs of floats, about 48 bits) on the
                     FP32 pipe; native FP64 only for coordinates relative to a vertex of
                     each element chunk and for converting sums to double. Coefficients
@@ -339,7 +339,8 @@ int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t l
  *                        formula (Eq. MagicFormula), as for Eq. MatElemMassWP1.
  * Records are read whole; a 16-byte aligned coef lets 3D records load as vectors.
  * Pattern: m = 1, built by fe_pattern or fe_batch_pattern (not a boundary pattern).
- * Every reassembly strategy; FE_F64X is not a form of this operator (FE_ERR_ARG).
+ * Every reassembly strategy for FE_F64 and FE_F32; FE_F64X (double coefficient records,
+ * double-float arithmetic) with the chunked strategy only (FE_ERR_ARG otherwise).
  * Asynchronous on `stream`; degenerate elements as for the other operators.
  */
 int fe_assemble_general(fe_pattern_h h, const double* q, const void* coef, int32_t coef_kind,

@@ -298,7 +298,7 @@ int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t l
 
 int fe_assemble_general(fe_pattern_h h, const double* q, const void* coef, int32_t coef_kind,
                         int32_t prec, void* vals, void* stream) {
-  FE_TRY(check_common(h, q, prec, vals));
+  FE_TRY(check_common(h, q, prec == FE_F64X ? FE_F64 : prec, vals));  // F64X: double data
   if (h->m != 1 || h->kdim != h->d || h->pk != 1 || !coef) return FE_ERR_ARG;
   if (coef_kind != FE_COEF_SCALAR && coef_kind != FE_COEF_P0 && coef_kind != FE_COEF_P0_INTERNAL &&
       coef_kind != FE_COEF_P1)

@@ -141,6 +141,37 @@ __device__ __forceinline__ bool df_degenerate(df det) {
   return ex == 0u || ex == 0xFFu;
 }
 
+// Double-float number with the arithmetic operators, so that value code written as a
+// template over the number type also runs in double-float. Built from a double only
+// for constants (the split is folded at compile time); data arrives through df_split.
+struct dfx {
+  float hi, lo;
+  dfx() = default;
+  __host__ __device__ constexpr dfx(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr explicit dfx(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __device__ __forceinline__ dfx(df v) : hi(v.hi), lo(v.lo) {}
+  __device__ __forceinline__ operator df() const { return df{hi, lo}; }
+};
+__device__ __forceinline__ dfx operator+(dfx a, dfx b) { return df_add(a, b); }
+__device__ __forceinline__ dfx operator-(dfx a, dfx b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfx operator-(dfx a) { return dfx(-a.hi, -a.lo); }
+__device__ __forceinline__ dfx operator*(dfx a, dfx b) { return df_mul_full(a, b); }
+__device__ __forceinline__ dfx& operator+=(dfx& a, dfx b) { return a = a + b; }
+__device__ __forceinline__ dfx& operator-=(dfx& a, dfx b) { return a = a - b; }
+__device__ __forceinline__ dfx& operator*=(dfx& a, dfx b) { return a = a * b; }
+__device__ __forceinline__ bool operator<(dfx a, dfx b) {  // normalised pairs
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ dfx tabs(dfx a) { return a.hi < 0.f ? -a : a; }
+template <>
+__device__ __forceinline__ dfx recip<dfx>(dfx x) { return df_recip(x); }
+
+// value of a number type from a double datum: identity, float rounding, or the split
+template <class T>
+__device__ __forceinline__ T from_double(double x) { return T(x); }
+template <>
+__device__ __forceinline__ dfx from_double<dfx>(double x) { return df_split(x); }
+
 // Double-float accumulator with the interface of the other forms' accumulators;
 // partial sums are float2 (hi, lo), final values double.
 struct AccX {

@@ -17,6 +17,7 @@
 // Reassembly follows the chunked plan of the symmetric operators; each edge carries two
 // sums, one per orientation, picked per incidence by the plan's orientation bit.
 #include "assemble_impl.cuh"
+#include "dfloat.cuh"
 #include "profile.cuh"
 
 namespace fe {
@@ -64,13 +65,29 @@ __device__ __forceinline__ void load_record(const T* __restrict__ rec, bool vec,
   for (int j = 0; j < GenCoef<D>::n; ++j) cf[j] = __ldg(rec + j);
 }
 
+// a coefficient of stored type R as the number type T of the arithmetic (the same type,
+// or a double split into a double-float pair)
+template <class T, class R>
+__device__ __forceinline__ T coef_value(R x) { return T(x); }
+template <>
+__device__ __forceinline__ dfx coef_value<dfx, double>(double x) { return df_split(x); }
+
+// one record of stored type R as numbers of type T
+template <int D, class T, class R>
+__device__ __forceinline__ void load_coef(const R* __restrict__ rec, bool vec, T cf[GenCoef<D>::n]) {
+  R r[GenCoef<D>::n];
+  load_record<D, R>(rec, vec, r);
+#pragma unroll
+  for (int j = 0; j < GenCoef<D>::n; ++j) cf[j] = coef_value<T, R>(r[j]);
+}
+
 // coefficient record of internal element e: the single record (scalar), or one per element
 // in input (P0) or internal (P0_INTERNAL) order
-template <int D, class T>
-__device__ __forceinline__ void general_coef(const T* __restrict__ coef, int kind, bool vec,
+template <int D, class T, class R = T>
+__device__ __forceinline__ void general_coef(const R* __restrict__ coef, int kind, bool vec,
                                              const int32_t* order, int64_t e, T cf[GenCoef<D>::n]) {
   const int64_t k = kind == FE_COEF_SCALAR ? 0 : (kind == FE_COEF_P0 ? (int64_t)order[e] : e);
-  load_record<D, T>(coef + k * GenCoef<D>::n, vec, cf);
+  load_coef<D, T, R>(coef + k * GenCoef<D>::n, vec, cf);
 }
 
 // P[a][b] = c_a . (A c_b) for all corners; the products are formed for corners 1..D and
@@ -169,8 +186,8 @@ __device__ __forceinline__ void general_values(const Geo<D, T>& g, const T cf[Ge
 // Local matrix with P1 coefficients: record vid[v] of coef belongs to corner v. The
 // corners are visited one at a time, keeping only the dot products the entries need:
 // Mb[a][v] = c_a . b(v), Nc[a][v] = c_a . c(v) (row 0 from sum_a c_a = 0).
-template <int D, class T>
-__device__ __forceinline__ void general_values_p1(const Geo<D, T>& g, const T* __restrict__ coef, bool vec,
+template <int D, class T, class R = T>
+__device__ __forceinline__ void general_values_p1(const Geo<D, T>& g, const R* __restrict__ coef, bool vec,
                                                   const int32_t vid[D + 1], GeneralVals<D, T>& out) {
   constexpr int NV = D + 1;
   T As[D * D], a0v[NV], Mb[NV][NV], Nc[NV][NV];
@@ -180,7 +197,7 @@ __device__ __forceinline__ void general_values_p1(const Geo<D, T>& g, const T* _
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     T cf[GenCoef<D>::n];
-    load_record<D, T>(coef + (int64_t)vid[v] * GenCoef<D>::n, vec, cf);
+    load_coef<D, T, R>(coef + (int64_t)vid[v] * GenCoef<D>::n, vec, cf);
 #pragma unroll
     for (int j = 0; j < D * D; ++j) As[j] += cf[j];
     const T* bb = cf + D * D;
@@ -265,6 +282,7 @@ struct GeneralArgs {
   int64_t npart;  // the second orientation of edge partial i is at npart + i
   fe_status_word* st;
   int64_t nnz;    // size of vals (bounds-checked builds)
+  const int32_t* me0;  // F64X form: corner 0 of each internal element (chunk reference vertex)
 };
 
 // One block per chunk, as the symmetric staged kernel: plan record by one bulk copy,
@@ -367,7 +385,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
 
 // Chunk-order sums of the partials of each shared vertex (one destination) and edge
 // (two: (i, j) from partials [s, t), (j, i) from [npart + s, npart + t)).
-template <class T>
+template <class T, class AccT = Acc<T>>
 __global__ void k_fixup_general(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
                                 int64_t nsh_v, int64_t nsh, int64_t npart,
                                 const void* __restrict__ partials, T* __restrict__ vals, int64_t nnz,
@@ -376,11 +394,11 @@ __global__ void k_fixup_general(const int32_t* __restrict__ sh_ptr, const int32_
   if (g >= nsh) return;
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
   if (!FE_FIXUP_VALID(s, t, npart, sh_dst[2 * g], sh_dst[2 * g + 1], g >= nsh_v, nnz, st, g)) return;
-  Acc<T> acc = Acc<T>::from_partial(partials, s);
+  AccT acc = AccT::from_partial(partials, s);
   for (int32_t i = s + 1; i < t; ++i) acc.add_partial(partials, i);
   vals[sh_dst[2 * g]] = acc.value();
   if (g >= nsh_v) {
-    Acc<T> acc2 = Acc<T>::from_partial(partials, npart + s);
+    AccT acc2 = AccT::from_partial(partials, npart + s);
     for (int32_t i = s + 1; i < t; ++i) acc2.add_partial(partials, npart + i);
     vals[sh_dst[2 * g + 1]] = acc2.value();
   }
@@ -448,7 +466,7 @@ int launch_general(fe_pattern_s* h, const ElemArgs& E, T* vals, cudaStream_t s) 
     if (L.total > 227u * 1024u) return FE_ERR_ARG;
     GeneralArgs G{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, E.q, E.w,
                   E.w_kind, vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status,
-                  h->nnz_s};
+                  h->nnz_s, h->me_int};
     auto kern = k_chunk_general<D, T, THREADS, P1>;
     static size_t configured = 0;
     FE_TRY(fe_smem_limit(kern, L.total, configured));
@@ -516,11 +534,162 @@ int launch_general_prec(fe_pattern_s* h, const double* q, const void* coef, int 
   return launch_general_dim<2, T>(h, E, vals, s);
 }
 
+// ---------------------------------------------------------------- FE_F64X form
+// The chunked kernel with double-float element values (general_values over dfx) from
+// coordinates relative to the chunk's reference vertex, double-float sums, double
+// values; coefficient records are double. Chunked strategy only.
+template <int D, int THREADS, bool P1>
+__global__ void __launch_bounds__(THREADS, P1 ? 2 : 3) k_chunk_general_x(GeneralArgs A, double* __restrict__ vals,
+                                                             float2* __restrict__ partials) {
+  constexpr int NV = D + 1, NP = Pairs<D>::n;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t c = blockIdx.x;
+  const int64_t e0 = c * A.chunk;
+  const int ne = (int)min((int64_t)A.chunk, A.nme - e0);
+  const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
+  const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
+  const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
+  const StagedSmem S = general_smem(D, 8, A.rec_max, A.max_lv, A.chunk);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
+  const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
+  const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
+  const uint16_t* lv_off = (const uint16_t*)(smem + R.lv_off);
+  const uint16_t* le_off = (const uint16_t*)(smem + R.le_off);
+  const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
+  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  float2* Kd = (float2*)(smem + S.kd);
+  float4* Ko = (float4*)(smem + S.ko);  // (E_ab, E_ba) of each element pair as two float pairs
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+
+  double xr[D];
+  {
+    const int64_t v0 = A.me0[e0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
+  }
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    x64_stage_vertex<D>(A.q, A.nq, lv_vid[u], xr, smem + S.q, u);
+    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
+  }
+  __syncthreads();
+
+  for (int el = threadIdx.x; el < ne; el += THREADS) {
+    int lv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
+    df cfv[D][D];
+    df det = x64_geometry<D>(smem + S.q, lv, cfv);
+    if (df_degenerate(det)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+      det = df{1.f, 0.f};
+    }
+    Geo<D, dfx> g;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int i = 0; i < D; ++i) g.c[a + 1][i] = cfv[a][i];
+    g.det = det;
+    GeneralVals<D, dfx> v;
+    if constexpr (P1) {
+      int32_t vid[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) vid[a] = lv_vid[lv[a]];
+      general_values_p1<D, dfx, double>(g, (const double*)A.coef, A.vec, vid, v);
+    } else {
+      dfx cf[GenCoef<D>::n];
+      general_coef<D, dfx, double>((const double*)A.coef, A.coef_kind, A.vec, A.order, e0 + el, cf);
+      general_values<D, dfx>(g, cf, v);
+    }
+#pragma unroll
+    for (int a = 0; a < NV; ++a) Kd[el * NV + a] = make_float2(v.diag[a].hi, v.diag[a].lo);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Ko[el * NP + p] = make_float4(v.lo[p].hi, v.lo[p].lo, v.hi[p].hi, v.hi[p].lo);
+  }
+  __syncthreads();
+
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int s = lv_off[u], t = lv_off[u + 1];
+    AccX acc = AccX::from_partial(Kd, inc_v[s]);
+    for (int j = s + 1; j < t; ++j) acc.add_partial(Kd, inc_v[j]);
+    const int32_t dst = lv_dst[u];
+    if (dst >= 0) vals[dst] = acc.value();
+    else acc.store_partial(partials, -1 - (int64_t)dst);
+  }
+  for (int u = threadIdx.x; u < nle; u += THREADS) {
+    const int s = le_off[u], t = le_off[u + 1];
+    const int x0 = inc_e[s];
+    const float4 v0 = Ko[x0 >> 1];
+    const df a0{v0.x, v0.y}, b0{v0.z, v0.w};
+    AccX lo((x0 & 1) ? b0 : a0), hi((x0 & 1) ? a0 : b0);
+    for (int j = s + 1; j < t; ++j) {
+      const int x = inc_e[j];
+      const float4 v = Ko[x >> 1];
+      const df a{v.x, v.y}, b{v.z, v.w};
+      lo.add((x & 1) ? b : a);
+      hi.add((x & 1) ? a : b);
+    }
+    const int32_t dst = le_dst[2 * u];
+    if (dst >= 0) {
+      vals[dst] = lo.value();
+      vals[le_dst[2 * u + 1]] = hi.value();
+    } else {
+      const int64_t pi = -1 - (int64_t)dst;
+      lo.store_partial(partials, pi);
+      hi.store_partial(partials, A.npart + pi);
+    }
+  }
+}
+
+template <int D, bool P1>
+int launch_general_x(fe_pattern_s* h, const double* q, const void* coef, int coef_kind, double* vals,
+                     cudaStream_t s) {
+  constexpr int THREADS = 256;
+  if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
+  const StagedSmem L = general_smem(D, 8, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->chunk);
+  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  const bool vec = ((uintptr_t)coef & 15u) == 0;
+  GeneralArgs G{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, coef, coef_kind,
+                vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status, h->nnz_s,
+                h->me_int};
+  auto kern = k_chunk_general_x<D, THREADS, P1>;
+  static size_t configured = 0;
+  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_PROF_BEGIN(h, FE_K_CHUNK, s);
+  kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(G, vals, (float2*)h->partials);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_PROF_END(h, FE_K_CHUNK, s);
+  const int64_t nsh = h->nsh_v + h->nsh_e;
+  if (nsh > 0) {
+    FE_PROF_BEGIN(h, FE_K_FIXUP, s);
+    k_fixup_general<double, AccX><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
+                                                                   h->npart, h->partials, vals, h->nnz_s,
+                                                                   h->status);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_PROF_END(h, FE_K_FIXUP, s);
+  }
+  return FE_OK;
+}
+
+int launch_general_f64x(fe_pattern_s* h, const double* q, const void* coef, int coef_kind, double* vals,
+                        cudaStream_t s) {
+  const bool p1 = coef_kind == FE_COEF_P1;
+  if (h->d == 3)
+    return p1 ? launch_general_x<3, true>(h, q, coef, coef_kind, vals, s)
+              : launch_general_x<3, false>(h, q, coef, coef_kind, vals, s);
+  return p1 ? launch_general_x<2, true>(h, q, coef, coef_kind, vals, s)
+            : launch_general_x<2, false>(h, q, coef, coef_kind, vals, s);
+}
+
 }  // namespace
 }  // namespace fe
 
 int fe_launch_general(fe_pattern_s* h, const double* q, const void* coef, int coef_kind, int prec,
                       void* vals, cudaStream_t s) {
+  if (prec == FE_F64X) return fe::launch_general_f64x(h, q, coef, coef_kind, (double*)vals, s);
   if (prec == FE_F64) return fe::launch_general_prec<double>(h, q, coef, coef_kind, (double*)vals, s);
   return fe::launch_general_prec<float>(h, q, coef, coef_kind, (float*)vals, s);
 }

@@ -60,6 +60,8 @@ def run(fe) -> dict:
     record("3d/general/p0", p, fe.fe_assemble_general(p, q3, coef, fe.COEF_P0))
     coef1 = cuda(meshgen.general_coefficients(5, 3, m3.nq))
     record("3d/general/p1", p, fe.fe_assemble_general(p, q3, coef1.float(), fe.COEF_P1, prec=fe.F32))
+    record("3d/general/p0/f64x", p, fe.fe_assemble_general(p, q3, coef, fe.COEF_P0, prec=fe.F64X))
+    record("3d/general/p1/f64x", p, fe.fe_assemble_general(p, q3, coef1, fe.COEF_P1, prec=fe.F64X))
     mk = meshgen.pk_mesh(3, 4, 2, seed=6)
     pk = fe.fe_pk_pattern(cuda(mk.q), cuda(mk.me), 2)
     record("3d/pk2_mass", pk, fe.fe_assemble_mass(pk, cuda(mk.q)))
@@ -92,6 +94,8 @@ def corrupted(fe) -> dict:
         "stiff/f32": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_stiff(p, q3, prec=fe.F32)),
         "stiff/f64x": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_stiff(p, q3, prec=fe.F64X)),
         "general": (lambda: fe.fe_pattern(q3, me3), lambda p: fe.fe_assemble_general(p, q3, coef, fe.COEF_P0)),
+        "general/f64x": (lambda: fe.fe_pattern(q3, me3),
+                         lambda p: fe.fe_assemble_general(p, q3, coef, fe.COEF_P0, prec=fe.F64X)),
         "elas": (lambda: fe.fe_pattern(q3, me3, m=3),
                  lambda p: fe.fe_assemble_elas(p, q3, lam, fe.COEF_SCALAR, lam, fe.COEF_SCALAR)),
         "elas/f64x": (lambda: fe.fe_pattern(q3, me3, m=3),

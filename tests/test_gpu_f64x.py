@@ -70,10 +70,7 @@ def test_f64x_reports_degenerate_elements_and_rejects_other_operators():
                 lambda: fe.fe_assemble_mass(p, to_cuda(qb), prec=fe.F64X)):
         run()
         assert p.status() == (3, min(bad))
-    # F64X is a form of mass, weighted mass, stiffness and elasticity on volume P1 patterns
-    coef = torch.ones((m.nme, 9), dtype=torch.float64, device="cuda")
-    with pytest.raises(fe.FEError):
-        fe.fe_assemble_general(p, to_cuda(m.q), coef, fe.COEF_P0, prec=fe.F64X)
+    # F64X is a form of the operators on volume P1 patterns only
     pb = fe.fe_boundary_pattern(to_cuda(m.q), to_cuda(meshgen.boundary_facets(m)))
     with pytest.raises(fe.FEError):
         fe.fe_assemble_mass(pb, to_cuda(m.q), prec=fe.F64X)

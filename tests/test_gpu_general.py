@@ -1,7 +1,7 @@
 """GPU parity of the general second-order operator (Eq. EDP) through the C ABI.
 
 The CUDA path is compared with the FP64 oracle on the same seeded inputs, entry by
-entry, within 1e-12 (FP64 form) or 1e-5 (FP32 form) of the normalised error. The
+entry, within 1e-12 (FP64 and F64X forms) or 1e-5 (FP32 form) of the normalised error. The
 operator is not symmetric, so each orientation of every edge is checked.
 """
 import numpy as np
@@ -13,7 +13,7 @@ from helpers import assert_pattern_equal, fe_or_skip, normalised_error, to_cuda
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5}
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
 
 
 def mesh(d, N, seed=0):
@@ -22,7 +22,7 @@ def mesh(d, N, seed=0):
 
 def dtype(prec):
     import torch
-    return torch.float64 if prec == 0 else torch.float32
+    return torch.float32 if prec == 1 else torch.float64
 
 
 @pytest.mark.parametrize("d,N", [(2, 37), (3, 9)])
@@ -145,8 +145,37 @@ def test_rejects_unsupported_calls():
     cf = to_cuda(meshgen.general_coefficients(9, 2, m.nme))
     with pytest.raises(fe.FEError):
         fe.fe_assemble_general(p, q, cf, fe.COEF_NONE)
-    with pytest.raises(fe.FEError):
-        fe.fe_assemble_general(p, q, cf, fe.COEF_P0, prec=fe.F64X)
     pv = fe.fe_pattern(q, me, m=2)
     with pytest.raises(fe.FEError):
         fe.fe_assemble_general(pv, q, cf, fe.COEF_P0)
+
+
+@pytest.mark.parametrize("d,N", [(2, 37), (3, 9), (3, 8)])
+@pytest.mark.parametrize("kind", ["p0", "p1", "scalar", "p0_internal"])
+def test_f64x_form(d, N, kind):
+    # the double-float form (chunked strategy only) to the FP64 gate, bit-identical reruns
+    fe = fe_or_skip()
+    m = mesh(d, N, seed=d * 10 + N + 3)
+    q, me = to_cuda(m.q), to_cuda(m.me)
+    p = fe.fe_pattern(q, me)
+    if kind == "p1":
+        cf = meshgen.general_coefficients(N + 60, d, m.nq)
+        ref, arg, k = oracle.assemble_general(m.q, m.me, cf, oracle.COEF_P1), cf, fe.COEF_P1
+    elif kind == "scalar":
+        cf = meshgen.general_coefficients(N + 61, d, 1)[0]
+        ref, arg, k = oracle.assemble_general(m.q, m.me, cf, oracle.COEF_SCALAR), cf.copy(), fe.COEF_SCALAR
+    else:
+        cf = meshgen.general_coefficients(N + 62, d, m.nme)
+        ref = oracle.assemble_general(m.q, m.me, cf, oracle.COEF_P0)
+        if kind == "p0":
+            arg, k = cf, fe.COEF_P0
+        else:
+            arg, k = cf[p.element_order().cpu().numpy()].copy(), fe.COEF_P0_INTERNAL
+    vals = fe.fe_assemble_general(p, q, to_cuda(arg), k, prec=fe.F64X)
+    assert p.status() == (0, -1)
+    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= TOL[2]
+    again = fe.fe_assemble_general(p, q, to_cuda(arg), k, prec=fe.F64X)
+    assert bool((again == vals).all())
+    p.set_strategy(fe.REASM_GATHER)
+    with pytest.raises(fe.FEError):
+        fe.fe_assemble_general(p, q, to_cuda(arg), k, prec=fe.F64X)
