@@ -36,7 +36,7 @@ UNIT = "Mtets/s"
 SM_COUNT = 152
 FP64_PIPE_PER_SM_CLK = 2.0      # nominal FP64 issue rate per SM per clock on GB300
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["elem.cuh", "plan.cuh", "tma.cuh", "assemble_impl.cuh", "assemble_scalar.inc",
+KERNEL_SOURCES = ["elem.cuh", "dfloat.cuh", "plan.cuh", "tma.cuh", "assemble_impl.cuh", "assemble_scalar.inc",
                   "assemble_f64.cu", "assemble_f32.cu", "assemble_f64x.cu"]
 
 
