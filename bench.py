@@ -558,7 +558,8 @@ def run_other(args):
             t0 = time.perf_counter()
             p = fe.fe_boundary_pattern(q, f)
             pms[label_n] = (time.perf_counter() - t0) * 1e3
-            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                                  ("f64x", fe.F64X, torch.float64)):
                 vals = torch.empty(p.nnz, dtype=T, device="cuda")
                 w = wv.to(T)
                 res = {}
@@ -571,7 +572,7 @@ def run_other(args):
                 out["forms"].setdefault(name, {"value": None, "numbering": {}})["numbering"][label_n] = res
             nnz = p.nnz
             del p
-        for name in ("f64", "f32"):
+        for name in ("f64", "f32", "f64x"):
             out["forms"][name]["value"] = out["forms"][name]["numbering"]["morton"]["mass"]["value"]
         out.update(metric="3D surface (facet) mass and P1-weighted mass, Mtris/s, fixed pattern (value: Morton "
                           "vertex numbering, mass)", unit="Mtris/s",

@@ -247,7 +247,7 @@ static int scalar_call(fe_pattern_h h, int kind, const double* q, const void* w,
     return fe_launch_pk_mass(h, q, prec, vals, (cudaStream_t)stream);
   }
   if (h && h->kdim != h->d) {  // boundary facets: mass and weighted mass only
-    FE_TRY(check_common(h, q, prec, vals));
+    FE_TRY(check_common(h, q, prec == FE_F64X ? FE_F64 : prec, vals));  // F64X: double data
     if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
     return fe_launch_boundary(h, kind, q, w, w_kind, prec, vals, (cudaStream_t)stream);
   }

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
 }
 
 // Sum of the chunk partials of each shared vertex / edge, in chunk order.
-template <class T>
+template <class T, class AccT = Acc<T>>
 __global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
                                int64_t nsh_v, int64_t nsh, const void* __restrict__ partials,
                                T* __restrict__ vals, int64_t nnz, int64_t npart, fe_status_word* st) {
@@ -407,11 +407,11 @@ __global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
   const int32_t d0 = sh_dst[2 * g], d1 = sh_dst[2 * g + 1];
   if (!FE_FIXUP_VALID(s, t, npart, d0, d1, g >= nsh_v, nnz, st, g)) return;
-  Acc<T> acc = Acc<T>::from_partial(partials, s);
+  AccT acc = AccT::from_partial(partials, s);
   int32_t i = s + 1;
   for (; i + 2 < t; i += 3) {  // three independent loads in flight, summed in order
-    Acc<T> b0 = Acc<T>::from_partial(partials, i), b1 = Acc<T>::from_partial(partials, i + 1),
-           b2 = Acc<T>::from_partial(partials, i + 2);
+    AccT b0 = AccT::from_partial(partials, i), b1 = AccT::from_partial(partials, i + 1),
+         b2 = AccT::from_partial(partials, i + 2);
     acc.add_acc(b0);
     acc.add_acc(b1);
     acc.add_acc(b2);

@@ -103,12 +103,11 @@ __device__ __forceinline__ df x64_cofactors(const df e[D][D], df cf[D][D]) {
   }
 }
 
-// Double-float geometry of the element whose corners are the staged local vertices
-// lv: the cofactor vectors cf[i] = c_{i+1} (i < D) of B = [x^1 - x^0, ...] and the
-// signed det B (returned). Edge vectors are exact double-float differences.
-template <int D>
-__device__ __forceinline__ df x64_geometry(const unsigned char* sq, const int lv[D + 1], df cf[D][D]) {
-  constexpr int NV = D + 1;
+// Edge vectors e[i] = x^{i+1} - x^0 (i < NE) of the corners lv[0..NE] staged by
+// x64_stage_vertex, as exact double-float differences of the split coordinates.
+template <int D, int NE>
+__device__ __forceinline__ void x64_edges(const unsigned char* sq, const int lv[NE + 1], df e[NE][D]) {
+  constexpr int NV = NE + 1;
   float xh[NV][D], xl[NV][D];
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
@@ -123,14 +122,29 @@ __device__ __forceinline__ df x64_geometry(const unsigned char* sq, const int lv
       xl[a][0] = h.z; xl[a][1] = h.w;
     }
   }
-  df e[D][D];
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+  for (int i = 0; i < NE; ++i)
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const df s = two_sum(xh[i + 1][k], -xh[0][k]);
       e[i][k] = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][k], xl[0][k])));
     }
+}
+
+// square root of a positive double-float: one Newton step from the float root
+__device__ __forceinline__ df df_sqrt(df a) {
+  const float s = __fsqrt_rn(a.hi);
+  const df r = df_add(a, df_neg(df_mul_full(df{s, 0.f}, df{s, 0.f})));  // a - s^2
+  return fast_two_sum(s, __fmul_rn(r.hi, __fdividef(0.5f, s)));
+}
+
+// Double-float geometry of the element whose corners are the staged local vertices
+// lv: the cofactor vectors cf[i] = c_{i+1} (i < D) of B = [x^1 - x^0, ...] and the
+// signed det B (returned). Edge vectors are exact double-float differences.
+template <int D>
+__device__ __forceinline__ df x64_geometry(const unsigned char* sq, const int lv[D + 1], df cf[D][D]) {
+  df e[D][D];
+  x64_edges<D, D>(sq, lv, e);
   return x64_cofactors<D>(e, cf);
 }
 
@@ -192,6 +206,7 @@ struct AccX {
     const float2 v = ((const float2*)p)[i];
     add(df{v.x, v.y});
   }
+  __device__ __forceinline__ void add_acc(const AccX& o) { add(o.s); }
 };
 
 }  // namespace fe

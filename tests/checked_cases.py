@@ -55,6 +55,7 @@ def run(fe) -> dict:
     pb = fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3)))
     record("3d/boundary_mass", pb, fe.fe_assemble_mass(pb, q3))
     record("3d/boundary_wmass", pb, fe.fe_assemble_wmass(pb, q3, w3.float(), fe.COEF_P1, prec=fe.F32))
+    record("3d/boundary_wmass/f64x", pb, fe.fe_assemble_wmass(pb, q3, w3, fe.COEF_P1, prec=fe.F64X))
     p = fe.fe_pattern(q3, me3)
     coef = cuda(meshgen.general_coefficients(4, 3, m3.nme))
     record("3d/general/p0", p, fe.fe_assemble_general(p, q3, coef, fe.COEF_P0))
@@ -103,6 +104,8 @@ def corrupted(fe) -> dict:
                                                     prec=fe.F64X)),
         "boundary": (lambda: fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3))),
                      lambda p: fe.fe_assemble_mass(p, q3)),
+        "boundary/f64x": (lambda: fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3))),
+                          lambda p: fe.fe_assemble_mass(p, q3, prec=fe.F64X)),
         "pk2": (lambda: fe.fe_pk_pattern(qk, cuda(mk.me), 2), lambda p: fe.fe_assemble_mass(p, qk)),
     }
     out = {}
