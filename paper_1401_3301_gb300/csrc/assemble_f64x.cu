@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __res
         }
         df ws = w[0];
 #pragma unroll
-        for (int a = 1; a < NV; ++a) ws = df_add(ws, w[a]);
+        for (int a = 1; a < NV; ++a) ws = df_add_fast(ws, w[a]);
 #pragma unroll
-        for (int a = 0; a < NV; ++a) dv[a] = df_twice(df_mul_full(base, df_add(ws, df_twice(w[a]))));
+        for (int a = 0; a < NV; ++a) dv[a] = df_twice(df_mul_full(base, df_add_fast(ws, df_twice(w[a]))));
 #pragma unroll
         for (int p = 0; p < NP; ++p)
-          ov[p] = df_mul_full(base, df_add(ws, df_add(w[Pairs<D>::a(p)], w[Pairs<D>::b(p)])));
+          ov[p] = df_mul_full(base, df_add_fast(ws, df_add_fast(w[Pairs<D>::a(p)], w[Pairs<D>::b(p)])));
       } else {
         constexpr DfConst kC = df_const(1.0 / factorial(D + 2));
         df m = df_mul_full(det, df_of(kC));
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __res
     df acc{v.x, v.y};
     for (int j = s + 1; j < t; ++j) {
       v = Kd[inc_v[j]];
-      acc = df_add(acc, df{v.x, v.y});
+      acc = df_add_fast(acc, df{v.x, v.y});
     }
     const int32_t dst = lv_dst[u];
     if (dst >= 0) vals[dst] = df_to_double(acc);
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __res
     df acc{v.x, v.y};
     for (int j = s + 1; j < t; ++j) {
       v = Ko[inc_e[j] >> 1];
-      acc = df_add(acc, df{v.x, v.y});
+      acc = df_add_fast(acc, df{v.x, v.y});
     }
     const int32_t dst = le_dst[2 * u];
     if (dst >= 0) {
@@ -209,7 +209,7 @@ __global__ void k_fixup_f64x(const int32_t* __restrict__ sh_ptr, const int32_t* 
   df acc{v.x, v.y};
   for (int32_t i = s + 1; i < t; ++i) {
     v = partials[i];
-    acc = df_add(acc, df{v.x, v.y});
+    acc = df_add_fast(acc, df{v.x, v.y});
   }
   const double val = df_to_double(acc);
   vals[sh_dst[2 * g]] = val;

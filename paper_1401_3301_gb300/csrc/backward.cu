@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
     for (int k = 0; k < D; ++k) {
       df s = c[1][k];
 #pragma unroll
-      for (int a = 2; a < NV; ++a) s = df_add(s, c[a][k]);
+      for (int a = 2; a < NV; ++a) s = df_add_fast(s, c[a][k]);
       c[0][k] = df_neg(s);
     }
     df W[D][D];  // C^T (G^ + G^T) C
@@ -295,15 +295,15 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
         const df ua = df_split(u[vv[a]]), va = df_split(v[vv[a]]);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          ub[k] = df_add(ub[k], df_mul_full(ua, c[a][k]));
-          vb[k] = df_add(vb[k], df_mul_full(va, c[a][k]));
+          ub[k] = df_add_fast(ub[k], df_mul_full(ua, c[a][k]));
+          vb[k] = df_add_fast(vb[k], df_mul_full(va, c[a][k]));
         }
       }
 #pragma unroll
       for (int k = 0; k < D; ++k)
 #pragma unroll
         for (int j = k; j < D; ++j) {
-          W[k][j] = df_add(df_mul_full(ub[k], vb[j]), df_mul_full(vb[k], ub[j]));
+          W[k][j] = df_add_fast(df_mul_full(ub[k], vb[j]), df_mul_full(vb[k], ub[j]));
           W[j][k] = W[k][j];
         }
     } else {
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
       for (int a = 0; a < NV; ++a)
 #pragma unroll
         for (int b = a; b < NV; ++b) {
-          Gs[a][b] = df_add(df_split(gv[m[b * NV + a]]), df_split(gv[m[a * NV + b]]));
+          Gs[a][b] = df_add_fast(df_split(gv[m[b * NV + a]]), df_split(gv[m[a * NV + b]]));
           Gs[b][a] = Gs[a][b];
         }
       df Pc[NV][D];
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
         for (int j = 0; j < D; ++j) {
           df p = df_mul_full(Gs[xx][0], c[0][j]);
 #pragma unroll
-          for (int y = 1; y < NV; ++y) p = df_add(p, df_mul_full(Gs[xx][y], c[y][j]));
+          for (int y = 1; y < NV; ++y) p = df_add_fast(p, df_mul_full(Gs[xx][y], c[y][j]));
           Pc[xx][j] = p;
         }
 #pragma unroll
@@ -333,14 +333,14 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
         for (int j = k; j < D; ++j) {
           df w = df_mul_full(c[0][k], Pc[0][j]);
 #pragma unroll
-          for (int xx = 1; xx < NV; ++xx) w = df_add(w, df_mul_full(c[xx][k], Pc[xx][j]));
+          for (int xx = 1; xx < NV; ++xx) w = df_add_fast(w, df_mul_full(c[xx][k], Pc[xx][j]));
           W[k][j] = w;
           W[j][k] = w;
         }
     }
     df t = W[0][0];
 #pragma unroll
-    for (int k = 1; k < D; ++k) t = df_add(t, W[k][k]);
+    for (int k = 1; k < D; ++k) t = df_add_fast(t, W[k][k]);
     t = df{0.5f * t.hi, 0.5f * t.lo};  // exact
     const df adet = det.hi < 0.f ? df_neg(det) : det;
     const df inv = df_recip(df_mul_full(adet, df{(float)factorial(D), 0.f}));  // 1 / (d! |det|)
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
 #pragma unroll
     for (int k = 0; k < D; ++k)
 #pragma unroll
-      for (int j = 0; j < D; ++j) Z[k][j] = df_mul_full(s, k == j ? df_add(t, df_neg(W[k][j])) : df_neg(W[k][j]));
+      for (int j = 0; j < D; ++j) Z[k][j] = df_mul_full(s, k == j ? df_add_fast(t, df_neg(W[k][j])) : df_neg(W[k][j]));
     float2* out = (float2*)A.corner + e * NV * D;
 #pragma unroll
     for (int cc = 0; cc < NV; ++cc)
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem_x(BwdArgs A) {
       for (int k = 0; k < D; ++k) {
         df o = df_mul_full(Z[k][0], c[cc][0]);
 #pragma unroll
-        for (int j = 1; j < D; ++j) o = df_add(o, df_mul_full(Z[k][j], c[cc][j]));
+        for (int j = 1; j < D; ++j) o = df_add_fast(o, df_mul_full(Z[k][j], c[cc][j]));
         out[cc * D + k] = make_float2(o.hi, o.lo);
       }
   }

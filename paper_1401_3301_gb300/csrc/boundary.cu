@@ -278,12 +278,12 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary_x(StagedArgs A, cons
       }
       df ws = w[0];
 #pragma unroll
-      for (int a = 1; a < NV; ++a) ws = df_add(ws, w[a]);
+      for (int a = 1; a < NV; ++a) ws = df_add_fast(ws, w[a]);
 #pragma unroll
-      for (int a = 0; a < NV; ++a) dv[a] = df_twice(df_mul_full(base, df_add(ws, df_twice(w[a]))));
+      for (int a = 0; a < NV; ++a) dv[a] = df_twice(df_mul_full(base, df_add_fast(ws, df_twice(w[a]))));
 #pragma unroll
       for (int p = 0; p < NP; ++p)
-        ov[p] = df_mul_full(base, df_add(ws, df_add(w[Pairs<KD>::a(p)], w[Pairs<KD>::b(p)])));
+        ov[p] = df_mul_full(base, df_add_fast(ws, df_add_fast(w[Pairs<KD>::a(p)], w[Pairs<KD>::b(p)])));
     } else {
       constexpr DfConst kC = df_const(1.0 / ((KD + 1) * (KD + 2)));
       df m = df_mul_full(meas, df_of(kC));

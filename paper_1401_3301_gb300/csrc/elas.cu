@@ -332,7 +332,7 @@ __device__ __forceinline__ df coef_sum_x(const void* c, int kind, const int32_t*
 #pragma unroll
     for (int a = 1; a <= D; ++a) {
       v = local_p1[lv[a]];
-      s = df_add(s, df{v.x, v.y});
+      s = df_add_fast(s, df{v.x, v.y});
     }
     return s;
   }
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __
     for (int i = 0; i < D; ++i) {
       df s = cf[0][i];
 #pragma unroll
-      for (int a = 1; a < D; ++a) s = df_add(s, cf[a][i]);
+      for (int a = 1; a < D; ++a) s = df_add_fast(s, cf[a][i]);
       Cg[(el * NV) * D + i] = make_float2(-s.hi, -s.lo);
 #pragma unroll
       for (int a = 1; a < NV; ++a) Cg[(el * NV + a) * D + i] = make_float2(cf[a - 1][i].hi, cf[a - 1][i].lo);
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __
 #pragma unroll
       for (int i = 0; i < D; ++i) x[i] = ld_df(Cg + inc * D + i);
       const df lp = ld_df(LM + 2 * el), mp = ld_df(LM + 2 * el + 1);
-      const df lm = df_add(lp, mp);
+      const df lm = df_add_fast(lp, mp);
       const df mxx = df_mul_full(mp, df_dot<D>(x, x));
 #pragma unroll
       for (int l = 0; l < D; ++l) {
