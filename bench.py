@@ -169,8 +169,14 @@ def run_reference(args):
     budget = 120.0 / max(1, args.steps + args.warmup)
     S = int(min(m.nme, max(10_000, rate * budget)))
     me = np.ascontiguousarray(m.me[:, :S])
-    for _ in range(args.warmup):
+    for k in range(args.warmup):
+        t0 = time.perf_counter()
         oracle.assemble(oracle.STIFF, m.q, me)
+        tw = time.perf_counter() - t0
+        if k == 0 and tw > 1.3 * budget and args.warmup > 1:
+            # the sort grows faster than linearly: shrink the sample to the step budget
+            S = int(max(10_000, S * budget / tw))
+            me = np.ascontiguousarray(m.me[:, :S])
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.assemble(oracle.STIFF, m.q, me)
