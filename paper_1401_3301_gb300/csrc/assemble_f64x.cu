@@ -198,24 +198,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __res
   }
 }
 
-__global__ void k_fixup_f64x(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
-                             int64_t nsh_v, int64_t nsh, const float2* __restrict__ partials,
-                             double* __restrict__ vals, int64_t nnz, int64_t npart, fe_status_word* st) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= nsh) return;
-  const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
-  if (!FE_FIXUP_VALID(s, t, npart, sh_dst[2 * g], sh_dst[2 * g + 1], g >= nsh_v, nnz, st, g)) return;
-  float2 v = partials[s];
-  df acc{v.x, v.y};
-  for (int32_t i = s + 1; i < t; ++i) {
-    v = partials[i];
-    acc = df_add_fast(acc, df{v.x, v.y});
-  }
-  const double val = df_to_double(acc);
-  vals[sh_dst[2 * g]] = val;
-  if (g >= nsh_v) vals[sh_dst[2 * g + 1]] = val;
-}
-
 template <int D, int KIND>
 int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
@@ -231,9 +213,9 @@ int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   const int64_t nsh = h->nsh_v + h->nsh_e;
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_FIXUP, s);
-    k_fixup_f64x<<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
-                                                   (const float2*)h->partials, vals, h->nnz_s, h->npart,
-                                                   h->status);
+    k_fixup_scalar<double, AccX><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
+                                                                  h->partials, vals, h->nnz_s, h->npart,
+                                                                  h->status);
     FE_CUDA_TRY(cudaGetLastError());
     FE_PROF_END(h, FE_K_FIXUP, s);
   }
