@@ -627,7 +627,8 @@ def run_other(args):
         m = meshgen.square_mesh(100, seed=0)
         q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
         p = fe.fe_pattern(q, me)
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                              ("f64x", fe.F64X, torch.float64)):
             v1 = torch.empty(p.nnz, dtype=T, device="cuda")
             v2 = torch.empty(p.nnz, dtype=T, device="cuda")
 
