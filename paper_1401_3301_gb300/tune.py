@@ -6,7 +6,8 @@ For one mesh and operator it times the chunked kernel over a grid of chunk sizes
 per block, and optionally the two-pass gather and atomic strategies, with CUDA events (median of `reps`
 calls after one warm-up). The winner is cached in a JSON file keyed by GPU name,
 dimension, dofs per vertex, operator, precision and the element count's power of
-two, so later meshes of the same class reuse it without timing.
+two, so later meshes of the same class reuse it without timing. With the environment
+variable FE_AUTOTUNE=0 nothing is timed and the library defaults are returned.
 """
 from __future__ import annotations
 
@@ -27,6 +28,15 @@ _FORM = {fe.F64: "f64", fe.F32: "f32", fe.F64X: "f64x"}
 
 def cache_path() -> str:
     return os.environ.get("FE_TUNE_CACHE", os.path.join(build_ext.BUILD, "tune.json"))
+
+
+def enabled() -> bool:
+    """False when FE_AUTOTUNE=0: autotune then returns the library defaults untimed."""
+    return os.environ.get("FE_AUTOTUNE", "1") != "0"
+
+
+# the configuration of a pattern built without flags (chunk 0: the library's default)
+DEFAULT = {"strategy": "chunked", "chunk": 0, "layout": 0, "threads": 256, "ms": None, "tried": 0}
 
 
 def _key(d, m, kind, prec, nme) -> str:
@@ -67,6 +77,8 @@ def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int =
              w_kind: int | None = None, reps: int = 10, chunks=CHUNKS, threads=THREADS, layouts=LAYOUTS,
              deterministic_only: bool = True, use_cache: bool = True) -> dict:
     """Best {strategy, chunk, layout, threads, ms} for this mesh class, from the cache or by timing."""
+    if not enabled():
+        return dict(DEFAULT)
     if w_kind is None:
         w_kind = fe.COEF_NONE if w is None else fe.COEF_P0
     d, nme = q.shape[0], me.shape[1]

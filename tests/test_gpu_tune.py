@@ -31,6 +31,23 @@ def test_autotune_caches_and_tuned_pattern_is_correct(tmp_path, monkeypatch):
     assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
 
 
+def test_autotune_disabled_returns_defaults_untimed(tmp_path, monkeypatch):
+    fe = fe_or_skip()
+    from paper_1401_3301_gb300 import tune
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("FE_TUNE_CACHE", str(cache))
+    monkeypatch.setenv("FE_AUTOTUNE", "0")
+    m = meshgen.kuhn_cube_mesh(6, seed=32)
+    q, me = to_cuda(m.q), to_cuda(m.me)
+    assert tune.autotune(q, me) == tune.DEFAULT
+    assert not cache.exists()  # nothing timed, nothing cached
+    p = tune.tuned_pattern(q, me)
+    assert p.plan_info()["chunk"] == fe.fe_pattern(q, me).plan_info()["chunk"]
+    ref = oracle.assemble(oracle.STIFF, m.q, m.me)
+    vals = fe.fe_assemble_stiff(p, q)
+    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
+
+
 @pytest.mark.parametrize("chunk,threads", [(256, 128), (768, 512), (1024, 256)])
 def test_chunk_and_thread_variants_agree_with_oracle(chunk, threads):
     fe = fe_or_skip()
