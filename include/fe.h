@@ -446,8 +446,9 @@ int fe_assemble_stiff_noalloc(fe_pattern_h h, const double* q, const void* w, in
  * with FE_CHECKED) says "bounds-checked" in it. */
 const char* fe_version(void);
 
-/* Text of the last CUDA runtime error seen by the library (host pointer, static;
- * empty if none). */
+/* Text of the last CUDA runtime error the library saw on the calling host thread
+ * (host pointer to a per-thread buffer, valid until that thread's next failing
+ * call; empty if none). */
 const char* fe_last_cuda_error(void);
 
 #ifdef __cplusplus

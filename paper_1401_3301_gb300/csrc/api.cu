@@ -4,6 +4,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "fe_internal.cuh"
 #include "plan.cuh"
@@ -28,7 +31,7 @@ int fe_launch_vjp(fe_pattern_s* h, const double* q, const void* w, int w_kind, c
                   void* dLdw, void* dLdq, int prec, cudaStream_t s);
 
 namespace {
-char g_last_cuda_error[256] = "";
+thread_local char g_last_cuda_error[256] = "";  // per calling host thread
 }
 
 int fe_cuda_fail(cudaError_t e) {
@@ -89,6 +92,24 @@ const char* fe_version(void) {
 }
 
 const char* fe_last_cuda_error(void) { return g_last_cuda_error; }
+}  // extern "C"
+
+int fe_smem_limit_raw(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> raised;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fe_cuda_fail(e);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = raised[{kernel, dev}];
+  if (bytes <= have) return FE_OK;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return fe_cuda_fail(e);
+  have = bytes;
+  return FE_OK;
+}
+
+extern "C" {
 
 int fe_pattern_csr(fe_pattern_h h, int64_t* n, int64_t* nnz, const int32_t** row_ptr,
                    const int32_t** col_idx) {

@@ -204,8 +204,7 @@ int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   const StagedSmem L = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   auto kern = k_chunk_f64x<D, KIND, THREADS>;
-  static size_t configured = 0;
-  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, (float2*)h->partials);
   FE_CUDA_TRY(cudaGetLastError());

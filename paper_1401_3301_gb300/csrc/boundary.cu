@@ -166,8 +166,7 @@ int launch(fe_pattern_s* h, const StagedArgs& A, T* vals, cudaStream_t s) {
   const StagedSmem L = boundary_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   auto kern = k_chunk_boundary<D, T, KIND, THREADS>;
-  static size_t configured = 0;
-  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, h->partials);
   FE_CUDA_TRY(cudaGetLastError());
@@ -329,8 +328,7 @@ int launch_x(fe_pattern_s* h, const StagedArgs& A, double* vals, cudaStream_t s)
   const StagedSmem L = boundary_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   auto kern = k_chunk_boundary_x<D, KIND, THREADS>;
-  static size_t configured = 0;
-  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, h->me_int, vals, (float2*)h->partials);
   FE_CUDA_TRY(cudaGetLastError());

@@ -296,8 +296,7 @@ int launch(fe_pattern_s* h, const ElasArgs& A, T* vals, cudaStream_t s) {
   const ElasSmem L = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   auto kern = k_chunk_elas<D, T, THREADS>;
-  static size_t configured = 0;
-  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_ELAS_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, h->partials);
   FE_CUDA_TRY(cudaGetLastError());
@@ -530,8 +529,7 @@ int launch_x(fe_pattern_s* h, const ElasArgs& A, double* vals, cudaStream_t s) {
   const ElasSmem L = elas_smem(D, 8, A.rec_max, A.max_lv, A.chunk);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   auto kern = k_chunk_elas_x<D, THREADS>;
-  static size_t configured = 0;
-  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_ELAS_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, (float2*)h->partials);
   FE_CUDA_TRY(cudaGetLastError());

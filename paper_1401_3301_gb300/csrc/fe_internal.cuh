@@ -126,15 +126,14 @@ int fe_pk_upload_table(fe_pattern_s* h, cudaStream_t s);
 int fe_ensure_scratch(fe_pattern_s* h, int strategy);
 int fe_build_vertex_map(fe_pattern_s* h, cudaStream_t s);
 
-// Raise a kernel's dynamic shared-memory limit once (not again inside a stream
-// capture): one static high-water mark per kernel instantiation.
+// Raise a kernel's dynamic shared-memory limit on the current device to at least
+// `bytes`: once per (kernel, device) and high-water mark, under a lock, so that the
+// attribute is not set again inside a stream capture (every kernel's first launch
+// happens outside one) and a process that drives several devices sets it on each.
+int fe_smem_limit_raw(const void* kernel, size_t bytes);
 template <class K>
-int fe_smem_limit(K kernel, size_t bytes, size_t& configured) {
-  if (bytes <= configured) return FE_OK;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return fe_cuda_fail(e);
-  configured = bytes;
-  return FE_OK;
+int fe_smem_limit(K kernel, size_t bytes) {
+  return fe_smem_limit_raw((const void*)kernel, bytes);
 }
 
 static inline int fe_grid(int64_t work, int per_block, int max_blocks = 1 << 30) {

@@ -468,8 +468,7 @@ int launch_general(fe_pattern_s* h, const ElemArgs& E, T* vals, cudaStream_t s) 
                   E.w_kind, vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status,
                   h->nnz_s, h->me_int};
     auto kern = k_chunk_general<D, T, THREADS, P1>;
-    static size_t configured = 0;
-    FE_TRY(fe_smem_limit(kern, L.total, configured));
+    FE_TRY(fe_smem_limit(kern, L.total));
     FE_PROF_BEGIN(h, FE_K_CHUNK, s);
     kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(G, vals, h->partials);
     FE_CUDA_TRY(cudaGetLastError());
@@ -656,8 +655,7 @@ int launch_general_x(fe_pattern_s* h, const double* q, const void* coef, int coe
                 vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status, h->nnz_s,
                 h->me_int};
   auto kern = k_chunk_general_x<D, THREADS, P1>;
-  static size_t configured = 0;
-  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(G, vals, (float2*)h->partials);
   FE_CUDA_TRY(cudaGetLastError());

@@ -695,8 +695,7 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     h->max_lv = mlv;
     const size_t fill_smem = 6u * (size_t)(mlv > mle ? mlv : mle) + 16u;
     const bool ordered = fill_smem <= 227u * 1024u && !(h->flags & FE_PATTERN_ENTITY_ORDER);
-    static size_t fill_configured = 0;
-    if (ordered) FE_TRY(fe_smem_limit(k_rec_fill, fill_smem, fill_configured));
+    if (ordered) FE_TRY(fe_smem_limit(k_rec_fill, fill_smem));
     k_rec_fill<<<(unsigned)h->nchunks, 256, ordered ? fill_smem : 0, s>>>(
         nme, C, nv, npair, h->m, ordered, h->ch_v_ptr, h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off,
         h->le_off, h->lv_vid, h->lv_dst, h->le_dst, h->lv_str, h->le_str, h->rec_off16, h->rec);

@@ -276,8 +276,7 @@ int launch_pk(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   PkArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, q, tab, h->order, h->ch_v_ptr, h->ch_e_ptr,
            h->rec, h->rec_off16, h->status, h->nnz_s, h->npart};
   auto kern = k_chunk_pk<D, K, T, THREADS>;
-  static size_t configured = 0;
-  FE_TRY(fe_smem_limit(kern, L.total, configured));
+  FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, h->partials);
   FE_CUDA_TRY(cudaGetLastError());
