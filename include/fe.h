@@ -8,7 +8,8 @@
  * and P_k mass (App. D), and assembles them into CSR form with duplicate
  * contributions summed, which is the `sparse(Ig, Jg, Kg, m, n)` constructor of
  * Section 3; also the gradients of L = u^T S(w) v (and general vector-Jacobian
- * products) of the stiffness matrix.
+ * products) of the stiffness matrix. Values come in three precision forms (FE_F64,
+ * FE_F32 and FE_F64X, defined below).
  *
  * Conventions shared by every call
  *   - Mesh (Section 2, Table 1): q is d x nq (coordinate c of vertex v at
