@@ -76,17 +76,26 @@ def test_degenerate_elements_are_reported_by_every_operator():
     p, pv = fe.fe_pattern(q, me), fe.fe_pattern(q, me, m=3)
     one = torch.ones(1, dtype=torch.float64, device="cuda")
     cf = to_cuda(meshgen.general_coefficients(1, 3, m.nme))
+    u = torch.ones(m.nq, dtype=torch.float64, device="cuda")
+    dq = torch.empty((3, m.nq), dtype=torch.float64, device="cuda")
     calls = [lambda: fe.fe_assemble_mass(p, q), lambda: fe.fe_assemble_stiff(p, q),
              lambda: fe.fe_assemble_stiff(p, q, prec=fe.F32), lambda: fe.fe_assemble_stiff(p, q, prec=fe.F64X),
-             lambda: fe.fe_assemble_general(p, q, cf, fe.COEF_P0)]
+             lambda: fe.fe_assemble_mass(p, q, prec=fe.F64X),
+             lambda: fe.fe_assemble_general(p, q, cf, fe.COEF_P0),
+             lambda: fe.fe_assemble_general(p, q, cf, fe.COEF_P0, prec=fe.F64X)]
+    for prec in (fe.F64, fe.F64X):
+        calls.append(lambda prec=prec: fe.fe_assemble_stiff_backward(p, q, None, fe.COEF_NONE, u, u, None, None, dq,
+                                                                     prec=prec))
     for call in calls:
         call()
         code, eid = p.status()
         assert code == 3 and 0 <= eid < m.nme
         assert a in m.me[:, eid] and b in m.me[:, eid]
-    fe.fe_assemble_elas(pv, q, one, fe.COEF_SCALAR, one, fe.COEF_SCALAR)
-    code, eid = pv.status()
-    assert code == 3 and a in m.me[:, eid] and b in m.me[:, eid]
+    for prec in (fe.F64, fe.F32, fe.F64X):
+        T = torch.float32 if prec == fe.F32 else torch.float64
+        fe.fe_assemble_elas(pv, q, one.to(T), fe.COEF_SCALAR, one.to(T), fe.COEF_SCALAR, prec=prec)
+        code, eid = pv.status()
+        assert code == 3 and a in m.me[:, eid] and b in m.me[:, eid], prec
     assert p.status() == (0, -1)  # read and cleared
 
 
@@ -116,3 +125,13 @@ def test_nan_coordinate_is_reported_as_degenerate():
         fe.fe_assemble_stiff(p, q, prec=prec)
         code, eid = p.status()
         assert code == 3 and v in m.me[:, eid], prec
+    # a facet mesh with a NaN on one of its vertices
+    fa = meshgen.boundary_facets(m)
+    qf = m.q.copy()
+    vf = fa[1, 5]
+    qf[0, vf] = np.nan
+    pb = fe.fe_boundary_pattern(to_cuda(qf), to_cuda(fa))
+    for prec in (fe.F64, fe.F32, fe.F64X):
+        fe.fe_assemble_mass(pb, to_cuda(qf), prec=prec)
+        code, eid = pb.status()
+        assert code == 3 and vf in fa[:, eid], prec
