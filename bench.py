@@ -531,12 +531,13 @@ def run_other(args):
             info = p.plan_info()
             res = {"N": N, "nodes": m.nq, "tets": m.nme, "nnz": p.nnz, "chunk": info["chunk"],
                    "pattern_build_ms": pms}
-            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32)):
+            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
+                                  ("f64x", fe.F64X, torch.float64)):
                 vals = torch.empty(p.nnz, dtype=T, device="cuda")
                 med, mean = _timed(lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals), K, W, flush)
                 p.check()
                 sT = 4 if prec == fe.F32 else 8
-                abytes = chunk_algorithmic_bytes(p, prec, info, points=(N + 1) ** 3)
+                abytes = chunk_algorithmic_bytes(p, fe.F64 if prec == fe.F64X else prec, info, points=(N + 1) ** 3)
                 res[name] = {"ms_per_step": mean, "ms_median": med, "Mnodes_per_s": m.nq / (mean * 1e-3) / 1e6,
                              "Mnnz_per_s": p.nnz / (mean * 1e-3) / 1e6,
                              "algorithmic_bytes": abytes, "GBps": abytes / (mean * 1e-3) / 1e9,

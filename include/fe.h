@@ -56,9 +56,9 @@ extern "C" {
 #define FE_F64 0 /* FP64 arithmetic, FP64 values */
 #define FE_F32 1 /* FP32 values; det B and |K| from FP64-accurate coordinates
                     differences in double-float arithmetic; compensated sums */
-#define FE_F64X 2 /* fe_assemble_mass, fe_assemble_wmass, fe_assemble_stiff (and its
-                    backward and VJP), fe_assemble_elas and fe_assemble_general on P1
-                    volume and facet patterns (not P_k): FP64 values of FP64-class accuracy
+#define FE_F64X 2 /* every operator (mass, weighted mass, stiffness with its backward
+                    and VJP, elasticity, general operator; volume, facet and P_k
+                    patterns), chunked strategy only: FP64 values of FP64-class accuracy
                     computed in double-float (pairs of floats, about 48 bits) on the
                     FP32 pipe; native FP64 only for coordinates relative to a vertex of
                     each element chunk and for converting sums to double. Coefficients

@@ -263,7 +263,7 @@ static int check_common(fe_pattern_h h, const double* q, int32_t prec, const voi
 static int scalar_call(fe_pattern_h h, int kind, const double* q, const void* w, int32_t w_kind,
                        int32_t prec, void* vals, void* stream) {
   if (h && h->pk > 1) {  // P_k patterns: the mass matrix only
-    FE_TRY(check_common(h, q, prec, vals));
+    FE_TRY(check_common(h, q, prec == FE_F64X ? FE_F64 : prec, vals));  // F64X: double values
     if (kind != 0) return FE_ERR_ARG;
     return fe_launch_pk_mass(h, q, prec, vals, (cudaStream_t)stream);
   }

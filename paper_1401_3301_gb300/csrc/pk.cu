@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "assemble_impl.cuh"
+#include "dfloat.cuh"
 #include "profile.cuh"
 
 namespace fe {
@@ -176,7 +177,9 @@ struct PkArgs {
 // node -> local node map into shared memory, |det B| per element from the FP64
 // coordinates of its d+1 vertices (its first d+1 nodes), then the fixed-order sums of
 // |det B| C over the incidences of each distinct node (diagonal) and node pair.
-template <int D, int K, class T, int THREADS>
+// X (FE_F64X form, T = double): |det B| and the table as double-float pairs in shared
+// memory, products and sums in double-float, double values, float2 partials.
+template <int D, int K, class T, int THREADS, bool X = false>
 __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ vals, void* __restrict__ partials) {
   constexpr int NV = binom(D + K, K), NP = NV * (NV - 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -200,9 +203,18 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
   uint16_t* lvid = (uint16_t*)(smem + S.lvid);
   T* Sc = (T*)(smem + S.sc);
   T* tab = (T*)(smem + S.tab);
+  float2* Sx = (float2*)(smem + S.sc);   // X: |det B| pairs
+  float2* tabx = (float2*)(smem + S.tab);  // X: table pairs
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
-  for (int i = threadIdx.x; i < NV + NP; i += THREADS) tab[i] = ((const T*)A.tab)[i];
+  for (int i = threadIdx.x; i < NV + NP; i += THREADS) {
+    if constexpr (X) {
+      const df v = df_split(((const double*)A.tab)[i]);
+      tabx[i] = make_float2(v.hi, v.lo);
+    } else {
+      tab[i] = ((const T*)A.tab)[i];
+    }
+  }
   for (int u = threadIdx.x; u < nlv; u += THREADS)
     for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   __syncthreads();
@@ -230,9 +242,47 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       det = 1.0;
     }
-    Sc[el] = (T)fabs(det);
+    if constexpr (X) {
+      const df v = df_split(fabs(det));
+      Sx[el] = make_float2(v.hi, v.lo);
+    } else {
+      Sc[el] = (T)fabs(det);
+    }
   }
   __syncthreads();
+
+  if constexpr (X) {
+    auto term = [&](int el, int k) {
+      const float2 a = Sx[el], b = tabx[k];
+      return df_mul_full(df{a.x, a.y}, df{b.x, b.y});
+    };
+    for (int u = threadIdx.x; u < nlv; u += THREADS) {
+      const int s = lv_off[u], t = lv_off[u + 1];
+      AccX acc(term(inc_v[s] / NV, inc_v[s] % NV));
+      for (int j = s + 1; j < t; ++j) acc.add(term(inc_v[j] / NV, inc_v[j] % NV));
+      const int32_t dst = lv_dst[u];
+      if (dst >= 0) vals[dst] = acc.value();
+      else acc.store_partial(partials, -1 - (int64_t)dst);
+    }
+    for (int u = threadIdx.x; u < nle; u += THREADS) {
+      const int s = le_off[u], t = le_off[u + 1];
+      const int i0 = inc_e[s] >> 1;
+      AccX acc(term(i0 / NP, NV + i0 % NP));
+      for (int j = s + 1; j < t; ++j) {
+        const int i = inc_e[j] >> 1;
+        acc.add(term(i / NP, NV + i % NP));
+      }
+      const int32_t dst = le_dst[2 * u];
+      if (dst >= 0) {
+        const double v = acc.value();
+        vals[dst] = v;
+        vals[le_dst[2 * u + 1]] = v;
+      } else {
+        acc.store_partial(partials, -1 - (int64_t)dst);
+      }
+    }
+    return;
+  }
 
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int s = lv_off[u], t = lv_off[u + 1];
@@ -265,7 +315,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
   }
 }
 
-template <int D, int K, class T>
+template <int D, int K, class T, bool X = false>
 int launch_pk(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   constexpr int NV = binom(D + K, K), NP = NV * (NV - 1) / 2;
   constexpr int THREADS = 256;
@@ -275,7 +325,7 @@ int launch_pk(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   const void* tab = sizeof(T) == 8 ? h->pk_tab : (const void*)((const double*)h->pk_tab + NV + NP);
   PkArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, q, tab, h->order, h->ch_v_ptr, h->ch_e_ptr,
            h->rec, h->rec_off16, h->status, h->nnz_s, h->npart};
-  auto kern = k_chunk_pk<D, K, T, THREADS>;
+  auto kern = k_chunk_pk<D, K, T, THREADS, X>;
   FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
   kern<<<(unsigned)h->nchunks, THREADS, L.total, s>>>(A, vals, h->partials);
@@ -284,27 +334,33 @@ int launch_pk(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   const int64_t nsh = h->nsh_v + h->nsh_e;
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_FIXUP, s);
-    k_fixup_scalar<T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->partials, vals, h->nnz_s, h->npart, h->status);
+    if constexpr (X)
+      k_fixup_scalar<double, AccX><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
+                                                                    h->partials, vals, h->nnz_s, h->npart,
+                                                                    h->status);
+    else
+      k_fixup_scalar<T><<<fe_grid(nsh, 256), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->partials,
+                                                          vals, h->nnz_s, h->npart, h->status);
     FE_CUDA_TRY(cudaGetLastError());
     FE_PROF_END(h, FE_K_FIXUP, s);
   }
   return FE_OK;
 }
 
-template <class T>
+template <class T, bool X = false>
 int launch_pk_prec(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   const int key = h->d * 10 + h->pk;
   switch (key) {
-    case 22: return launch_pk<2, 2, T>(h, q, vals, s);
-    case 23: return launch_pk<2, 3, T>(h, q, vals, s);
-    case 24: return launch_pk<2, 4, T>(h, q, vals, s);
-    case 25: return launch_pk<2, 5, T>(h, q, vals, s);
-    case 26: return launch_pk<2, 6, T>(h, q, vals, s);
-    case 32: return launch_pk<3, 2, T>(h, q, vals, s);
-    case 33: return launch_pk<3, 3, T>(h, q, vals, s);
-    case 34: return launch_pk<3, 4, T>(h, q, vals, s);
-    case 35: return launch_pk<3, 5, T>(h, q, vals, s);
-    case 36: return launch_pk<3, 6, T>(h, q, vals, s);
+    case 22: return launch_pk<2, 2, T, X>(h, q, vals, s);
+    case 23: return launch_pk<2, 3, T, X>(h, q, vals, s);
+    case 24: return launch_pk<2, 4, T, X>(h, q, vals, s);
+    case 25: return launch_pk<2, 5, T, X>(h, q, vals, s);
+    case 26: return launch_pk<2, 6, T, X>(h, q, vals, s);
+    case 32: return launch_pk<3, 2, T, X>(h, q, vals, s);
+    case 33: return launch_pk<3, 3, T, X>(h, q, vals, s);
+    case 34: return launch_pk<3, 4, T, X>(h, q, vals, s);
+    case 35: return launch_pk<3, 5, T, X>(h, q, vals, s);
+    case 36: return launch_pk<3, 6, T, X>(h, q, vals, s);
     default: return FE_ERR_ARG;
   }
 }
@@ -343,6 +399,7 @@ int fe_pk_upload_table(fe_pattern_s* h, cudaStream_t s) {
 
 int fe_launch_pk_mass(fe_pattern_s* h, const double* q, int prec, void* vals, cudaStream_t s) {
   if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
+  if (prec == FE_F64X) return fe::launch_pk_prec<double, true>(h, q, (double*)vals, s);
   if (prec == FE_F64) return fe::launch_pk_prec<double>(h, q, (double*)vals, s);
   return fe::launch_pk_prec<float>(h, q, (float*)vals, s);
 }

@@ -70,8 +70,7 @@ def test_f64x_reports_degenerate_elements_and_rejects_other_operators():
                 lambda: fe.fe_assemble_mass(p, to_cuda(qb), prec=fe.F64X)):
         run()
         assert p.status() == (3, min(bad))
-    # F64X is not a form of the P_k mass
-    pm = meshgen.pk_mesh(2, 3, 2, seed=1)
-    pk = fe.fe_pk_pattern(to_cuda(pm.q), to_cuda(pm.me), 2)
+    # F64X runs the chunked strategy only
+    p.set_strategy(fe.REASM_GATHER)
     with pytest.raises(fe.FEError):
-        fe.fe_assemble_mass(pk, to_cuda(pm.q), prec=fe.F64X)
+        fe.fe_assemble_stiff(p, to_cuda(m.q), prec=fe.F64X)
