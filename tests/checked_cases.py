@@ -66,6 +66,7 @@ def run(fe) -> dict:
     mk = meshgen.pk_mesh(3, 4, 2, seed=6)
     pk = fe.fe_pk_pattern(cuda(mk.q), cuda(mk.me), 2)
     record("3d/pk2_mass", pk, fe.fe_assemble_mass(pk, cuda(mk.q)))
+    record("3d/pk2_mass/f64x", pk, fe.fe_assemble_mass(pk, cuda(mk.q), prec=fe.F64X))
     return out
 
 
@@ -107,6 +108,8 @@ def corrupted(fe) -> dict:
         "boundary/f64x": (lambda: fe.fe_boundary_pattern(q3, cuda(meshgen.boundary_facets(m3))),
                           lambda p: fe.fe_assemble_mass(p, q3, prec=fe.F64X)),
         "pk2": (lambda: fe.fe_pk_pattern(qk, cuda(mk.me), 2), lambda p: fe.fe_assemble_mass(p, qk)),
+        "pk2/f64x": (lambda: fe.fe_pk_pattern(qk, cuda(mk.me), 2),
+                     lambda p: fe.fe_assemble_mass(p, qk, prec=fe.F64X)),
     }
     out = {}
     for name, (make, assemble) in cases.items():
