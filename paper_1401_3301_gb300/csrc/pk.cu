@@ -281,36 +281,35 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
         acc.store_partial(partials, -1 - (int64_t)dst);
       }
     }
-    return;
-  }
-
-  for (int u = threadIdx.x; u < nlv; u += THREADS) {
-    const int s = lv_off[u], t = lv_off[u + 1];
-    const int x0 = inc_v[s];
-    Acc<T> acc(Sc[x0 / NV] * tab[x0 % NV]);
-    for (int j = s + 1; j < t; ++j) {
-      const int x = inc_v[j];
-      acc.add(Sc[x / NV] * tab[x % NV]);
+  } else {
+    for (int u = threadIdx.x; u < nlv; u += THREADS) {
+      const int s = lv_off[u], t = lv_off[u + 1];
+      const int x0 = inc_v[s];
+      Acc<T> acc(Sc[x0 / NV] * tab[x0 % NV]);
+      for (int j = s + 1; j < t; ++j) {
+        const int x = inc_v[j];
+        acc.add(Sc[x / NV] * tab[x % NV]);
+      }
+      const int32_t dst = lv_dst[u];
+      if (dst >= 0) vals[dst] = acc.value();
+      else acc.store_partial(partials, -1 - (int64_t)dst);
     }
-    const int32_t dst = lv_dst[u];
-    if (dst >= 0) vals[dst] = acc.value();
-    else acc.store_partial(partials, -1 - (int64_t)dst);
-  }
-  for (int u = threadIdx.x; u < nle; u += THREADS) {
-    const int s = le_off[u], t = le_off[u + 1];
-    const int i0 = inc_e[s] >> 1;
-    Acc<T> acc(Sc[i0 / NP] * tab[NV + i0 % NP]);
-    for (int j = s + 1; j < t; ++j) {
-      const int i = inc_e[j] >> 1;
-      acc.add(Sc[i / NP] * tab[NV + i % NP]);
-    }
-    const int32_t dst = le_dst[2 * u];
-    if (dst >= 0) {
-      const T v = acc.value();
-      vals[dst] = v;
-      vals[le_dst[2 * u + 1]] = v;
-    } else {
-      acc.store_partial(partials, -1 - (int64_t)dst);
+    for (int u = threadIdx.x; u < nle; u += THREADS) {
+      const int s = le_off[u], t = le_off[u + 1];
+      const int i0 = inc_e[s] >> 1;
+      Acc<T> acc(Sc[i0 / NP] * tab[NV + i0 % NP]);
+      for (int j = s + 1; j < t; ++j) {
+        const int i = inc_e[j] >> 1;
+        acc.add(Sc[i / NP] * tab[NV + i % NP]);
+      }
+      const int32_t dst = le_dst[2 * u];
+      if (dst >= 0) {
+        const T v = acc.value();
+        vals[dst] = v;
+        vals[le_dst[2 * u + 1]] = v;
+      } else {
+        acc.store_partial(partials, -1 - (int64_t)dst);
+      }
     }
   }
 }
