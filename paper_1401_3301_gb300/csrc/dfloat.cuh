@@ -62,12 +62,28 @@ __device__ __forceinline__ df df_cross_term(df a, df b, df c, df d) {
   return fast_two_sum(h.hi, lo);
 }
 
+// x . y of double-float vectors: the products of the high parts exactly (FMA
+// two-products) and summed by two-sums, every low-order term (the product errors, the
+// cross terms with the low parts, the two-sum errors) in one float, one final
+// normalisation; the error is about 2^-46 of sum |x_k y_k|.
 template <int D>
 __device__ __forceinline__ df df_dot(const df* x, const df* y) {
-  df s = df_mul_full(x[0], y[0]);
+  float p[D], lo = 0.f;
 #pragma unroll
-  for (int k = 1; k < D; ++k) s = df_add_fast(s, df_mul_full(x[k], y[k]));
-  return s;
+  for (int k = 0; k < D; ++k) {
+    p[k] = __fmul_rn(x[k].hi, y[k].hi);
+    lo = __fadd_rn(lo, __fmaf_rn(x[k].hi, y[k].hi, -p[k]));
+    lo = __fmaf_rn(x[k].hi, y[k].lo, lo);
+    lo = __fmaf_rn(x[k].lo, y[k].hi, lo);
+  }
+  float s = p[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) {
+    const df t = two_sum(s, p[k]);
+    s = t.hi;
+    lo = __fadd_rn(lo, t.lo);
+  }
+  return fast_two_sum(s, lo);
 }
 
 // Coordinates of global vertex vid relative to the reference point xr (FP64
