@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -140,6 +141,21 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
+def host_cpu():
+    """The host's CPU (model name from /proc/cpuinfo where it gives one) and core count."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "logical_cpus": os.cpu_count()}
+
+
 def cpu_baseline(m, sample):
     import oracle
     oracle.build()
@@ -148,7 +164,7 @@ def cpu_baseline(m, sample):
     t0 = time.perf_counter()
     oracle.assemble(oracle.STIFF, m.q, me)
     dt = time.perf_counter() - t0
-    return {"value": S / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": S / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"first {S:,} of the {m.nme:,} randomly ordered tets of the same mesh "
                       f"(element loop + triplet sort-and-sum into CSR, FP64, one thread); {dt:.1f} s"}
 
@@ -187,7 +203,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {**workload_config(args.N), "strategy": "oracle",
                                             "parallelism": "host, one thread"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"each step: the first {S:,} of the {m.nme:,} randomly ordered "
                                        "tets (element loop + triplet sort-and-sum, FP64)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -29,6 +29,7 @@ def test_reference_arm_line():
     assert d["config"]["workload"].startswith("3D P1 stiffness")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host"]["logical_cpus"] >= 1 and cb["host"]["model"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
