@@ -142,18 +142,27 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
 def host_cpu():
-    """The host's CPU (model name from /proc/cpuinfo where it gives one) and core count."""
-    model = platform.machine()
+    """The host's CPU model (lscpu, else /proc/cpuinfo, else the machine type) and its
+    logical CPU count."""
+    model = None
     try:
-        with open("/proc/cpuinfo") as f:
-            for line in f:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware"):
-                    model = line.split(":", 1)[1].strip()
-                    break
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
-    return {"model": model, "logical_cpus": os.cpu_count()}
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.split(":")[0].strip().lower() in ("model name", "cpu model", "hardware"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model or platform.machine(), "logical_cpus": os.cpu_count()}
 
 
 def cpu_baseline(m, sample):
