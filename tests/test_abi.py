@@ -37,3 +37,17 @@ def test_library_exports_every_declared_symbol():
     assert b"sm_103a" in lib.fe_version()
     syms = subprocess.run(["nm", "-D", path], capture_output=True, text=True).stdout
     assert "orc_" not in syms  # the oracle is test infrastructure, never part of the library
+
+
+def test_checked_library_exports_the_same_boundary():
+    if not any(os.path.exists(os.path.join(p, "nvcc")) for p in os.environ.get("PATH", "").split(":")) \
+            and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit to build the library")
+    from paper_1401_3301_gb300 import build_ext
+    path = build_ext.build(checked=True)
+    assert path == build_ext.LIB_CHECKED
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.fe_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" in lib.fe_version()

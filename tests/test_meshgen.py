@@ -46,3 +46,26 @@ def test_streams_are_independent_and_uniform():
     assert sorted(p.tolist()) == list(range(1000))
     s = meshgen.batch_sizes(0, 256, 16, 512)
     assert s.min() >= 16 and s.max() <= 512
+
+
+def test_recipe_sizes_of_the_other_workloads():
+    # P_k lattice meshes: (kN + 1)^d nodes, the coarse element count, ndfe rows
+    for d, N, k in ((2, 5, 3), (3, 3, 2)):
+        m = meshgen.pk_mesh(d, N, k, seed=1)
+        ndfe = {(2, 3): 10, (3, 2): 10}[(d, k)]
+        assert m.nq == (k * N + 1) ** d and m.me.shape == (ndfe, (2 if d == 2 else 6) * N ** d)
+        assert m.me.min() == 0 and m.me.max() == m.nq - 1
+    # the facet workload: 2 N^2 triangles in 3D on (N+1)^2 vertices
+    s = meshgen.surface_mesh(20, seed=0)
+    assert s.q.shape == (3, 21 ** 2) and s.me.shape == (3, 2 * 20 ** 2)
+    # boundary of the Kuhn cube: 2 N^2 triangles on each of the 6 faces
+    k = meshgen.kuhn_cube_mesh(5, seed=2)
+    assert meshgen.boundary_facets(k).shape == (3, 12 * 5 ** 2)
+    # general-operator records: d*d + 2d + 1 values; A = exp(g0) I + 0.3 N is not symmetric
+    # and its symmetric part is positive definite for most records; a0 = exp(g1) > 0
+    c = meshgen.general_coefficients(3, 3, 2000)
+    assert c.shape == (2000, 16)
+    A = c[:, :9].reshape(-1, 3, 3)
+    assert np.abs(A - A.transpose(0, 2, 1)).max(axis=(1, 2)).min() > 0
+    sym = 0.5 * (A + A.transpose(0, 2, 1))
+    assert (np.linalg.eigvalsh(sym).min(axis=1) > 0).mean() > 0.7 and (c[:, 15] > 0).all()
