@@ -244,7 +244,8 @@ def element_weights(seed: int, nme: int) -> np.ndarray:
 
 def general_coefficients(seed: int, d: int, n: int) -> np.ndarray:
     """n records (rows) of convection-diffusion-reaction coefficients, (n, d*d + 2d + 1):
-    A = exp(g0) I + 0.3 N (a non-symmetric, diffusion-dominated tensor, row-major), b and c
+    A = exp(g0) I + 0.3 N (a non-symmetric tensor, row-major; its symmetric part is positive
+    definite for most records), b and c
     with N(0, 1) entries, a0 = exp(g1); g0, g1 and the entries of N iid N(0, 1)."""
     nc = d * d + 2 * d + 1
     z = normal(stream_key(seed, GEN_COEF), (nc + 2) * n).reshape(n, nc + 2)
