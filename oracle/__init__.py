@@ -4,7 +4,10 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()`` 
 the CPU-baseline leg of ``bench.py``. The library's GPU path never imports it.
 
 ``build()`` compiles fe_oracle.c with the host C compiler into ``oracle/_build``.
-Every function here only converts arguments; the arithmetic is in fe_oracle.c.
+The assembly arithmetic is in fe_oracle.c; the functions here convert arguments,
+except ``pk_multi_indices``, ``_pk_basis`` and ``pk_mass_table``, which compute the
+P_k node order and the exact-rational P_k mass table (App. D) in Python with
+Fractions before the C assembly uses it.
 """
 from __future__ import annotations
 
@@ -48,12 +51,13 @@ def _load():
         lib.orc_simplex.argtypes = [I32, P, P, P, P]
         lib.orc_element.argtypes = [I32, I32, P, P, P, P, P]
         lib.orc_assemble.argtypes = [I32, I32, I64, I64, P, P, I32, P, I32, P,
-                                     P, P, P, P, P, P, P]
+                                     P, P, P, P, P, P, P, P]
         lib.orc_stiff_loss.argtypes = [I32, I64, I64, P, P, P, P, P, P, P, P, P]
         lib.orc_facet.argtypes = [I32, P, P]
-        lib.orc_assemble_boundary.argtypes = [I32, I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P]
-        lib.orc_assemble_general.argtypes = [I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P]
-        lib.orc_assemble_table.argtypes = [I32, I64, I64, I32, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_assemble_boundary.argtypes = [I32, I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P, P]
+        lib.orc_assemble_general.argtypes = [I32, I64, I64, P, P, I32, P, P, P, P, P, P, P, P, P]
+        lib.orc_assemble_table.argtypes = [I32, I64, I64, I32, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_pattern.argtypes = [I32, I32, I64, I64, P, P, P, P, P]
         lib.orc_free.argtypes = [P]
         _lib = lib
     return _lib
@@ -102,6 +106,24 @@ def element(kind: int, X: np.ndarray, cv1=None, cv2=None):
     return E.reshape(nl, nl).T.copy(), S.reshape(nl, nl).T.copy()
 
 
+def _csr_result(lib, n, nnz, rp, ci, va, sc, sa) -> dict:
+    """The malloc'ed CSR arrays of an oracle assembly as numpy arrays (freed after copying)."""
+
+    def take(p, ctype, count, dtype):
+        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
+        out = np.array(arr, dtype=dtype)
+        lib.orc_free(p)
+        return out
+
+    N, NNZ = n.value, nnz.value
+    return dict(n=N, nnz=NNZ,
+                row_ptr=take(rp, C.c_int64, N + 1, np.int64),
+                col_idx=take(ci, C.c_int32, NNZ, np.int32),
+                val=take(va, C.c_double, NNZ, np.float64),
+                scale=take(sc, C.c_double, NNZ, np.float64),
+                abssum=take(sa, C.c_double, NNZ, np.float64))
+
+
 def _coef(c):
     """(kind, array) for a coefficient given as None, a number, or a per-element/vertex array."""
     if c is None:
@@ -115,7 +137,9 @@ def _coef(c):
 def assemble(kind: int, q: np.ndarray, me: np.ndarray, c1=None, c2=None) -> dict:
     """Assemble the global matrix. c1/c2: None, a number, or (COEF_P0|COEF_P1, array).
 
-    Returns dict(n, nnz, row_ptr int64, col_idx int32, val float64, scale float64).
+    Returns dict(n, nnz, row_ptr int64, col_idx int32, val float64, scale float64,
+    abssum float64): per entry the sum, the sum of its contributions' normwise condition
+    scales, and the sum of their absolute values.
     """
     q = np.ascontiguousarray(q, dtype=np.float64)
     me = np.ascontiguousarray(me, dtype=np.int32)
@@ -124,26 +148,35 @@ def assemble(kind: int, q: np.ndarray, me: np.ndarray, c1=None, c2=None) -> dict
     k1, a1 = _coef(c1)
     k2, a2 = _coef(c2)
     n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
-    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    rp, ci, va, sc, sa = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
     lib = _load()
     rc = lib.orc_assemble(kind, d, nq, nme, _ptr(q), _ptr(me), k1, _ptr(a1), k2, _ptr(a2),
                           C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
-                          C.byref(sc), C.byref(bad))
+                          C.byref(sc), C.byref(sa), C.byref(bad))
     if rc:
         raise OracleError(rc, bad.value)
 
-    def take(p, ctype, count, dtype):
-        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
-        out = np.array(arr, dtype=dtype)
-        lib.orc_free(p)
-        return out
+    return _csr_result(lib, n, nnz, rp, ci, va, sc, sa)
 
-    N, NNZ = n.value, nnz.value
-    return dict(n=N, nnz=NNZ,
-                row_ptr=take(rp, C.c_int64, N + 1, np.int64),
-                col_idx=take(ci, C.c_int32, NNZ, np.int32),
-                val=take(va, C.c_double, NNZ, np.float64),
-                scale=take(sc, C.c_double, NNZ, np.float64))
+
+def pattern(me: np.ndarray, nq: int, m: int = 1) -> tuple:
+    """(row_ptr int64, col_idx int32) of the assembled matrix's nonzero pattern alone,
+    with m dofs per vertex, from the connectivity me ((d+1) x nme)."""
+    me = np.ascontiguousarray(me, dtype=np.int32)
+    d = me.shape[0] - 1
+    nnz, bad = C.c_int64(), C.c_int64()
+    rp, ci = C.c_void_p(), C.c_void_p()
+    lib = _load()
+    rc = lib.orc_pattern(d, m, nq, me.shape[1], _ptr(me), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+    n, NNZ = m * nq, nnz.value
+    row_ptr = np.array(np.ctypeslib.as_array(C.cast(rp, C.POINTER(C.c_int64)), shape=(n + 1,)), dtype=np.int64)
+    col_idx = np.array(np.ctypeslib.as_array(C.cast(ci, C.POINTER(C.c_int32)), shape=(max(NNZ, 1),))[:NNZ],
+                       dtype=np.int32)
+    lib.orc_free(rp)
+    lib.orc_free(ci)
+    return row_ptr, col_idx
 
 
 def facet_measure(X: np.ndarray) -> float:
@@ -163,24 +196,15 @@ def assemble_boundary(kind: int, q: np.ndarray, facets: np.ndarray, c1=None) -> 
     d, nq = q.shape
     k1, a1 = _coef(c1)
     n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
-    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    rp, ci, va, sc, sa = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
     lib = _load()
     rc = lib.orc_assemble_boundary(kind, d, nq, fa.shape[1], _ptr(q), _ptr(fa), k1, _ptr(a1),
                                    C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
-                                   C.byref(sc), C.byref(bad))
+                                   C.byref(sc), C.byref(sa), C.byref(bad))
     if rc:
         raise OracleError(rc, bad.value)
 
-    def take(p, ctype, count, dtype):
-        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
-        out = np.array(arr, dtype=dtype)
-        lib.orc_free(p)
-        return out
-
-    N, NNZ = n.value, nnz.value
-    return dict(n=N, nnz=NNZ, row_ptr=take(rp, C.c_int64, N + 1, np.int64),
-                col_idx=take(ci, C.c_int32, NNZ, np.int32), val=take(va, C.c_double, NNZ, np.float64),
-                scale=take(sc, C.c_double, NNZ, np.float64))
+    return _csr_result(lib, n, nnz, rp, ci, va, sc, sa)
 
 
 def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, kind: int) -> dict:
@@ -192,24 +216,15 @@ def assemble_general(q: np.ndarray, me: np.ndarray, coef: np.ndarray, kind: int)
     cf = np.ascontiguousarray(coef, dtype=np.float64)
     d, nq = q.shape
     n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
-    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    rp, ci, va, sc, sa = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
     lib = _load()
     rc = lib.orc_assemble_general(d, nq, me.shape[1], _ptr(q), _ptr(me), kind,
                                   _ptr(cf), C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va),
-                                  C.byref(sc), C.byref(bad))
+                                  C.byref(sc), C.byref(sa), C.byref(bad))
     if rc:
         raise OracleError(rc, bad.value)
 
-    def take(p, ctype, count, dtype):
-        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
-        out = np.array(arr, dtype=dtype)
-        lib.orc_free(p)
-        return out
-
-    N, NNZ = n.value, nnz.value
-    return dict(n=N, nnz=NNZ, row_ptr=take(rp, C.c_int64, N + 1, np.int64),
-                col_idx=take(ci, C.c_int32, NNZ, np.int32), val=take(va, C.c_double, NNZ, np.float64),
-                scale=take(sc, C.c_double, NNZ, np.float64))
+    return _csr_result(lib, n, nnz, rp, ci, va, sc, sa)
 
 
 def pk_multi_indices(d: int, k: int) -> list:
@@ -275,24 +290,15 @@ def assemble_pk_mass(q: np.ndarray, me: np.ndarray, k: int) -> dict:
     assert me.shape[0] == ndfe
     flat = np.ascontiguousarray(tab.T)  # flat[b * ndfe + a] = entry (a, b)
     n, nnz, bad = C.c_int64(), C.c_int64(), C.c_int64()
-    rp, ci, va, sc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    rp, ci, va, sc, sa = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
     lib = _load()
     rc = lib.orc_assemble_table(d, nq, me.shape[1], ndfe, _ptr(q), _ptr(me), _ptr(flat), C.byref(n),
                                 C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(va), C.byref(sc),
-                                C.byref(bad))
+                                C.byref(sa), C.byref(bad))
     if rc:
         raise OracleError(rc, bad.value)
 
-    def take(p, ctype, count, dtype):
-        arr = np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(max(count, 1),))[:count]
-        out = np.array(arr, dtype=dtype)
-        lib.orc_free(p)
-        return out
-
-    N, NNZ = n.value, nnz.value
-    return dict(n=N, nnz=NNZ, row_ptr=take(rp, C.c_int64, N + 1, np.int64),
-                col_idx=take(ci, C.c_int32, NNZ, np.int32), val=take(va, C.c_double, NNZ, np.float64),
-                scale=take(sc, C.c_double, NNZ, np.float64))
+    return _csr_result(lib, n, nnz, rp, ci, va, sc, sa)
 
 
 def stiff_loss(q, me, w, u, v, grads: bool = True):

@@ -270,9 +270,11 @@ static int cmp_triplet(const void* pa, const void* pb) {
 }
 
 /* Sort the triplets by (row, column, element, slot) and sum equal (row, column)
- * into a CSR matrix of order n (the `sparse` constructor of Section 3). */
+ * into a CSR matrix of order n (the `sparse` constructor of Section 3). Beside each
+ * sum: the sum of the contributions' condition scales (scale) and the sum of their
+ * absolute values (abssum), the scale of a cancelling sum's rounding error. */
 static int triplets_to_csr(triplet* t, int64_t nt, int64_t n, int64_t** row_ptr, int32_t** col_idx,
-                           double** val, double** scale, int64_t* nnz_out) {
+                           double** val, double** scale, double** abssum, int64_t* nnz_out) {
   qsort(t, (size_t)nt, sizeof(triplet), cmp_triplet);
   int64_t nnz = 0;
   for (int64_t i = 0; i < nt; ++i)
@@ -281,7 +283,8 @@ static int triplets_to_csr(triplet* t, int64_t nt, int64_t n, int64_t** row_ptr,
   *col_idx = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
   *val = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
   *scale = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
-  if (!*row_ptr || !*col_idx || !*val || !*scale) return ORC_ERR_NOMEM;
+  *abssum = (double*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+  if (!*row_ptr || !*col_idx || !*val || !*scale || !*abssum) return ORC_ERR_NOMEM;
   int64_t j = -1;
   for (int64_t i = 0; i < nt; ++i) {
     if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) {
@@ -289,10 +292,12 @@ static int triplets_to_csr(triplet* t, int64_t nt, int64_t n, int64_t** row_ptr,
       (*col_idx)[j] = (int32_t)t[i].col;
       (*val)[j] = 0.0;
       (*scale)[j] = 0.0;
+      (*abssum)[j] = 0.0;
       (*row_ptr)[t[i].row + 1] += 1;
     }
     (*val)[j] += t[i].v;
     (*scale)[j] += t[i].s;
+    (*abssum)[j] += fabs(t[i].v);
   }
   for (int64_t r = 0; r < n; ++r) (*row_ptr)[r + 1] += (*row_ptr)[r];
   *nnz_out = nnz;
@@ -304,13 +309,14 @@ static int triplets_to_csr(triplet* t, int64_t nt, int64_t n, int64_t** row_ptr,
  * me is (d+1) x nme (me[a*nme + k]). The result is a CSR matrix of order
  * n = m nq with sorted column indices, returned in malloc'ed arrays that the
  * caller frees with orc_free. scale receives, per entry, the sum over its
- * contributions of their condition scale (see orc_element). On error *bad_id is
+ * contributions of their condition scale (see orc_element), abssum the sum of
+ * their absolute values. On error *bad_id is
  * the offending element (or vertex index for ORC_ERR_INDEX).
  */
 int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, const int32_t* me,
                  int c1_kind, const double* c1, int c2_kind, const double* c2,
                  int64_t* n_out, int64_t* nnz_out, int64_t** row_ptr, int32_t** col_idx,
-                 double** val, double** scale, int64_t* bad_id) {
+                 double** val, double** scale, double** abssum, int64_t* bad_id) {
   *bad_id = -1;
   if (d < 1 || d > 3 || nq < 0 || nme < 0) return ORC_ERR_ARG;
   int m = (kind == ORC_ELAS) ? d : 1;
@@ -345,7 +351,7 @@ int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, cons
       }
   }
   if (rc) { free(t); return rc; }
-  rc = triplets_to_csr(t, nt, n, row_ptr, col_idx, val, scale, nnz_out);
+  rc = triplets_to_csr(t, nt, n, row_ptr, col_idx, val, scale, abssum, nnz_out);
   free(t);
   if (rc) return rc;
   *n_out = n;
@@ -353,6 +359,69 @@ int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, cons
 }
 
 void orc_free(void* p) { free(p); }
+
+static int cmp_u64(const void* pa, const void* pb) {
+  const uint64_t a = *(const uint64_t*)pa, b = *(const uint64_t*)pb;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/*
+ * Nonzero pattern alone of the matrix that orc_assemble builds (the `sparse`
+ * constructor of Section 3 keeps one entry per distinct (row, column) of the
+ * triplets): every element contributes the (d+1)^2 vertex pairs (me(a,k), me(b,k));
+ * they are sorted as keys row * nq + column and repeated keys dropped. With m dofs
+ * per vertex (m > 1, vector problems of Section 5, dof = m vertex + component) each
+ * vertex pair (v, w) stands for the m x m block of entries (m v + l, m w + n).
+ * Returns malloc'ed CSR arrays (order m nq, sorted columns) the caller frees with
+ * orc_free; *bad_id is the offending element when an index is out of range.
+ */
+int orc_pattern(int d, int m, int64_t nq, int64_t nme, const int32_t* me, int64_t* nnz_out,
+                int64_t** row_ptr, int32_t** col_idx, int64_t* bad_id) {
+  *bad_id = -1;
+  if (d < 1 || d > 3 || m < 1 || nq < 0 || nme < 0) return ORC_ERR_ARG;
+  const int nv = d + 1;
+  const int64_t nk = nme * nv * nv;
+  uint64_t* key = (uint64_t*)malloc((size_t)(nk > 0 ? nk : 1) * sizeof(uint64_t));
+  if (!key) return ORC_ERR_NOMEM;
+  for (int64_t k = 0; k < nme; ++k)
+    for (int b = 0; b < nv; ++b)
+      for (int a = 0; a < nv; ++a) {
+        const int32_t r = me[(int64_t)a * nme + k], c = me[(int64_t)b * nme + k];
+        if (r < 0 || r >= nq || c < 0 || c >= nq) {
+          *bad_id = k;
+          free(key);
+          return ORC_ERR_INDEX;
+        }
+        key[(k * nv + b) * nv + a] = (uint64_t)r * (uint64_t)nq + (uint64_t)c;
+      }
+  qsort(key, (size_t)nk, sizeof(uint64_t), cmp_u64);
+  int64_t nu = 0;
+  for (int64_t i = 0; i < nk; ++i)
+    if (i == 0 || key[i] != key[i - 1]) key[nu++] = key[i];
+  /* scalar pattern as CSR: rows are vertices */
+  int64_t* vptr = (int64_t*)calloc((size_t)nq + 1, sizeof(int64_t));
+  if (!vptr) { free(key); return ORC_ERR_NOMEM; }
+  for (int64_t i = 0; i < nu; ++i) vptr[key[i] / (uint64_t)nq + 1] += 1;
+  for (int64_t v = 0; v < nq; ++v) vptr[v + 1] += vptr[v];
+  const int64_t n = (int64_t)m * nq, nnz = nu * m * m;
+  *row_ptr = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
+  *col_idx = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+  if (!*row_ptr || !*col_idx) { free(key); free(vptr); return ORC_ERR_NOMEM; }
+  int64_t j = 0;
+  (*row_ptr)[0] = 0;
+  for (int64_t v = 0; v < nq; ++v)
+    for (int l = 0; l < m; ++l) {
+      for (int64_t i = vptr[v]; i < vptr[v + 1]; ++i) {
+        const int64_t w = (int64_t)(key[i] % (uint64_t)nq);
+        for (int c = 0; c < m; ++c) (*col_idx)[j++] = (int32_t)(m * w + c);
+      }
+      (*row_ptr)[m * v + l + 1] = j;
+    }
+  free(key);
+  free(vptr);
+  *nnz_out = nnz;
+  return ORC_OK;
+}
 
 /*
  * General second-order operator of Eq. EDP, -div(A grad u) + div(b u) + c . grad u + a0 u,
@@ -373,7 +442,7 @@ void orc_free(void* p) { free(p); }
  */
 int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const int32_t* me,
                          int coef_kind, const double* coef, int64_t* n_out, int64_t* nnz_out,
-                         int64_t** row_ptr, int32_t** col_idx, double** val, double** scale,
+                         int64_t** row_ptr, int32_t** col_idx, double** val, double** scale, double** abssum,
                          int64_t* bad_id) {
   *bad_id = -1;
   if (d < 2 || d > 3) return ORC_ERR_ARG;
@@ -451,7 +520,7 @@ int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const 
       }
   }
   if (rc) { free(t); return rc; }
-  rc = triplets_to_csr(t, nme * ns, nq, row_ptr, col_idx, val, scale, nnz_out);
+  rc = triplets_to_csr(t, nme * ns, nq, row_ptr, col_idx, val, scale, abssum, nnz_out);
   free(t);
   *n_out = nq;
   return rc;
@@ -467,7 +536,7 @@ int orc_assemble_general(int d, int64_t nq, int64_t nme, const double* q, const 
  */
 int orc_assemble_table(int d, int64_t nq, int64_t nme, int ndfe, const double* q, const int32_t* me,
                        const double* tab, int64_t* n_out, int64_t* nnz_out, int64_t** row_ptr,
-                       int32_t** col_idx, double** val, double** scale, int64_t* bad_id) {
+                       int32_t** col_idx, double** val, double** scale, double** abssum, int64_t* bad_id) {
   *bad_id = -1;
   if (d < 2 || d > 3 || ndfe < d + 1) return ORC_ERR_ARG;
   const int64_t ns = (int64_t)ndfe * ndfe;
@@ -497,7 +566,7 @@ int orc_assemble_table(int d, int64_t nq, int64_t nme, int ndfe, const double* q
       }
   }
   if (rc) { free(t); return rc; }
-  rc = triplets_to_csr(t, nme * ns, nq, row_ptr, col_idx, val, scale, nnz_out);
+  rc = triplets_to_csr(t, nme * ns, nq, row_ptr, col_idx, val, scale, abssum, nnz_out);
   free(t);
   *n_out = nq;
   return rc;
@@ -533,7 +602,7 @@ int orc_facet(int d, const double* X, double* meas) {
  */
 int orc_assemble_boundary(int kind, int d, int64_t nq, int64_t nf, const double* q, const int32_t* fa,
                           int c1_kind, const double* c1, int64_t* n_out, int64_t* nnz_out,
-                          int64_t** row_ptr, int32_t** col_idx, double** val, double** scale,
+                          int64_t** row_ptr, int32_t** col_idx, double** val, double** scale, double** abssum,
                           int64_t* bad_id) {
   *bad_id = -1;
   if (d < 2 || d > 3 || (kind != ORC_MASS && kind != ORC_WMASS)) return ORC_ERR_ARG;
@@ -575,7 +644,7 @@ int orc_assemble_boundary(int kind, int d, int64_t nq, int64_t nf, const double*
       }
   }
   if (rc) { free(t); return rc; }
-  rc = triplets_to_csr(t, nf * ns, nq, row_ptr, col_idx, val, scale, nnz_out);
+  rc = triplets_to_csr(t, nf * ns, nq, row_ptr, col_idx, val, scale, abssum, nnz_out);
   free(t);
   *n_out = nq;
   return rc;

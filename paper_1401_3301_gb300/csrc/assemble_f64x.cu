@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __res
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     df cf[D][D];  // cofactor vectors c_1..c_D
-    df det = x64_geometry<D>(smem + S.q, lv, cf);
+    df det = x64_geometry_guarded<D>(smem + S.q, lv, cf, A.q, A.nq, lv_vid);
     if (df_degenerate(det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       det = df{1.f, 0.f};

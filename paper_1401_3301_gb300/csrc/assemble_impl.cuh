@@ -122,6 +122,7 @@ __device__ __forceinline__ void element_geo(const ElemArgs& A, int64_t e, int32_
     float xh[NV][D], xl[NV][D];
     load_x32<D>(A.qs, v, xh, xl);
     geo_f32<D>(xh, xl, g);
+    guard_det_f32<D>(g, A.q, A.nq, v);
   }
   if (!det_ok(g.det)) {
     fe_report(A.st, FE_ERR_DEGENERATE, A.order[e]);
@@ -237,8 +238,11 @@ __device__ __forceinline__ void stage_vertex(const double* __restrict__ q, int64
 }
 
 // Geometry of an element whose corners are the local vertices lv of the staged array sq.
+// FP32 form: a det B that fails its guard is recomputed in FP64 from q and the global
+// vertex ids lv_vid of the chunk's local vertices.
 template <int D, class T>
-__device__ __forceinline__ void staged_geo(const unsigned char* sq, const int lv[D + 1], Geo<D, T>& g) {
+__device__ __forceinline__ void staged_geo(const unsigned char* sq, const int lv[D + 1], Geo<D, T>& g,
+                                           const double* __restrict__ q, int64_t nq, const int32_t* lv_vid) {
   constexpr int NV = D + 1;
   if constexpr (sizeof(T) == 8) {
     double x[NV][D];
@@ -267,6 +271,12 @@ __device__ __forceinline__ void staged_geo(const unsigned char* sq, const int lv
       }
     }
     geo_f32<D>(xh, xl, g);
+    if (fabsf(g.det) < kDetGuardF32 * g.dsc) {
+      int32_t v[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) v[a] = lv_vid[lv[a]];
+      g.det = (float)det_from_q<D>(q, nq, v);
+    }
   }
 }
 
@@ -344,7 +354,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     Geo<D, T> g;
-    staged_geo<D, T>(smem + S.q, lv, g);
+    staged_geo<D, T>(smem + S.q, lv, g, A.q, A.nq, lv_vid);
     if (!det_ok(g.det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       g.det = T(1);

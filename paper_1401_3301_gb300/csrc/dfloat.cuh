@@ -131,7 +131,8 @@ __device__ __forceinline__ df x64_cofactors(const df e[D][D], df cf[D][D]) {
 // Edge vectors e[i] = x^{i+1} - x^0 (i < NE) of the corners lv[0..NE] staged by
 // x64_stage_vertex, as exact double-float differences of the split coordinates.
 template <int D, int NE>
-__device__ __forceinline__ void x64_edges(const unsigned char* sq, const int lv[NE + 1], df e[NE][D]) {
+__device__ __forceinline__ void x64_edges(const unsigned char* sq, const int lv[NE + 1], df e[NE][D],
+                                          float* xmax = nullptr) {
   constexpr int NV = NE + 1;
   float xh[NV][D], xl[NV][D];
 #pragma unroll
@@ -154,6 +155,14 @@ __device__ __forceinline__ void x64_edges(const unsigned char* sq, const int lv[
       const df s = two_sum(xh[i + 1][k], -xh[0][k]);
       e[i][k] = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][k], xl[0][k])));
     }
+  if (xmax) {
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) m = fmaxf(m, fabsf(xh[a][k]));
+    *xmax = m;
+  }
 }
 
 // square root of a positive double-float: one Newton step from the float root
@@ -171,6 +180,31 @@ __device__ __forceinline__ df x64_geometry(const unsigned char* sq, const int lv
   df e[D][D];
   x64_edges<D, D>(sq, lv, e);
   return x64_cofactors<D>(e, cf);
+}
+
+// x64_geometry with the det B guard of the F64X form (elem.cuh, kDetGuardF64X): a det B
+// below the guard times Xmax Emax^2 of the chunk-relative coordinates is recomputed in
+// FP64 from q and the global ids lv_vid of the chunk's local vertices.
+template <int D>
+__device__ __forceinline__ df x64_geometry_guarded(const unsigned char* sq, const int lv[D + 1], df cf[D][D],
+                                                   const double* __restrict__ q, int64_t nq,
+                                                   const int32_t* lv_vid) {
+  df e[D][D];
+  float xm;
+  x64_edges<D, D>(sq, lv, e, &xm);
+  df det = x64_cofactors<D>(e, cf);
+  float em = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int k = 0; k < D; ++k) em = fmaxf(em, fabsf(e[i][k].hi));
+  if (fabsf(det.hi) < kDetGuardF64X * xm * em * em) {
+    int32_t v[D + 1];
+#pragma unroll
+    for (int a = 0; a <= D; ++a) v[a] = lv_vid[lv[a]];
+    det = df_split(det_from_q<D>(q, nq, v));
+  }
+  return det;
 }
 
 // det B is zero or not finite (tested on its float rounding)

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     Geo<D, T> g;
-    staged_geo<D, T>(smem + S.q, lv, g);
+    staged_geo<D, T>(smem + S.q, lv, g, A.q, A.nq, lv_vid);
     if (!det_ok(g.det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       g.det = T(1);
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     df cf[D][D];
-    df det = x64_geometry<D>(smem + S.q, lv, cf);
+    df det = x64_geometry_guarded<D>(smem + S.q, lv, cf, A.q, A.nq, lv_vid);
     if (df_degenerate(det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       det = df{1.f, 0.f};

@@ -103,8 +103,35 @@ struct csum {
 template <int D, class T>
 struct Geo {
   T c[D + 1][D];
-  T det;  // FP64 form: det B; FP32 form: det B (double-float) rounded to float
+  T det;      // FP64 form: det B; FP32 form: det B (double-float) rounded to float
+  float dsc;  // FP32 form: error scale of the double-float det B (det_guard_f32)
 };
+
+// Guard on the double-float det B of the FP32 and F64X forms. Taking each coordinate as
+// a pair of floats moves it by less than 2^-47 |x|, so an edge by 2^-46 Xmax (Xmax the
+// largest |coordinate| of the element) and det B by at most about 2^-41 Xmax Emax^2
+// (Emax the largest |edge component|); the double-float products and sums of the rounded
+// edges add less than that. Where |det B| < guard * Xmax Emax^2 (a badly shaped element:
+// a sliver, a needle, or an element far smaller than its distance from the origin) the
+// kernels recompute det B in FP64 from the FP64 coordinates (det_from_q), whose edges
+// carry an error of u |e| only, so det B and |K| keep FP64 relative accuracy.
+// FP32 form: guard 2^-15, so a det B that is kept is within 2^-26 of its value.
+constexpr float kDetGuardF32 = 1.0f / 32768.0f;
+// F64X form (coordinates relative to the chunk's reference vertex): guard 2^-7, which
+// well-shaped elements clear by a wide margin (a Kuhn tetrahedron with its vertices
+// jittered by up to 0.15 h: |det B| / (Xmax Emax^2) above 0.01 in a chunk of diameter
+// up to about 10 h).
+constexpr float kDetGuardF64X = 1.0f / 128.0f;
+
+template <int D>
+__device__ __forceinline__ float abs_max(const float x[D + 1][D]) {
+  float m = 0.f;
+#pragma unroll
+  for (int a = 0; a <= D; ++a)
+#pragma unroll
+    for (int k = 0; k < D; ++k) m = fmaxf(m, fabsf(x[a][k]));
+  return m;
+}
 
 template <class T>
 __device__ __forceinline__ void cofactors3(const T e[3][3], Geo<3, T>& g) {
@@ -172,10 +199,15 @@ __device__ __forceinline__ void geo_f32(const float xh[D + 1][D], const float xl
       e[i][c] = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(xl[i + 1][c], xl[0][c])));
     }
   float eh[D][D];
+  float emax = 0.f;
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int c = 0; c < D; ++c) eh[i][c] = e[i][c].hi;
+    for (int c = 0; c < D; ++c) {
+      eh[i][c] = e[i][c].hi;
+      emax = fmaxf(emax, fabsf(eh[i][c]));
+    }
+  g.dsc = abs_max<D>(xh) * emax * emax;
   // det B = det(eh) + sum_i el_i . c_i + O(el^2): det(eh) in double-float from exact
   // products of the rounded edges, the low parts el against the float cofactors.
   if constexpr (D == 3) {
@@ -237,6 +269,33 @@ __device__ __forceinline__ void load_x32(const float4* __restrict__ qs, const in
       xl[a][0] = h.z; xl[a][1] = h.w;
     }
   }
+}
+
+// det B in FP64 of the element with vertex ids v, from the FP64 coordinates q (d x nq):
+// one FP64 subtraction per edge component, then the cofactor expansion along the first
+// edge. Taken only for elements whose double-float det B fails its guard, so it is kept
+// out of line.
+template <int D>
+__device__ __noinline__ double det_from_q(const double* __restrict__ q, int64_t nq, const int32_t* v) {
+  double x0[D], e[D][D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) x0[k] = __ldg(q + (int64_t)k * nq + v[0]);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int k = 0; k < D; ++k) e[i][k] = __ldg(q + (int64_t)k * nq + v[i + 1]) - x0[k];
+  if constexpr (D == 3)
+    return e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) + e[0][1] * (e[1][2] * e[2][0] - e[1][0] * e[2][2]) +
+           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+  else
+    return e[0][0] * e[1][1] - e[0][1] * e[1][0];
+}
+
+// FP32 form: replace a double-float det B that fails its guard by the FP64 one
+template <int D>
+__device__ __forceinline__ void guard_det_f32(Geo<D, float>& g, const double* __restrict__ q, int64_t nq,
+                                              const int32_t* v) {
+  if (fabsf(g.det) < kDetGuardF32 * g.dsc) g.det = (float)det_from_q<D>(q, nq, v);
 }
 
 // det B usable: nonzero, normal and finite (checked on the exponent bits)

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     Geo<D, T> g;
-    staged_geo<D, T>(smem + S.q, lv, g);
+    staged_geo<D, T>(smem + S.q, lv, g, A.q, A.nq, lv_vid);
     if (!det_ok(g.det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       g.det = T(1);
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(THREADS, P1 ? 2 : 3) k_chunk_general_x(General
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     df cfv[D][D];
-    df det = x64_geometry<D>(smem + S.q, lv, cfv);
+    df det = x64_geometry_guarded<D>(smem + S.q, lv, cfv, A.q, A.nq, lv_vid);
     if (df_degenerate(det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       det = df{1.f, 0.f};

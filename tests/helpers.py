@@ -24,6 +24,81 @@ def to_cuda(a, dtype=None):
     return t.cuda()
 
 
+# Per-form tolerance and unit roundoff (prec 0 = FP64, 1 = FP32, 2 = F64X; F64X is
+# double-float arithmetic, about 47 significant bits, on coordinates taken relative to a
+# reference vertex of the element chunk). RESOLVE = 16: a form's arithmetic errors in an
+# entry stay within about 16 units of its roundoff of the entry's normwise scale.
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
+UNIT = {0: 2.0 ** -53, 1: 2.0 ** -24, 2: 2.0 ** -46}
+RESOLVE = 16.0
+FORM_NAME = {0: "FP64", 1: "FP32", 2: "F64X"}
+
+# label -> {measure: max}, collected over the session and printed by conftest
+PARITY_LOG: dict = {}
+
+
+def value_errors(got, ref_val, ref_scale, ref_abs, unit=0.0, tol=1.0, well=1e-3):
+    """Per-nonzero error measures of computed values a against the oracle's sums b.
+
+    N_ij is the sum of the contributions' normwise scales (the size their arithmetic
+    rounds at), A_ij the sum of |contributions| (the condition scale of the sum).
+    norm:     |a - b| / max(|b|, N_ij)
+    comp:     |a - b| / max(|b|, A_ij), over every entry (0 / 0 = 0, x / 0 = inf);
+    comp_res: the same over the resolved entries, A_ij >= RESOLVE (unit / tol) N_ij: below
+              that the contributions cancel to less than the form's own rounding of each
+              of them can resolve at the tolerance (no implementation in that arithmetic,
+              the FP64 oracle included, meets it there), and those entries are held to
+              the normwise measure instead;
+    plain:    |a - b| / |b| over the entries with |b| >= well A_ij, b != 0.
+    Returns the measures and the counts n_unres (unresolved entries) and n_plain."""
+    a = np.asarray(got, dtype=np.float64)
+    b = np.asarray(ref_val, dtype=np.float64)
+    if a.size == 0:
+        return dict(norm=0.0, comp=0.0, comp_res=0.0, plain=0.0, n_unres=0, n_plain=0)
+    d = np.abs(a - b)
+    ab = np.abs(b)
+
+    def ratio(den, sel=None):
+        if sel is not None:
+            d_, den = d[sel], den[sel]
+        else:
+            d_ = d
+        if d_.size == 0:
+            return 0.0
+        pos = den > 0
+        r = np.where(pos, d_ / np.where(pos, den, 1.0), np.where(d_ > 0, np.inf, 0.0))
+        return float(np.max(r))
+
+    res = ref_abs >= RESOLVE * (unit / tol) * ref_scale
+    wsel = (ab >= well * ref_abs) & (ab > 0)
+    plain = float(np.max(d[wsel] / ab[wsel])) if wsel.any() else 0.0
+    dn = np.maximum(ab, ref_scale)
+    dc = np.maximum(ab, ref_abs)
+    return dict(norm=ratio(dn), comp=ratio(dc), comp_res=ratio(dc, res), plain=plain,
+                n_unres=int((~res).sum()), n_plain=int(wsel.sum()))
+
+
+def check_values(got, ref, prec, label, sl=slice(None)):
+    """Gate computed values against an oracle result dict (entries sl of it), after
+    logging the measures of value_errors under ``label``: the normwise error over every
+    entry and the error against the sum of |contributions| over the resolved entries,
+    both within the form's tolerance."""
+    tol = TOL[prec]
+    e = value_errors(got, ref["val"][sl], ref["scale"][sl], ref["abssum"][sl], UNIT[prec], tol)
+    key = f"{label} [{FORM_NAME.get(prec, prec)}]"
+    log = PARITY_LOG.setdefault(key, dict(norm=0.0, comp=0.0, comp_res=0.0, plain=0.0, n_unres=0,
+                                          n_plain=0, n=0, cases=0))
+    for k in ("norm", "comp", "comp_res", "plain"):
+        log[k] = max(log[k], e[k])
+    log["n_unres"] += e["n_unres"]
+    log["n_plain"] += e["n_plain"]
+    log["n"] += int(np.asarray(got).size)
+    log["cases"] += 1
+    assert e["norm"] <= tol, (label, FORM_NAME[prec], "normwise", e["norm"], tol)
+    assert e["comp_res"] <= tol, (label, FORM_NAME[prec], "sum of |contributions|", e["comp_res"], tol)
+    return e
+
+
 def normalised_error(got, ref_val, ref_scale):
     """max over entries of |got - ref| / max(|ref|, scale): relative error per nonzero,
     with cancelling sums measured against the size of their contributions."""

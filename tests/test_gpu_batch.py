@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import fe_or_skip, normalised_error, to_cuda
+from helpers import check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -34,15 +34,14 @@ def test_batch_matches_each_mesh(prec):
     wmass = fe.fe_assemble_wmass(p, qu, to_cuda(np.concatenate(w_v)).to(T), fe.COEF_P1, prec=prec)
     assert p.status() == (0, -1)
     rp, ci = (t.cpu().numpy() for t in p.csr())
-    tol = 1e-5 if prec == 1 else 1e-12
     for b, m in enumerate(meshes):
         rs = oracle.assemble(oracle.STIFF, m.q, m.me, c1=(oracle.COEF_P0, w_el[b]))
         rw = oracle.assemble(oracle.WMASS, m.q, m.me, c1=(oracle.COEF_P1, w_v[b]))
         sl = slice(int(no[b]), int(no[b + 1]))
         np.testing.assert_array_equal(rp[vo[b]:vo[b + 1] + 1] - no[b], rs["row_ptr"])
         np.testing.assert_array_equal(ci[sl] - vo[b], rs["col_idx"])
-        assert normalised_error(stiff[sl].double().cpu().numpy(), rs["val"], rs["scale"]) <= tol
-        assert normalised_error(wmass[sl].double().cpu().numpy(), rw["val"], rw["scale"]) <= tol
+        check_values(stiff[sl].double().cpu().numpy(), rs, prec, "2D batch: stiffness P0 w")
+        check_values(wmass[sl].double().cpu().numpy(), rw, prec, "2D batch: weighted mass P1")
 
 
 def test_graph_replay_with_fresh_weights_is_bit_identical_to_direct_calls():

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import fe_or_skip, normalised_error, to_cuda
+from helpers import check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -23,9 +23,9 @@ def test_single_element_2d_and_3d():
         assert p.nnz == (d + 1) ** 2
         for kind, fn in ((oracle.MASS, fe.fe_assemble_mass), (oracle.STIFF, fe.fe_assemble_stiff)):
             ref = oracle.assemble(kind, X, me)
-            for prec, tol in ((0, 1e-12), (1, 1e-5)):
+            for prec in (0, 1):
                 got = fn(p, to_cuda(X), prec=prec).double().cpu().numpy()
-                assert normalised_error(got, ref["val"], ref["scale"]) <= tol
+                check_values(got, ref, prec, "single element")
 
 
 def test_unreferenced_vertices_give_empty_rows():
@@ -42,7 +42,7 @@ def test_unreferenced_vertices_give_empty_rows():
     for strategy in (0, 1, 2):
         p.set_strategy(strategy)
         got = fe.fe_assemble_stiff(p, to_cuda(q)).cpu().numpy()
-        assert normalised_error(got, ref["val"], ref["scale"]) <= 1e-12
+        check_values(got, ref, 0, "3D stiffness, unreferenced vertices")
 
 
 def test_size_limits_are_checked_before_any_device_work():

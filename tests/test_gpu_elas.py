@@ -4,12 +4,9 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import assert_pattern_equal, fe_or_skip, normalised_error, to_cuda
+from helpers import assert_pattern_equal, check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
-
-TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
-
 
 def mesh(d, N, seed):
     return meshgen.square_mesh(N, seed=seed) if d == 2 else meshgen.kuhn_cube_mesh(N, seed=seed)
@@ -46,8 +43,7 @@ def test_elasticity_parity(d, N, kind, prec):
     assert_pattern_equal(p, ref)
     vals = fe.fe_assemble_elas(p, q, ld.to(T).cuda(), lk, md.to(T).cuda(), mk, prec=prec)
     assert p.status() == (0, -1)
-    err = normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"])
-    assert err <= TOL[prec], err
+    check_values(vals.double().cpu().numpy(), ref, prec, f"{d}D elasticity, {kind} Lame")
 
 
 @pytest.mark.parametrize("prec", [0, 2])

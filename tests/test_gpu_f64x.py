@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import fe_or_skip, normalised_error, to_cuda
+from helpers import check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -25,8 +25,8 @@ def test_f64x_matches_oracle_to_fp64_tolerance(d, N, offset):
         vals = fe.fe_assemble_stiff(p, q, None if coef is None else to_cuda(coef), prec=fe.F64X)
         assert vals.dtype == torch.float64
         assert p.status() == (0, -1)
-        err = normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"])
-        assert err <= 1e-12, err
+        check_values(vals.cpu().numpy(), ref, 2, f"{d}D stiffness{'' if coef is None else ' P0 w'}"
+                     f"{', offset' if offset else ''}")
         again = fe.fe_assemble_stiff(p, q, None if coef is None else to_cuda(coef), prec=fe.F64X)
         assert bool((again == vals).all())
 
@@ -48,12 +48,12 @@ def test_f64x_mass_and_weighted_mass_match_oracle(d, N, offset):
         (lambda: fe.fe_assemble_wmass(p, q, to_cuda(we), fe.COEF_P0, prec=fe.F64X),
          oracle.assemble(oracle.WMASS, qn, m.me, c1=(oracle.COEF_P0, we))),
     ]
+    names = ["mass", "weighted mass P1", "weighted mass P0"]
     for k, (run, ref) in enumerate(cases):
         vals = run()
         assert vals.dtype == torch.float64
         assert p.status() == (0, -1)
-        err = normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"])
-        assert err <= 1e-12, (k, err)
+        check_values(vals.cpu().numpy(), ref, 2, f"{d}D {names[k]}{', offset' if offset else ''}")
         assert bool((run() == vals).all())
 
 

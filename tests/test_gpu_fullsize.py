@@ -1,9 +1,10 @@
 """Parity at the full benchmark sizes, in the configurations bench.py times.
 
 At these sizes the oracle cannot assemble whole matrices within seconds, so the checks are
-(a) sampled rows: the oracle assembles only the elements that touch a random set of
+(a) the whole CSR pattern bit for bit against the oracle's pattern-only construction;
+(b) sampled rows: the oracle assembles only the elements that touch a random set of
 vertices, which makes exactly those rows complete, and the GPU rows must match them entry
-for entry (pattern bit for bit, values within the form's tolerance); and (b) identities of
+for entry (pattern bit for bit, values within the form's tolerance); and (c) identities of
 the whole matrix that hold at any size.
 """
 import numpy as np
@@ -11,23 +12,25 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import fe_or_skip, normalised_error, sub_mesh_rows, to_cuda
+from helpers import check_values, fe_or_skip, sub_mesh_rows, to_cuda
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
+def row_entries(rp, rows):
+    """Indices of the nonzeros of the given CSR rows, row after row."""
+    rows = np.asarray(rows, dtype=np.int64)
+    return np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows]) if len(rows) else np.zeros(0, np.int64)
 
 
-def check_rows(rp, ci, vals, ref, rows, tol, m=1):
-    """GPU CSR rows (numpy) against the oracle's complete rows; m dofs per vertex."""
-    for r in rows:
-        for c in range(m):
-            i = m * r + c
-            a, b = rp[i], rp[i + 1]
-            ra, rb = ref["row_ptr"][i], ref["row_ptr"][i + 1]
-            np.testing.assert_array_equal(ci[a:b], ref["col_idx"][ra:rb])
-            err = normalised_error(vals[a:b], ref["val"][ra:rb], ref["scale"][ra:rb])
-            assert err <= tol, (i, err)
+def check_rows(rp, ci, vals, ref, rows, prec, label, m=1, base=0):
+    """GPU CSR rows (numpy) against the oracle's complete rows; m dofs per vertex; the
+    GPU rows start at row base (a mesh inside a batch) and columns are shifted by it."""
+    dof_rows = (m * np.asarray(rows, dtype=np.int64)[:, None] + np.arange(m)[None, :]).ravel()
+    got = row_entries(rp, dof_rows + base)
+    want = row_entries(ref["row_ptr"], dof_rows)
+    np.testing.assert_array_equal(np.diff(rp)[dof_rows + base], np.diff(ref["row_ptr"])[dof_rows])
+    np.testing.assert_array_equal(ci[got] - base, ref["col_idx"][want])
+    check_values(vals[got], ref, prec, label, sl=want)
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +55,7 @@ def test_headline_stiffness_sampled_rows_and_identities(headline, prec):
     rows = np.random.default_rng(1).choice(m.nq, 300, replace=False)
     keep = sub_mesh_rows(m.me, rows, m.nq)
     ref = oracle.assemble(oracle.STIFF, m.q, np.ascontiguousarray(m.me[:, keep]))
-    check_rows(rp, ci, v, ref, rows, TOL[prec])
+    check_rows(rp, ci, v, ref, rows, prec, "3D N=100 stiffness, sampled rows")
     # S 1 = 0 and u^T S u = |a|^2 |Omega| for u = a.x + c (exact for P1 on the unit cube)
     A = torch.sparse_csr_tensor(torch.from_numpy(rp).long(), torch.from_numpy(ci).long(), torch.from_numpy(v),
                                 size=(p.n, p.n))
@@ -62,6 +65,33 @@ def test_headline_stiffness_sampled_rows_and_identities(headline, prec):
     u = torch.from_numpy(a @ m.q + 0.4).unsqueeze(1)
     uSu = float(u.T @ (A @ u))
     assert uSu == pytest.approx(float(a @ a), rel=1e-10 if prec != 1 else 2e-3)
+
+
+def test_headline_whole_pattern_bit_exact(headline):
+    # the whole CSR pattern of the 6,000,000-tet mesh (15,210,901 nonzeros, a 5-pass radix
+    # sort of 40-bit keys) against the oracle's sorted-key pattern, on the pattern the
+    # autotuner picks for each form (the CSR does not depend on the chunk plan)
+    fe, m, q, me = headline
+    from paper_1401_3301_gb300 import tune
+    rp_ref, ci_ref = oracle.pattern(m.me, m.nq)
+    assert len(ci_ref) == 15_210_901
+    for prec in (0, 1, 2):
+        p = tune.tuned_pattern(q, me, "stiff", prec)
+        rp, ci = (t.cpu().numpy() for t in p.csr())
+        np.testing.assert_array_equal(rp.astype(np.int64), rp_ref)
+        np.testing.assert_array_equal(ci, ci_ref)
+
+
+def test_elasticity_n80_whole_pattern_bit_exact():
+    # 3,072,000 tets, m = 3: 70,336,089 nonzeros in 3 x 3 blocks
+    fe = fe_or_skip()
+    m = meshgen.kuhn_cube_mesh(80, seed=0)
+    p = fe.fe_pattern(to_cuda(m.q), to_cuda(m.me), m=3)
+    rp_ref, ci_ref = oracle.pattern(m.me, m.nq, 3)
+    assert len(ci_ref) == 70_336_089
+    rp, ci = (t.cpu().numpy() for t in p.csr())
+    np.testing.assert_array_equal(rp.astype(np.int64), rp_ref)
+    np.testing.assert_array_equal(ci, ci_ref)
 
 
 def test_headline_mass_and_weighted_mass_sampled_rows(headline):
@@ -76,10 +106,11 @@ def test_headline_mass_and_weighted_mass_sampled_rows(headline):
     for prec in (0, 1):
         T = torch.float64 if prec == 0 else torch.float32
         mass = fe.fe_assemble_mass(p, q, prec=prec).double().cpu().numpy()
-        check_rows(rp, ci, mass, oracle.assemble(oracle.MASS, m.q, sub), rows, TOL[prec])
+        check_rows(rp, ci, mass, oracle.assemble(oracle.MASS, m.q, sub), rows, prec, "3D N=100 mass, sampled rows")
         assert mass.sum() == pytest.approx(1.0, rel=1e-12 if prec == 0 else 1e-5)  # 1^T M 1 = |Omega|
         wm = fe.fe_assemble_wmass(p, q, to_cuda(wv).to(T), fe.COEF_P1, prec=prec).double().cpu().numpy()
-        check_rows(rp, ci, wm, oracle.assemble(oracle.WMASS, m.q, sub, c1=(oracle.COEF_P1, wv)), rows, TOL[prec])
+        check_rows(rp, ci, wm, oracle.assemble(oracle.WMASS, m.q, sub, c1=(oracle.COEF_P1, wv)), rows, prec,
+                   "3D N=100 weighted mass P1, sampled rows")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -99,7 +130,7 @@ def test_elasticity_n80_sampled_rows(prec):
     keep = sub_mesh_rows(m.me, rows, m.nq)
     ref = oracle.assemble(oracle.ELAS, m.q, np.ascontiguousarray(m.me[:, keep]), c1=lam0, c2=mu0)
     rp, ci = (t.cpu().numpy() for t in p.csr())
-    check_rows(rp, ci, vals, ref, rows, TOL[prec], m=3)
+    check_rows(rp, ci, vals, ref, rows, prec, "3D N=80 elasticity, sampled rows", m=3)
 
 
 def test_differentiation_n64_against_oracle_gradients():
@@ -131,8 +162,8 @@ def test_2d_n100_whole_matrices():
                      (oracle.STIFF, lambda prec: fe.fe_assemble_stiff(p, q, prec=prec))):
         ref = oracle.assemble(kind, m.q, m.me)
         for prec in (0, 1):
-            err = normalised_error(fn(prec).double().cpu().numpy(), ref["val"], ref["scale"])
-            assert err <= TOL[prec], (kind, prec, err)
+            check_values(fn(prec).double().cpu().numpy(), ref, prec,
+                         "2D N=100 " + ("mass" if kind == oracle.MASS else "stiffness") + ", whole matrix")
 
 
 def test_batch_of_256_meshes_sampled_meshes():
@@ -159,19 +190,13 @@ def test_batch_of_256_meshes_sampled_meshes():
         ref = oracle.assemble(oracle.STIFF, x.q, x.me, c1=(oracle.COEF_P0, ws[b]))
         sl = slice(int(no[b]), int(no[b + 1]))
         np.testing.assert_array_equal(ci[sl] - vo[b], ref["col_idx"])
-        assert normalised_error(s[sl], ref["val"], ref["scale"]) <= 1e-12
+        check_values(s[sl], ref, 0, "2D batch of 256: smallest meshes whole")
     b = order[-1]
     x = meshes[b]
     rows = np.random.default_rng(4).choice(x.nq, 200, replace=False)
     keep = sub_mesh_rows(x.me, rows, x.nq)
     ref = oracle.assemble(oracle.STIFF, x.q, np.ascontiguousarray(x.me[:, keep]), c1=(oracle.COEF_P0, ws[b][keep]))
-    base = int(vo[b])
-    for r in rows:
-        i = base + r
-        a, e = rp[i], rp[i + 1]
-        ra, rb = ref["row_ptr"][r], ref["row_ptr"][r + 1]
-        np.testing.assert_array_equal(ci[a:e] - base, ref["col_idx"][ra:rb])
-        assert normalised_error(s[a:e], ref["val"][ra:rb], ref["scale"][ra:rb]) <= 1e-12
+    check_rows(rp, ci, s, ref, rows, 0, "2D batch of 256: largest mesh, sampled rows", base=int(vo[b]))
 
 
 def test_surface_n2000_boundary_mass_sampled_rows():
@@ -189,8 +214,9 @@ def test_surface_n2000_boundary_mass_sampled_rows():
     for prec in (0, 1):
         T = torch.float64 if prec == 0 else torch.float32
         mass = fe.fe_assemble_mass(p, q, prec=prec).double().cpu().numpy()
-        check_rows(rp, ci, mass, oracle.assemble_boundary(oracle.MASS, m.q, sub), rows, TOL[prec])
+        check_rows(rp, ci, mass, oracle.assemble_boundary(oracle.MASS, m.q, sub), rows, prec,
+                   "surface N=2000 facet mass, sampled rows")
         wm = fe.fe_assemble_wmass(p, q, to_cuda(wv).to(T), fe.COEF_P1, prec=prec).double().cpu().numpy()
         check_rows(rp, ci, wm, oracle.assemble_boundary(oracle.WMASS, m.q, sub, c1=(oracle.COEF_P1, wv)), rows,
-                   TOL[prec])
+                   prec, "surface N=2000 facet weighted mass P1, sampled rows")
         assert p.status() == (0, -1)

@@ -9,12 +9,9 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import assert_pattern_equal, fe_or_skip, normalised_error, to_cuda
+from helpers import assert_pattern_equal, check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
-
-TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
-
 
 def mesh(d, N, seed=0):
     return meshgen.square_mesh(N, seed=seed) if d == 2 else meshgen.kuhn_cube_mesh(N, seed=seed)
@@ -39,8 +36,7 @@ def test_parity_per_element(d, N, strategy, prec):
     assert_pattern_equal(p, ref)
     vals = fe.fe_assemble_general(p, q, to_cuda(cf, dtype(prec)), fe.COEF_P0, prec=prec)
     assert p.status() == (0, -1)
-    err = normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"])
-    assert err <= TOL[prec], err
+    check_values(vals.double().cpu().numpy(), ref, prec, f"{d}D general operator, P0 coefficients")
 
 
 @pytest.mark.parametrize("d,N", [(2, 29), (3, 8)])
@@ -56,8 +52,7 @@ def test_parity_p1_coefficients(d, N, strategy, prec):
     p.set_strategy(strategy)
     vals = fe.fe_assemble_general(p, q, to_cuda(cf, dtype(prec)), fe.COEF_P1, prec=prec)
     assert p.status() == (0, -1)
-    err = normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"])
-    assert err <= TOL[prec], err
+    check_values(vals.double().cpu().numpy(), ref, prec, f"{d}D general operator, P1 coefficients")
 
 
 @pytest.mark.parametrize("d", [2, 3])
@@ -71,14 +66,14 @@ def test_parity_scalar_and_internal_order(d, prec):
     # one coefficient set for the whole mesh
     ref = oracle.assemble_general(m.q, m.me, cf[0], oracle.COEF_SCALAR)
     vals = fe.fe_assemble_general(p, q, to_cuda(cf[0].copy(), dtype(prec)), fe.COEF_SCALAR, prec=prec)
-    assert normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"]) <= TOL[prec]
+    check_values(vals.double().cpu().numpy(), ref, prec, "3D general operator, scalar coefficients")
     # per element, given in the pattern's internal order
     order = p.element_order().cpu().numpy()
     ref = oracle.assemble_general(m.q, m.me, cf, oracle.COEF_P0)
     vals = fe.fe_assemble_general(p, q, to_cuda(cf[order].copy(), dtype(prec)), fe.COEF_P0_INTERNAL,
                                   prec=prec)
     assert p.status() == (0, -1)
-    assert normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"]) <= TOL[prec]
+    check_values(vals.double().cpu().numpy(), ref, prec, "3D general operator, scalar coefficients")
 
 
 @pytest.mark.parametrize("chunk", [32, 96])
@@ -93,7 +88,7 @@ def test_small_chunks_many_partials(chunk):
     p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(chunk))
     assert p.plan_info()["partial_edges"] > 0
     vals = fe.fe_assemble_general(p, q, to_cuda(cf), fe.COEF_P0)
-    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= TOL[0]
+    check_values(vals.cpu().numpy(), ref, 0, "3D general operator, small chunks")
 
 
 def test_deterministic_and_not_symmetric():
@@ -134,7 +129,7 @@ def test_batched_pattern():
     for i, x in enumerate(meshes):
         ref = oracle.assemble_general(x.q, x.me, cfs[i], oracle.COEF_P0)
         got = vals[int(no[i]):int(no[i + 1])].cpu().numpy()
-        assert normalised_error(got, ref["val"], ref["scale"]) <= TOL[0]
+        check_values(got, ref, 0, "2D general operator, batch")
 
 
 def test_rejects_unsupported_calls():
@@ -173,7 +168,7 @@ def test_f64x_form(d, N, kind):
             arg, k = cf[p.element_order().cpu().numpy()].copy(), fe.COEF_P0_INTERNAL
     vals = fe.fe_assemble_general(p, q, to_cuda(arg), k, prec=fe.F64X)
     assert p.status() == (0, -1)
-    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= TOL[2]
+    check_values(vals.cpu().numpy(), ref, 2, f"{d}D general operator, {kind} coefficients")
     again = fe.fe_assemble_general(p, q, to_cuda(arg), k, prec=fe.F64X)
     assert bool((again == vals).all())
     p.set_strategy(fe.REASM_GATHER)

@@ -12,12 +12,9 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import assert_pattern_equal, fe_or_skip, normalised_error, to_cuda
+from helpers import assert_pattern_equal, check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
-
-TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
-
 
 def test_library_table_is_the_exact_table_rounded():
     fe = fe_or_skip()
@@ -46,8 +43,7 @@ def test_parity(d, N, k, prec):
     assert_pattern_equal(p, ref)
     vals = fe.fe_assemble_mass(p, q, prec=prec)
     assert p.status() == (0, -1)
-    err = normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"])
-    assert err <= TOL[prec], err
+    check_values(vals.double().cpu().numpy(), ref, prec, f"{d}D P{k} mass")
     if prec != 1:
         import torch
         assert torch.equal(vals, fe.fe_assemble_mass(p, q, prec=prec))  # fixed summation order

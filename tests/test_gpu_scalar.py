@@ -9,12 +9,9 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import assert_pattern_equal, fe_or_skip, normalised_error, to_cuda
+from helpers import assert_pattern_equal, check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
-
-TOL = {0: 1e-12, 1: 1e-5}
-
 
 def mesh(d, N, seed=0):
     return meshgen.square_mesh(N, seed=seed) if d == 2 else meshgen.kuhn_cube_mesh(N, seed=seed)
@@ -76,8 +73,7 @@ def test_parity_all_kinds(d, N, strategy, prec):
             assert_pattern_equal(p, ref)
         vals = run(fe, p, kind, q, prec, None if c is None else to_cuda(c))
         assert p.status() == (0, -1)
-        err = normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"])
-        assert err <= TOL[prec], (kind, err)
+        check_values(vals.double().cpu().numpy(), ref, prec, f"{d}D {kind}, strategy {strategy}")
 
 
 @pytest.mark.parametrize("d", [2, 3])
@@ -156,7 +152,7 @@ def test_moved_vertices_same_pattern():
     p = fe.fe_pattern(q, me)
     ref = oracle.assemble(oracle.STIFF, m2.q, m2.me)
     vals = fe.fe_assemble_stiff(p, to_cuda(m2.q))
-    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
+    check_values(vals.cpu().numpy(), ref, 0, "3D stiffness, fixed pattern, new coordinates")
 
 
 def test_errors_are_reported():
@@ -197,9 +193,8 @@ def test_split_coordinates_fp32_form_accuracy_on_large_offsets():
     q, me = to_cuda(qs), to_cuda(m.me)
     p = fe.fe_pattern(q, me)
     ref = oracle.assemble(oracle.STIFF, qs, m.me)
-    err = normalised_error(fe.fe_assemble_stiff(p, q, prec=1).double().cpu().numpy(), ref["val"],
-                           ref["scale"])
-    assert err <= 1e-5, err
+    check_values(fe.fe_assemble_stiff(p, q, prec=1).double().cpu().numpy(), ref, 1,
+                 "3D stiffness, coordinates offset to 3000")
 
 
 def test_unordered_mesh_shrinks_chunks_and_stays_correct():
@@ -213,6 +208,6 @@ def test_unordered_mesh_shrinks_chunks_and_stays_correct():
     ref = oracle.assemble(oracle.WMASS, m.q, m.me, c1=(oracle.COEF_P1, meshgen.vertex_weights(1, m.nq)))
     import torch
     vals = fe.fe_assemble_wmass(p, q, to_cuda(meshgen.vertex_weights(1, m.nq)), fe.COEF_P1)
-    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
+    check_values(vals.cpu().numpy(), ref, 0, "3D weighted mass P1, unordered mesh")
     ref_s = oracle.assemble(oracle.STIFF, m.q, m.me)
-    assert normalised_error(fe.fe_assemble_stiff(p, q).cpu().numpy(), ref_s["val"], ref_s["scale"]) <= 1e-12
+    check_values(fe.fe_assemble_stiff(p, q).cpu().numpy(), ref_s, 0, "3D stiffness, unordered mesh")

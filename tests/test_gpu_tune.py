@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
-from helpers import fe_or_skip, normalised_error, to_cuda
+from helpers import check_values, fe_or_skip, to_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def test_autotune_caches_and_tuned_pattern_is_correct(tmp_path, monkeypatch):
     p = tune.tuned_pattern(q, me, chunks=(256, 512), threads=(128, 256), reps=3)
     ref = oracle.assemble(oracle.STIFF, m.q, m.me)
     vals = fe.fe_assemble_stiff(p, q)
-    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
+    check_values(vals.cpu().numpy(), ref, 0, "3D stiffness, tuned pattern")
 
 
 def test_autotune_disabled_returns_defaults_untimed(tmp_path, monkeypatch):
@@ -45,7 +45,7 @@ def test_autotune_disabled_returns_defaults_untimed(tmp_path, monkeypatch):
     assert p.plan_info()["chunk"] == fe.fe_pattern(q, me).plan_info()["chunk"]
     ref = oracle.assemble(oracle.STIFF, m.q, m.me)
     vals = fe.fe_assemble_stiff(p, q)
-    assert normalised_error(vals.cpu().numpy(), ref["val"], ref["scale"]) <= 1e-12
+    check_values(vals.cpu().numpy(), ref, 0, "3D stiffness, tuned pattern")
 
 
 @pytest.mark.parametrize("chunk,threads", [(256, 128), (768, 512), (1024, 256)])
@@ -57,9 +57,9 @@ def test_chunk_and_thread_variants_agree_with_oracle(chunk, threads):
     p.set_threads(threads)
     assert p.plan_info()["chunk"] == chunk
     ref = oracle.assemble(oracle.STIFF, m.q, m.me)
-    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+    for prec in (0, 1):
         vals = fe.fe_assemble_stiff(p, q, prec=prec)
-        assert normalised_error(vals.double().cpu().numpy(), ref["val"], ref["scale"]) <= tol
+        check_values(vals.double().cpu().numpy(), ref, prec, "3D stiffness, tuned pattern")
 
 
 def test_record_layouts_give_identical_values():

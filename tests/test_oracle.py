@@ -292,6 +292,86 @@ def test_pattern_brute_force(d):
     assert re["nnz"] == d * d * res["nnz"]
 
 
+@pytest.mark.parametrize("d,m_dofs", [(2, 1), (2, 2), (3, 1), (3, 3)])
+def test_pattern_alone_against_dense_adjacency(d, m_dofs):
+    # oracle.pattern (sorted keys, no values) against a dense boolean adjacency and, for
+    # vector unknowns, its Kronecker product with an m x m block of ones
+    m = meshgen.square_mesh(6, seed=31) if d == 2 else meshgen.kuhn_cube_mesh(3, seed=31)
+    rp, ci = oracle.pattern(m.me, m.nq, m_dofs)
+    adj = np.zeros((m.nq, m.nq), bool)
+    for k in range(m.nme):
+        adj[np.ix_(m.me[:, k], m.me[:, k])] = True
+    big = np.kron(adj, np.ones((m_dofs, m_dofs), bool))
+    r, c = np.nonzero(big)
+    np.testing.assert_array_equal(np.repeat(np.arange(m_dofs * m.nq), np.diff(rp)), r)
+    np.testing.assert_array_equal(ci, c)
+    # the same pattern as the full assembly's `sparse` step
+    kind, cs = (oracle.STIFF, ()) if m_dofs == 1 else (oracle.ELAS, (0.5, 0.3))
+    res = oracle.assemble(kind, m.q, m.me, *cs)
+    np.testing.assert_array_equal(rp, res["row_ptr"])
+    np.testing.assert_array_equal(ci, res["col_idx"])
+
+
+def exact_p1_matrices(q, me):
+    """Stiffness and mass entries of a P1 mesh in exact rational arithmetic: the coordinates
+    are taken as the exact rationals the doubles are, c_a the rows of adj(B) (c_0 = -sum),
+    stiffness |K| g_a.g_b = c_a.c_b / (d! |det B|), mass |det B| (1 + delta) / (d+2)!.
+    Returns {(i, j): [stiffness, mass, sum |stiffness contributions|]}."""
+    d = q.shape[0]
+    out = {}
+    for k in range(me.shape[1]):
+        v = [int(x) for x in me[:, k]]
+        X = [[Fraction(float(q[c, x])) for c in range(d)] for x in v]
+        B = [[X[i + 1][c] - X[0][c] for i in range(d)] for c in range(d)]  # column i = edge i
+        if d == 2:
+            det = B[0][0] * B[1][1] - B[0][1] * B[1][0]
+            adj = [[B[1][1], -B[0][1]], [-B[1][0], B[0][0]]]           # adj(B)
+        else:
+            det = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1])
+                   - B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0])
+                   + B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0]))
+            adj = [[(B[(j + 1) % 3][(i + 1) % 3] * B[(j + 2) % 3][(i + 2) % 3]
+                     - B[(j + 1) % 3][(i + 2) % 3] * B[(j + 2) % 3][(i + 1) % 3]) for j in range(3)]
+                   for i in range(3)]
+        c = [[-sum(adj[i][j] for i in range(d)) for j in range(d)]] + [adj[i] for i in range(d)]
+        fd, f2 = math.factorial(d), math.factorial(d + 2)
+        for a in range(d + 1):
+            for b in range(d + 1):
+                s = sum(c[a][j] * c[b][j] for j in range(d)) / (fd * abs(det))
+                mval = abs(det) * (2 if a == b else 1) / f2
+                e = out.setdefault((v[a], v[b]), [Fraction(0), Fraction(0), Fraction(0)])
+                e[0] += s
+                e[1] += mval
+                e[2] += abs(s)
+    return out
+
+
+@pytest.mark.parametrize("d,N", [(2, 6), (3, 3)])
+def test_values_against_exact_rational_arithmetic(d, N):
+    # the oracle's FP64 sums against the exactly computed matrices of the same (double)
+    # coordinates: errors within a few units of rounding of the normwise scale, and the
+    # sum of |contributions| (the condition scale of each entry) reproduced exactly
+    m = meshgen.square_mesh(N, seed=33) if d == 2 else meshgen.kuhn_cube_mesh(N, seed=33)
+    ex = exact_p1_matrices(m.q, m.me)
+    rs = oracle.assemble(oracle.STIFF, m.q, m.me)
+    rm = oracle.assemble(oracle.MASS, m.q, m.me)
+    rows = np.repeat(np.arange(rs["n"]), np.diff(rs["row_ptr"]))
+    keys = list(zip(rows.tolist(), rs["col_idx"].tolist()))
+    assert set(keys) == set(ex)
+    s_ex = np.array([float(ex[k][0]) for k in keys])
+    m_ex = np.array([float(ex[k][1]) for k in keys])
+    a_ex = np.array([float(ex[k][2]) for k in keys])
+    u = 2.0 ** -53
+    assert np.all(np.abs(rs["val"] - s_ex) <= 64 * u * rs["scale"])
+    assert np.all(np.abs(rs["abssum"] - a_ex) <= 64 * u * rs["scale"])
+    assert np.all(np.abs(rm["val"] - m_ex) <= 8 * u * np.abs(m_ex))
+    # per entry against the sum of |contributions|: the oracle itself meets the FP64 gate
+    # (entries whose every contribution is exactly zero are exactly zero on both sides)
+    zero = a_ex == 0
+    assert np.all(rs["val"][zero] == 0) and np.all(rs["abssum"][zero] == 0)
+    assert np.max(np.abs(rs["val"] - s_ex)[~zero] / a_ex[~zero]) <= 1e-13
+
+
 # ---------------------------------------------------------------- derivatives
 @pytest.mark.parametrize("d", [2, 3])
 def test_stiffness_loss_gradients(d):
