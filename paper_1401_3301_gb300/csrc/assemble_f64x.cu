@@ -38,7 +38,7 @@ struct X64Args {
 };
 
 template <int D, int KIND, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_chunk_f64x(X64Args A, double* __restrict__ vals,
+__global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args A, double* __restrict__ vals,
                                                         float2* __restrict__ partials) {
   constexpr int NV = D + 1, NP = Pairs<D>::n;
   extern __shared__ __align__(128) unsigned char smem[];

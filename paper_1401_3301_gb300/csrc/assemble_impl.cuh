@@ -30,6 +30,8 @@ __device__ __forceinline__ T elem_coef(const void* w, int w_kind, const int32_t*
 }
 
 // Local matrix entries from the geometry. wv: vertex values of the weight (P1 kind).
+// Stiffness: FP64 forms the Gram matrix of c_1..c_D and the row of vertex 0 from row
+// sums (fewer FP64 operations); FP32 takes c_a . c_b for every pair, c_0 included.
 // DEFER (stiffness): leave the per-element factor w / (d! |det B|) in out.scale for the
 // caller to apply while summing (one FMA per incidence instead of six products here).
 template <int D, class T, int KIND, bool DEFER = false>
@@ -44,6 +46,28 @@ __device__ __forceinline__ void values_from_geo(const Geo<D, T>& g, bool has_coe
     if constexpr (DEFER) {
       out.scale = inv;
       inv = T(1);
+    }
+    if constexpr (sizeof(T) == 4) {
+      // FP32: every entry from its own cofactors (c_0 from geo_f32): the row sums that
+      // the FP64 form uses for vertex 0 would cancel in float where c_0 is short
+      {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+          T t = g.c[a][0] * g.c[a][0];
+#pragma unroll
+          for (int k = 1; k < D; ++k) t += g.c[a][k] * g.c[a][k];
+          out.diag[a] = t * inv;
+        }
+#pragma unroll
+        for (int p = 0; p < Pairs<D>::n; ++p) {
+          const int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
+          T t = g.c[a][0] * g.c[b][0];
+#pragma unroll
+          for (int k = 1; k < D; ++k) t += g.c[a][k] * g.c[b][k];
+          out.off[p] = t * inv;
+        }
+        return;
+      }
     }
     // scaled Gram matrix of c_1..c_D; the row of vertex 0 follows from sum_a c_a = 0
     T G[D][D];
@@ -109,7 +133,7 @@ struct ElemArgs {
 
 // geometry of internal element e (vertex ids in v), coordinates gathered from global
 // memory; a degenerate element is reported and given det B = 1
-template <int D, class T>
+template <int D, class T, bool COF = true>
 __device__ __forceinline__ void element_geo(const ElemArgs& A, int64_t e, int32_t v[D + 1], Geo<D, T>& g) {
   constexpr int NV = D + 1;
 #pragma unroll
@@ -121,8 +145,8 @@ __device__ __forceinline__ void element_geo(const ElemArgs& A, int64_t e, int32_
   } else {
     float xh[NV][D], xl[NV][D];
     load_x32<D>(A.qs, v, xh, xl);
-    geo_f32<D>(xh, xl, g);
-    guard_det_f32<D>(g, A.q, A.nq, v);
+    geo_f32<D, COF>(xh, xl, g);
+    guard_geo_f32<D>(g, A.q, A.nq, v);
   }
   if (!det_ok(g.det)) {
     fe_report(A.st, FE_ERR_DEGENERATE, A.order[e]);
@@ -136,7 +160,7 @@ __device__ __forceinline__ void element_values(const ElemArgs& A, int64_t e, Sca
   constexpr int NV = D + 1;
   int32_t v[NV];
   Geo<D, T> g;
-  element_geo<D, T>(A, e, v, g);
+  element_geo<D, T, KIND == K_STIFF>(A, e, v, g);
   T wv[NV];
   if constexpr (KIND == K_WMASS_P1) {
 #pragma unroll
@@ -164,6 +188,7 @@ struct Acc<double> {
   }
   __device__ __forceinline__ void add_partial(const void* p, int64_t i) { s += ((const double*)p)[i]; }
   __device__ __forceinline__ void add_acc(const Acc& o) { s += o.s; }
+  __device__ __forceinline__ void scale2() { s *= 2.0; }  // exact
 };
 template <>
 struct Acc<float> {
@@ -187,6 +212,10 @@ struct Acc<float> {
     s.add2(v.x, v.y);
   }
   __device__ __forceinline__ void add_acc(const Acc& o) { s.add2(o.s.s, o.s.c); }
+  __device__ __forceinline__ void scale2() {  // exact: every rounding of the sum scales by 2
+    s.s *= 2.f;
+    s.c *= 2.f;
+  }
 };
 
 // ---------------------------------------------------------------- FE_REASM_CHUNKED
@@ -212,13 +241,22 @@ __device__ __forceinline__ bool load_plan_record(unsigned char* smem, uint64_t* 
 }
 
 // Coordinates of global vertex vid into local slot u of the staged coordinate array
-// sq: FP64 (x, y[, z]) in 16 (2D) or 32 (3D) bytes; FP32 the (hi, lo) float split.
+// sq: FP64 (x, y[, z]) in 16 (2D) or 32 (3D) bytes; FP32 the (hi, lo) float split of
+// x - xr, xr a reference vertex of the chunk (one FP64 subtraction per coordinate), so
+// that the split's error (2^-47 of the split value) scales with the chunk's extent, not
+// with the distance from the origin; xr = nullptr splits x itself.
 template <int D, class T>
 __device__ __forceinline__ void stage_vertex(const double* __restrict__ q, int64_t nq, int64_t vid,
-                                             unsigned char* sq, int u) {
+                                             unsigned char* sq, int u, const double* xr = nullptr) {
   double x[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) x[k] = __ldg(q + k * nq + vid);
+  if constexpr (sizeof(T) == 4) {
+    if (xr) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[k] -= xr[k];
+    }
+  }
   if constexpr (sizeof(T) == 8) {
     double* xs = (double*)sq + (D == 3 ? 4 : 2) * u;
     ((double2*)xs)[0] = make_double2(x[0], x[1]);
@@ -240,7 +278,7 @@ __device__ __forceinline__ void stage_vertex(const double* __restrict__ q, int64
 // Geometry of an element whose corners are the local vertices lv of the staged array sq.
 // FP32 form: a det B that fails its guard is recomputed in FP64 from q and the global
 // vertex ids lv_vid of the chunk's local vertices.
-template <int D, class T>
+template <int D, class T, bool COF = true>
 __device__ __forceinline__ void staged_geo(const unsigned char* sq, const int lv[D + 1], Geo<D, T>& g,
                                            const double* __restrict__ q, int64_t nq, const int32_t* lv_vid) {
   constexpr int NV = D + 1;
@@ -270,12 +308,12 @@ __device__ __forceinline__ void staged_geo(const unsigned char* sq, const int lv
         xl[a][0] = h.z; xl[a][1] = h.w;
       }
     }
-    geo_f32<D>(xh, xl, g);
-    if (fabsf(g.det) < kDetGuardF32 * g.dsc) {
+    geo_f32<D, COF>(xh, xl, g);
+    if (g.full || fabsf(g.det) < kDetGuardF32 * g.dsc) {
       int32_t v[NV];
 #pragma unroll
       for (int a = 0; a < NV; ++a) v[a] = lv_vid[lv[a]];
-      g.det = (float)det_from_q<D>(q, nq, v);
+      guard_geo_f32<D>(g, q, nq, v);
     }
   }
 }
@@ -294,6 +332,21 @@ struct StagedArgs {
   const uint32_t* rec_off16;
   fe_status_word* st;
   int64_t nnz, npart;  // sizes of vals and of the partial sums (bounds-checked builds)
+  const int32_t* me0;  // FP32 form: corner 0 of each internal element (chunk reference vertex)
+};
+
+// FP32 form: coordinates of the chunk's reference vertex, corner 0 of its first element
+// (independent of the record's vertex order), or none without me0
+template <int D>
+struct ChunkRef {
+  double x[D];
+  bool on;
+  __device__ __forceinline__ ChunkRef(const double* __restrict__ q, int64_t nq, const int32_t* me0, int64_t e0)
+      : on(me0 != nullptr) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = on ? __ldg(q + k * nq + me0[e0]) : 0.0;
+  }
+  __device__ __forceinline__ const double* ptr() const { return on ? x : nullptr; }
 };
 
 constexpr uint32_t kBarrierSpin = 1u << 22;
@@ -339,9 +392,10 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   // 0. vertex coordinates of the chunk, and the local vertex of every element corner
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
-    stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u);
+    stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
     if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
     for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
@@ -354,7 +408,7 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     Geo<D, T> g;
-    staged_geo<D, T>(smem + S.q, lv, g, A.q, A.nq, lv_vid);
+    staged_geo<D, T, KIND == K_STIFF>(smem + S.q, lv, g, A.q, A.nq, lv_vid);
     if (!det_ok(g.det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
       g.det = T(1);

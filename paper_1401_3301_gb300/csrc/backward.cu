@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_bwd_elem(BwdArgs A) {
       float xh[NV][D], xl[NV][D];
       load_x32<D>(A.qs, vv, xh, xl);
       geo_f32<D>(xh, xl, g);
-      guard_det_f32<D>(g, A.q, A.nq, vv);
+      guard_geo_f32<D>(g, A.q, A.nq, vv);
     }
     if (!det_ok(g.det)) {
       fe_report(A.st, FE_ERR_DEGENERATE, A.order[e]);

@@ -183,7 +183,7 @@ __device__ __forceinline__ df x64_geometry(const unsigned char* sq, const int lv
 }
 
 // x64_geometry with the det B guard of the F64X form (elem.cuh, kDetGuardF64X): a det B
-// below the guard times Xmax Emax^2 of the chunk-relative coordinates is recomputed in
+// below the guard times Xmax Emax^(d-1) of the chunk-relative coordinates is recomputed in
 // FP64 from q and the global ids lv_vid of the chunk's local vertices.
 template <int D>
 __device__ __forceinline__ df x64_geometry_guarded(const unsigned char* sq, const int lv[D + 1], df cf[D][D],
@@ -198,7 +198,7 @@ __device__ __forceinline__ df x64_geometry_guarded(const unsigned char* sq, cons
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int k = 0; k < D; ++k) em = fmaxf(em, fabsf(e[i][k].hi));
-  if (fabsf(det.hi) < kDetGuardF64X * xm * em * em) {
+  if (fabsf(det.hi) < kDetGuardF64X * xm * (D == 3 ? em * em : em)) {
     int32_t v[D + 1];
 #pragma unroll
     for (int a = 0; a <= D; ++a) v[a] = lv_vid[lv[a]];

@@ -118,9 +118,10 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
   // 0. coordinates (and P1 Lame values) of the chunk's vertices; local vertex of each corner
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
-    stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u);
+    stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
     if (A.lam_kind == FE_COEF_P1) lam_l[u] = ((const T*)A.lam)[vid];
     if (A.mu_kind == FE_COEF_P1) mu_l[u] = ((const T*)A.mu)[vid];
     for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;

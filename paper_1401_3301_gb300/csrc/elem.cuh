@@ -11,8 +11,8 @@
 //       lam' c_a[l] c_b[n] + mu' (delta_ln c_a . c_b + c_b[l] c_a[n]),
 //       lam' = lambda^s / (d! (d+1) |det B|), mu' likewise.
 // FP64 form: everything in double. FP32 form: coordinates arrive split into
-// (hi, lo) float pairs; edge vectors and det B are formed in double-float
-// arithmetic (FP64-class accuracy on the FP32 pipe), cofactors and values in float.
+// (hi, lo) float pairs; edge vectors, cofactors and det B are formed in double-float
+// arithmetic on the FP32 pipe (cofactors then rounded to float), values in float.
 #pragma once
 
 #include <stdint.h>
@@ -104,14 +104,15 @@ template <int D, class T>
 struct Geo {
   T c[D + 1][D];
   T det;      // FP64 form: det B; FP32 form: det B (double-float) rounded to float
-  float dsc;  // FP32 form: error scale of the double-float det B (det_guard_f32)
+  float dsc;  // FP32 form: error scale of the double-float det B (guard_geo_f32)
+  bool full;  // FP32 form: badly shaped element, to be recomputed in FP64 (geo_exact_f32)
 };
 
 // Guard on the double-float det B of the FP32 and F64X forms. Taking each coordinate as
 // a pair of floats moves it by less than 2^-47 |x|, so an edge by 2^-46 Xmax (Xmax the
-// largest |coordinate| of the element) and det B by at most about 2^-41 Xmax Emax^2
+// largest |coordinate| of the element) and det B by at most about 2^-41 Xmax Emax^(d-1)
 // (Emax the largest |edge component|); the double-float products and sums of the rounded
-// edges add less than that. Where |det B| < guard * Xmax Emax^2 (a badly shaped element:
+// edges add less than that. Where |det B| < guard * Xmax Emax^(d-1) (a badly shaped element:
 // a sliver, a needle, or an element far smaller than its distance from the origin) the
 // kernels recompute det B in FP64 from the FP64 coordinates (det_from_q), whose edges
 // carry an error of u |e| only, so det B and |K| keep FP64 relative accuracy.
@@ -159,6 +160,7 @@ __device__ __forceinline__ void cofactors2(const T e[2][2], Geo<2, T>& g) {
 
 template <int D, class T>
 __device__ __forceinline__ void form_c0(Geo<D, T>& g) {
+  if constexpr (sizeof(T) == 4) return;  // FP32: geo_f32 forms c_0 (accurately where it is small)
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     T s = -g.c[1][i];
@@ -166,6 +168,32 @@ __device__ __forceinline__ void form_c0(Geo<D, T>& g) {
     for (int a = 2; a <= D; ++a) s -= g.c[a][i];
     g.c[0][i] = s;
   }
+}
+
+// FP32 form: c_0 = -sum_a c_a (set by geo_f32 with the other cofactors)
+template <int D>
+__device__ __forceinline__ void form_c0_float(Geo<D, float>& g) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float s = -g.c[1][i];
+#pragma unroll
+    for (int a = 2; a <= D; ++a) s -= g.c[a][i];
+    g.c[0][i] = s;
+  }
+}
+
+// smallest of the cofactors' largest |component|
+template <int D>
+__device__ __forceinline__ float min_cofactor(const Geo<D, float>& g) {
+  float m = 3.4e38f;
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    float x = fabsf(g.c[a][0]);
+#pragma unroll
+    for (int k = 1; k < D; ++k) x = fmaxf(x, fabsf(g.c[a][k]));
+    m = fminf(m, x);
+  }
+  return m;
 }
 
 // FP64 geometry from vertex coordinates x[a][c]
@@ -186,8 +214,17 @@ __device__ __forceinline__ void geo_f64(const double x[D + 1][D], Geo<D, double>
 }
 
 // FP32 geometry from split coordinates (x = xh + xl): double-float edge vectors and
-// det B, float cofactors from the rounded edges.
-template <int D>
+// det B (rounded to float in g.det), float cofactors c_0..c_D from the rounded edges
+// (c_0 = -sum_a c_a), each component within about 3 2^-24 Emax^2 of its value.
+// Where some cofactor is smaller than kShapeGuard Emax^2 in every component (a tiny
+// face, a short edge or nearly parallel edges: needles and caps), that error would be
+// large against the cofactor itself, and so would the split coordinates' error against
+// a short edge: g.full is set, and the caller recomputes the element from the FP64
+// coordinates (geo_exact_f32). COF = false (operators without gradients) skips that
+// guard.
+constexpr float kShapeGuard = 0.25f;
+
+template <int D, bool COF = true>
 __device__ __forceinline__ void geo_f32(const float xh[D + 1][D], const float xl[D + 1][D],
                                         Geo<D, float>& g) {
   df e[D][D];
@@ -207,7 +244,7 @@ __device__ __forceinline__ void geo_f32(const float xh[D + 1][D], const float xl
       eh[i][c] = e[i][c].hi;
       emax = fmaxf(emax, fabsf(eh[i][c]));
     }
-  g.dsc = abs_max<D>(xh) * emax * emax;
+  g.dsc = abs_max<D>(xh) * (D == 3 ? emax * emax : emax);
   // det B = det(eh) + sum_i el_i . c_i + O(el^2): det(eh) in double-float from exact
   // products of the rounded edges, the low parts el against the float cofactors.
   if constexpr (D == 3) {
@@ -240,6 +277,53 @@ __device__ __forceinline__ void geo_f32(const float xh[D + 1][D], const float xl
       for (int k = 0; k < 2; ++k) lo = __fmaf_rn(e[i][k].lo, g.c[i + 1][k], lo);
     g.det = __fadd_rn(dh.hi, lo);
   }
+  form_c0_float<D>(g);
+  g.full = COF && min_cofactor<D>(g) < kShapeGuard * (D == 3 ? emax * emax : emax);
+}
+
+// FP32 form, badly shaped element (g.full): det B and the cofactors recomputed in FP64
+// from the FP64 coordinates of the element's vertices v (edges by one FP64 subtraction
+// each, c_a = e_{a+1} x e_{a+2}, c_0 = -sum_a c_a, det B = e_1 . c_1), then rounded to
+// float. Rare, so kept out of line.
+template <int D>
+__device__ __noinline__ void geo_exact_f32(const double* __restrict__ q, int64_t nq, const int32_t* v,
+                                           Geo<D, float>& g) {
+  double x0[D], e[D][D], c[D + 1][D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) x0[k] = __ldg(q + (int64_t)k * nq + v[0]);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int k = 0; k < D; ++k) e[i][k] = __ldg(q + (int64_t)k * nq + v[i + 1]) - x0[k];
+  double det;
+  if constexpr (D == 3) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double* u = e[(i + 1) % 3];
+      const double* w = e[(i + 2) % 3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) c[i + 1][k] = u[(k + 1) % 3] * w[(k + 2) % 3] - u[(k + 2) % 3] * w[(k + 1) % 3];
+    }
+    det = e[0][0] * c[1][0] + e[0][1] * c[1][1] + e[0][2] * c[1][2];
+  } else {
+    c[1][0] = e[1][1];
+    c[1][1] = -e[1][0];
+    c[2][0] = -e[0][1];
+    c[2][1] = e[0][0];
+    det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double s = -c[1][k];
+#pragma unroll
+    for (int a = 2; a <= D; ++a) s -= c[a][k];
+    c[0][k] = s;
+  }
+#pragma unroll
+  for (int a = 0; a <= D; ++a)
+#pragma unroll
+    for (int k = 0; k < D; ++k) g.c[a][k] = (float)c[a][k];
+  g.det = (float)det;
 }
 
 // coordinates of the d+1 vertices gathered from global memory
@@ -291,11 +375,13 @@ __device__ __noinline__ double det_from_q(const double* __restrict__ q, int64_t 
     return e[0][0] * e[1][1] - e[0][1] * e[1][0];
 }
 
-// FP32 form: replace a double-float det B that fails its guard by the FP64 one
+// FP32 form: recompute a badly shaped element in FP64 (geo_exact_f32), or replace a
+// double-float det B that fails its guard by the FP64 one
 template <int D>
-__device__ __forceinline__ void guard_det_f32(Geo<D, float>& g, const double* __restrict__ q, int64_t nq,
+__device__ __forceinline__ void guard_geo_f32(Geo<D, float>& g, const double* __restrict__ q, int64_t nq,
                                               const int32_t* v) {
-  if (fabsf(g.det) < kDetGuardF32 * g.dsc) g.det = (float)det_from_q<D>(q, nq, v);
+  if (g.full) geo_exact_f32<D>(q, nq, v, g);
+  else if (fabsf(g.det) < kDetGuardF32 * g.dsc) g.det = (float)det_from_q<D>(q, nq, v);
 }
 
 // det B usable: nonzero, normal and finite (checked on the exponent bits)

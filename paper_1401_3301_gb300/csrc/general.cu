@@ -316,8 +316,9 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
   T2* Ko = (T2*)(smem + S.ko);
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
 
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
-    stage_vertex<D, T>(A.q, A.nq, lv_vid[u], smem + S.q, u);
+    stage_vertex<D, T>(A.q, A.nq, lv_vid[u], smem + S.q, u, xr.ptr());
     for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();

@@ -27,7 +27,8 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream purposes
-JITTER, ELEM_PERM, VERT_PERM, VERT_WEIGHT, ELEM_WEIGHT, VECTORS, BATCH_SIZES, GEN_COEF = 1, 2, 3, 4, 5, 6, 7, 8
+JITTER, ELEM_PERM, VERT_PERM, VERT_WEIGHT, ELEM_WEIGHT, VECTORS, BATCH_SIZES, GEN_COEF, SHAPES = (
+    1, 2, 3, 4, 5, 6, 7, 8, 9)
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -154,6 +155,52 @@ def kuhn_cube_mesh(N: int, seed: int = 0, jitter: float = 0.15, perm_vertices: b
         tets.append(np.stack([base, p1, p2, p3]))
     me = np.stack(tets, axis=2).reshape(4, -1).astype(np.int32)
     return _finish(3, q, me, seed, jitter, interior, 1.0 / N, perm_vertices, perm_elements)
+
+
+def _rotation(key: int, i: int, d: int) -> np.ndarray:
+    """A random d x d rotation (QR of a Gaussian matrix, signs fixed, det +1)."""
+    u = uniform(key, 2 * d * d, offset=2 * d * d * i)
+    g = np.sqrt(-2.0 * np.log(1.0 - u[0::2])) * np.cos(2.0 * np.pi * u[1::2])
+    Q, R = np.linalg.qr(g.reshape(d, d))
+    Q = Q * np.sign(np.diag(R))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    return Q
+
+
+def badly_shaped_mesh(d: int, flat: list, seed: int = 0, size: float = 0.02,
+                      center=None, spread: float = 0.1) -> Mesh:
+    """Isolated, badly shaped simplices (no shared vertices), three per flatness value eps
+    in ``flat``, each turned by its own random rotation, scaled to ``size`` and placed at a
+    random point of the box of side ``spread`` around ``center`` (default the middle of the
+    unit box; the default spread of 5 sizes is the extent of an element chunk of a mesh). 3D: a sliver (four nearly coplanar vertices spanning a unit square, lifted by
+    -+eps), a cap (one vertex at height eps over the middle of the opposite face) and a
+    needle (three edges along one direction, spread by eps); det B is about eps (eps^2 for
+    the needle) of the products it is formed from. 2D: a cap (one vertex at height eps over
+    the middle of the opposite edge), a needle (a short edge of length eps) and a sliver
+    (the cap's apex moved near an end of the base)."""
+    key = stream_key(seed, SHAPES)
+    c0 = np.full(d, 0.5) if center is None else np.asarray(center, dtype=np.float64)
+    verts, k = [], 0
+    for eps in flat:
+        if d == 3:
+            shapes = [
+                [(0, 0, eps), (1, 0, -eps), (1, 1, eps), (0, 1, -eps)],                # sliver
+                [(0, 0, 0), (1, 0, 0), (0.3, 0.9, 0), (0.45, 0.3, eps)],            # cap
+                [(0, 0, 0), (1, 0, 0), (0.6, np.sqrt(eps), 0), (0.4, 0, np.sqrt(eps))],  # needle
+            ]
+        else:
+            shapes = [[(0, 0), (1, 0), (0.5, eps)], [(0, 0), (eps, 0), (0.3, 1.0)], [(0, 0), (1, 0), (0.98, eps)]]
+        for sh in shapes:
+            X = np.array(sh, dtype=np.float64)
+            X = X - X.mean(axis=0)
+            R = _rotation(key, k, d)
+            off = (uniform(key, d, offset=10 ** 6 + d * k) - 0.5) * spread
+            verts.append((X @ R.T) * size + c0 + off)
+            k += 1
+    q = np.concatenate(verts, axis=0).T.copy()
+    me = np.arange(q.shape[1], dtype=np.int32).reshape(-1, d + 1).T.copy()
+    return Mesh(d, q, me)
 
 
 def pk_node_order(d: int, k: int) -> list:

@@ -1,4 +1,7 @@
 """Shared test helpers: library loading, oracle comparison and error metrics."""
+import math
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -120,3 +123,37 @@ def sub_mesh_rows(me, rows_vertices, nq):
     mark[rows_vertices] = True
     keep = mark[me].any(axis=0)
     return np.nonzero(keep)[0]
+
+
+def exact_p1_matrices(q, me):
+    """Stiffness and mass entries of a P1 mesh in exact rational arithmetic: the coordinates
+    are taken as the exact rationals the doubles are, c_a the rows of adj(B) (c_0 = -sum),
+    stiffness |K| g_a.g_b = c_a.c_b / (d! |det B|), mass |det B| (1 + delta) / (d+2)!.
+    Returns {(i, j): [stiffness, mass, sum |stiffness contributions|]}."""
+    d = q.shape[0]
+    out = {}
+    for k in range(me.shape[1]):
+        v = [int(x) for x in me[:, k]]
+        X = [[Fraction(float(q[c, x])) for c in range(d)] for x in v]
+        B = [[X[i + 1][c] - X[0][c] for i in range(d)] for c in range(d)]  # column i = edge i
+        if d == 2:
+            det = B[0][0] * B[1][1] - B[0][1] * B[1][0]
+            adj = [[B[1][1], -B[0][1]], [-B[1][0], B[0][0]]]           # adj(B)
+        else:
+            det = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1])
+                   - B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0])
+                   + B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0]))
+            adj = [[(B[(j + 1) % 3][(i + 1) % 3] * B[(j + 2) % 3][(i + 2) % 3]
+                     - B[(j + 1) % 3][(i + 2) % 3] * B[(j + 2) % 3][(i + 1) % 3]) for j in range(3)]
+                   for i in range(3)]
+        c = [[-sum(adj[i][j] for i in range(d)) for j in range(d)]] + [adj[i] for i in range(d)]
+        fd, f2 = math.factorial(d), math.factorial(d + 2)
+        for a in range(d + 1):
+            for b in range(d + 1):
+                s = sum(c[a][j] * c[b][j] for j in range(d)) / (fd * abs(det))
+                mval = abs(det) * (2 if a == b else 1) / f2
+                e = out.setdefault((v[a], v[b]), [Fraction(0), Fraction(0), Fraction(0)])
+                e[0] += s
+                e[1] += mval
+                e[2] += abs(s)
+    return out
