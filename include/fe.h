@@ -46,7 +46,11 @@ extern "C" {
 #define FE_ERR_OVERFLOW 4   /* a size does not fit the library's 32-bit indices */
 #define FE_ERR_CUDA 5       /* a CUDA runtime call failed */
 #define FE_ERR_TIMEOUT 6    /* a bounded device-side wait for a chunk's plan record
-                               gave up; that chunk's values are missing */
+                               gave up; that chunk's values are missing, and the
+                               block that gave up may have left its record copy in
+                               flight into shared memory (it waits once more, also
+                               bounded): treat every value of that launch and of any
+                               launch overlapping it as undefined */
 #define FE_ERR_NOMEM 7      /* device allocation failed */
 #define FE_ERR_SCRATCH_LIMIT 8 /* the mesh needs more scratch than fe_assemble_stiff_noalloc has */
 #define FE_ERR_BOUNDS 9     /* bounds-checked builds only (FE_CHECKED): an index fell outside its
@@ -244,6 +248,11 @@ int fe_pattern_set_strategy(fe_pattern_h h, int32_t strategy);
  * (default) or 512. Set by the autotuner (paper_1401_3301_gb300/tune.py). */
 int fe_pattern_set_threads(fe_pattern_h h, int32_t threads);
 
+/* Launch shape of fe_assemble_wmass_stiff: 1 (default) a persistent grid of as many
+ * blocks as fit on the device at once, each looping over element chunks; 0 one block
+ * per chunk. Set by the autotuner. FE_ERR_ARG for other values. */
+int fe_pattern_set_persistent(fe_pattern_h h, int32_t persistent);
+
 /* Device bytes held by the handle (pattern, plan and scratch). */
 int fe_pattern_memory(fe_pattern_h h, int64_t* bytes);
 
@@ -306,6 +315,24 @@ int fe_assemble_wmass(fe_pattern_h h, const double* q, const void* w, int32_t w_
                       int32_t prec, void* vals, void* stream);
 int fe_assemble_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
                       int32_t prec, void* vals, void* stream);
+
+/*
+ * fe_assemble_wmass_stiff -- the weighted mass and the stiffness matrix with the same
+ * per-element coefficient in one pass, for repeated reassembly with new coefficients
+ * (the motivation of Section 1; the paper assembles each matrix by its own pass,
+ * Algorithms 6 and 7). vals_mass receives the matrix of fe_assemble_wmass and
+ * vals_stiff that of fe_assemble_stiff for the same w / w_kind (FE_COEF_NONE: the
+ * plain mass matrix and the unweighted stiffness), bit for bit: one chunk kernel
+ * reads each plan record once, forms each element's geometry once and keeps both
+ * matrices' sums in the separate calls' order; one fixup completes the shared
+ * entries. w_kind: FE_COEF_NONE, FE_COEF_P0 or FE_COEF_P0_INTERNAL (w NULL only for
+ * NONE). prec: FE_F64 or FE_F32 (FE_F64X: FE_ERR_ARG). Pattern: m = 1 volume pattern
+ * from fe_pattern or fe_batch_pattern, chunked strategy (else FE_ERR_ARG). The two
+ * value arrays must be distinct, nnz entries each. Asynchronous on `stream`; launch
+ * shape as set by fe_pattern_set_persistent.
+ */
+int fe_assemble_wmass_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
+                            int32_t prec, void* vals_mass, void* vals_stiff, void* stream);
 
 /*
  * fe_assemble_elas -- elastic stiffness (Eq. StiffElasMat, Section 5.1) for an
@@ -419,13 +446,15 @@ int fe_profile_read(fe_pattern_h h, int32_t max_kernels, char* names, double* ms
 
 /*
  * fe_assemble_stiff_noalloc -- the stiffness assembly of fe_assemble_stiff (same
- * arguments, same result up to the summation order), computed by the two-pass
- * scheme of FE_REASM_GATHER, that allocates no device memory. The paper has no
+ * arguments, with prec FE_F64 or FE_F32 only: FE_F64X gives FE_ERR_ARG; same result up
+ * to the summation order), computed by the two-pass scheme of FE_REASM_GATHER, that
+ * allocates no device memory. The paper has no
  * counterpart: this exists for callers that may not call cudaMalloc while they
  * assemble, such as a plugin inside an application that owns the whole
  * device-memory budget, or a time-stepping loop that cannot afford the device
  * synchronisation cudaMalloc may cause. Build the pattern first (fe_pattern
- * allocates); this call then only reads the handle and writes `vals`.
+ * allocates); this call then reads the handle and writes `vals`, and in FE_F32 also
+ * rewrites the handle's split-coordinate buffer (allocated with the pattern).
  *   - Its element values go to a fixed 16 MiB scratch array that is part of the
  *     library's device image (every GPU that loads the library holds it until the
  *     process exits). Meshes that need more, i.e. nme (d+1)^2 times 8 bytes
@@ -434,11 +463,18 @@ int fe_profile_read(fe_pattern_h h, int32_t max_kernels, char* names, double* ms
  *     in FP64, 262,144 in FP32).
  *   - The first call on a device looks up the scratch array's device address
  *     (cudaGetSymbolAddress, no allocation) with that device current, and caches
- *     it; make that first call before any stream capture.
+ *     it; make that first call before any stream capture. The cache lives as long as
+ *     the process's device contexts: a cudaDeviceReset invalidates it, as it does
+ *     every pattern handle's device memory.
  *   - Every call, on any handle, shares the one scratch array, which keeps the last
  *     call's contents: two calls whose kernels overlap on the GPU (different
  *     streams, no ordering between them) race and give wrong results. Every slot
  *     the second pass reads is written by the first, so nothing needs clearing.
+ *   - In FE_F32 the call also rewrites the handle's split-coordinate buffer, which the
+ *     FE_F32 calls of fe_assemble_stiff (gather and atomic strategies), of
+ *     fe_assemble_general and of the backward calls on the same handle use too: order
+ *     such calls on one handle (one stream, or events), even where neither of them
+ *     uses the scratch array.
  */
 int fe_assemble_stiff_noalloc(fe_pattern_h h, const double* q, const void* w, int32_t w_kind,
                               int32_t prec, void* vals, void* stream);

@@ -16,6 +16,10 @@ int fe_launch_scalar_f64(fe_pattern_s* h, int kind, const double* q, const void*
                          void* vals, cudaStream_t s);
 int fe_launch_scalar_f32(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind,
                          void* vals, cudaStream_t s);
+int fe_launch_pair_f64(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals_mass,
+                       void* vals_stiff, cudaStream_t s);
+int fe_launch_pair_f32(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals_mass,
+                       void* vals_stiff, cudaStream_t s);
 int fe_launch_f64x(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, void* vals,
                    cudaStream_t s);
 int fe_launch_boundary(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, int prec,
@@ -195,6 +199,12 @@ int fe_pattern_set_threads(fe_pattern_h h, int32_t threads) {
   return FE_OK;
 }
 
+int fe_pattern_set_persistent(fe_pattern_h h, int32_t persistent) {
+  if (!h || (persistent != 0 && persistent != 1)) return FE_ERR_ARG;
+  h->persistent = persistent;
+  return FE_OK;
+}
+
 int fe_pattern_memory(fe_pattern_h h, int64_t* bytes) {
   if (!h || !bytes) return FE_ERR_ARG;
   *bytes = h->bytes;
@@ -303,6 +313,18 @@ int fe_assemble_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_
   if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL)
     return FE_ERR_ARG;
   return scalar_call(h, 3, q, w, w_kind, prec, vals, stream);
+}
+
+int fe_assemble_wmass_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_kind, int32_t prec,
+                            void* vals_mass, void* vals_stiff, void* stream) {
+  FE_TRY(check_common(h, q, prec, vals_mass));
+  if (!vals_stiff || vals_stiff == vals_mass) return FE_ERR_ARG;
+  if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
+  if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL) return FE_ERR_ARG;
+  if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == FE_F64) return fe_launch_pair_f64(h, q, w, w_kind, vals_mass, vals_stiff, s);
+  return fe_launch_pair_f32(h, q, w, w_kind, vals_mass, vals_stiff, s);
 }
 
 int fe_assemble_elas(fe_pattern_h h, const double* q, const void* lam, int32_t lam_kind,

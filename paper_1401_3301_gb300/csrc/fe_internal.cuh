@@ -43,6 +43,7 @@ void fe_host_pipe_free(struct fe_pattern_s* h);
 struct fe_pattern_s {
   int d = 0, m = 1, nv = 0, npair = 0, flags = 0, strategy = FE_REASM_CHUNKED;
   int threads = 256;                // threads per block of the chunked scalar kernel
+  int persistent = 1;               // weighted mass + stiffness kernel: resident grid looping over chunks
   int kdim = 0;                     // element dimension: d (volume) or d - 1 (boundary facets)
   int pk = 1;                       // polynomial degree of the element nodes (App. D); nv nodes
   void* pk_tab = nullptr;           // pk > 1: P_k mass table, double[nv + npair] then float[nv + npair]

@@ -59,6 +59,8 @@ def lib() -> C.CDLL:
         L.fe_assemble_mass.argtypes = [P, P, I32, P, P]
         L.fe_assemble_wmass.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_assemble_stiff.argtypes = [P, P, P, I32, I32, P, P]
+        L.fe_assemble_wmass_stiff.argtypes = [P, P, P, I32, I32, P, P, P]
+        L.fe_pattern_set_persistent.argtypes = [P, I32]
         L.fe_assemble_elas.argtypes = [P, P, P, I32, P, I32, I32, P, P]
         L.fe_assemble_general.argtypes = [P, P, P, I32, I32, P, P]
         L.fe_pk_pattern.argtypes = [P, I32, I32, P, P]
@@ -90,7 +92,7 @@ def lib() -> C.CDLL:
                      "fe_batch_count", "fe_batch_gather_q", "fe_pattern_set_threads",
                      "fe_boundary_pattern", "fe_assemble_general", "fe_pk_pattern", "fe_pk_mass_table",
                      "fe_morton_vertex_order", "fe_apply_vertex_order", "fe_assemble_stiff_host",
-                     "fe_selftest_wait_timeout"):
+                     "fe_selftest_wait_timeout", "fe_assemble_wmass_stiff", "fe_pattern_set_persistent"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -178,6 +180,9 @@ class Pattern:
 
     def set_threads(self, threads: int):
         _check(lib().fe_pattern_set_threads(self.handle, threads))
+
+    def set_persistent(self, persistent: bool):
+        _check(lib().fe_pattern_set_persistent(self.handle, 1 if persistent else 0))
 
     def memory(self) -> int:
         b = C.c_int64()
@@ -363,6 +368,20 @@ def fe_assemble_stiff(p: Pattern, q: torch.Tensor, w: torch.Tensor | None = None
     _check(lib().fe_assemble_stiff(p.handle, _dev(q, torch.float64, "q"), _dev(w, _vtype(prec), "w"),
                                    w_kind, prec, _dev(vals, _vtype(prec), "vals"), _stream(stream)))
     return vals
+
+
+def fe_assemble_wmass_stiff(p: Pattern, q: torch.Tensor, w: torch.Tensor | None = None,
+                            w_kind: int | None = None, prec: int = F64, vals_mass=None, vals_stiff=None,
+                            stream=None):
+    """(weighted mass, stiffness) with one per-element coefficient, in one pass (include/fe.h)."""
+    vals_mass = _out(p, vals_mass, prec)
+    vals_stiff = _out(p, vals_stiff, prec)
+    if w_kind is None:
+        w_kind = COEF_NONE if w is None else COEF_P0
+    _check(lib().fe_assemble_wmass_stiff(p.handle, _dev(q, torch.float64, "q"), _dev(w, _vtype(prec), "w"), w_kind,
+                                         prec, _dev(vals_mass, _vtype(prec), "vals_mass"),
+                                         _dev(vals_stiff, _vtype(prec), "vals_stiff"), _stream(stream)))
+    return vals_mass, vals_stiff
 
 
 def fe_assemble_stiff_host(p: Pattern, q_host: torch.Tensor, vals_host: torch.Tensor, w_host=None,

@@ -1,10 +1,11 @@
 """Autotuner of the fixed-pattern reassembly.
 
-For one mesh and operator it times the chunked kernel over a grid of chunk sizes
-(elements per block, i.e. work per thread), the two layouts of the chunk records
-(distinct vertices and edges by incidence count, or in nonzero order) and threads
-per block, and optionally the two-pass gather and atomic strategies, with CUDA events (median of `reps`
-calls after one warm-up). The winner is cached in a JSON file keyed by GPU name,
+For one mesh (or one batch of meshes) and operator it times the chunked kernel over a
+grid of chunk sizes (elements per block, i.e. work per thread), the two layouts of the
+chunk records (distinct vertices and edges by incidence count, or in nonzero order) and
+threads per block, for the fused weighted mass + stiffness kernel also its launch shape
+(persistent grid or one block per chunk), and optionally the two-pass gather and atomic
+strategies, with CUDA events (median of `reps` calls after one warm-up). The winner is cached in a JSON file keyed by GPU name,
 dimension, dofs per vertex, operator, precision and the element count's power of
 two, so later meshes of the same class reuse it without timing. With the environment
 variable FE_AUTOTUNE=0 nothing is timed and the library defaults are returned.
@@ -22,6 +23,7 @@ from . import build_ext, fe
 
 CHUNKS = (256, 384, 512, 768, 1024)
 THREADS = (128, 256, 512)
+PERSISTENT = (True, False)
 LAYOUTS = (0, fe.PATTERN_ENTITY_ORDER)
 _FORM = {fe.F64: "f64", fe.F32: "f32", fe.F64X: "f64x"}
 
@@ -36,7 +38,8 @@ def enabled() -> bool:
 
 
 # the configuration of a pattern built without flags (chunk 0: the library's default)
-DEFAULT = {"strategy": "chunked", "chunk": 0, "layout": 0, "threads": 256, "ms": None, "tried": 0}
+DEFAULT = {"strategy": "chunked", "chunk": 0, "layout": 0, "threads": 256, "persistent": True, "ms": None,
+           "tried": 0}
 
 
 def _key(d, m, kind, prec, nme) -> str:
@@ -44,7 +47,9 @@ def _key(d, m, kind, prec, nme) -> str:
     return f"{name}|d{d}|m{m}|{kind}|{_FORM[prec]}|2^{int(math.log2(max(nme, 1)))}"
 
 
-def _call(p, q, kind, prec, w, w_kind, vals):
+def _call(p, q, kind, prec, w, w_kind, vals, vals2=None):
+    if kind == "wmass_stiff":
+        return fe.fe_assemble_wmass_stiff(p, q, w, w_kind, prec=prec, vals_mass=vals, vals_stiff=vals2)
     if kind == "stiff":
         return fe.fe_assemble_stiff(p, q, w, w_kind, prec=prec, vals=vals)
     if kind == "mass":
@@ -75,14 +80,20 @@ def _load(path):
 
 def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int = fe.F64, w=None,
              w_kind: int | None = None, reps: int = 10, chunks=CHUNKS, threads=THREADS, layouts=LAYOUTS,
-             deterministic_only: bool = True, use_cache: bool = True) -> dict:
-    """Best {strategy, chunk, layout, threads, ms} for this mesh class, from the cache or by timing."""
+             deterministic_only: bool = True, use_cache: bool = True, pattern=None, tag: str = "") -> dict:
+    """Best {strategy, chunk, layout, threads, persistent, ms} for this mesh class, from the cache
+    or by timing. pattern(flags) builds the pattern to tune (default fe_pattern(q, me, flags));
+    tag distinguishes mesh classes in the cache key (e.g. batches). q is the coordinate array
+    the assembly reads (for a batch, the union coordinates) and me sizes the element count."""
     if not enabled():
         return dict(DEFAULT)
     if w_kind is None:
         w_kind = fe.COEF_NONE if w is None else fe.COEF_P0
     d, nme = q.shape[0], me.shape[1]
-    key = _key(d, 1, kind, prec, nme)
+    key = _key(d, 1, kind, prec, nme) + (f"|{tag}" if tag else "")
+    if pattern is None:
+        def pattern(flags):
+            return fe.fe_pattern(q, me, flags=flags)
     path = cache_path()
     cache = _load(path)
     if use_cache and key in cache:
@@ -90,24 +101,33 @@ def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int =
     T = torch.float32 if prec == fe.F32 else torch.float64
     if prec == fe.F64X:
         threads = (256,)  # the F64X kernel's block size is fixed; the setting does not reach it
+    shapes = PERSISTENT if kind == "wmass_stiff" else (True,)
     results = []
-    vals = None
+    vals = vals2 = None
     for c in chunks:
         for lay in layouts:
-            p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(c) | lay)
+            p = pattern(fe.PATTERN_CHUNK(c) | lay)
             if vals is None:
                 vals = torch.empty(p.nnz, dtype=T, device=q.device)
+                vals2 = torch.empty(p.nnz, dtype=T, device=q.device) if kind == "wmass_stiff" else None
             for t in threads:
                 p.set_threads(t)
-                ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals), reps)
-                results.append({"strategy": "chunked", "chunk": c, "layout": lay, "threads": t, "ms": ms})
+                for per in shapes:
+                    p.set_persistent(per)
+                    try:
+                        ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals, vals2), reps)
+                    except fe.FEError:  # chunk too large for one block's shared memory
+                        continue
+                    results.append({"strategy": "chunked", "chunk": c, "layout": lay, "threads": t,
+                                    "persistent": per, "ms": ms})
             p.destroy()
     if not deterministic_only:
-        p = fe.fe_pattern(q, me)
+        p = pattern(0)
         for name, s in (("gather", fe.REASM_GATHER), ("atomic", fe.REASM_ATOMIC)):
             p.set_strategy(s)
             ms = _time(lambda: _call(p, q, kind, prec, w, w_kind, vals), reps)
-            results.append({"strategy": name, "chunk": 0, "layout": 0, "threads": 256, "ms": ms})
+            results.append({"strategy": name, "chunk": 0, "layout": 0, "threads": 256, "persistent": True,
+                            "ms": ms})
         p.destroy()
     best = dict(min(results, key=lambda r: r["ms"]))
     best["tried"] = len(results)
@@ -121,12 +141,15 @@ def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int =
     return best
 
 
-def tuned_pattern(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int = fe.F64, **kw) -> fe.Pattern:
-    """A pattern built and configured with the autotuned chunk size, threads and strategy."""
-    best = autotune(q, me, kind=kind, prec=prec, **kw)
+def tuned_pattern(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int = fe.F64, pattern=None,
+                  **kw) -> fe.Pattern:
+    """A pattern built and configured with the autotuned chunk size, threads, launch shape
+    and strategy (pattern: as for autotune)."""
+    best = autotune(q, me, kind=kind, prec=prec, pattern=pattern, **kw)
     strategy = {"chunked": fe.REASM_CHUNKED, "gather": fe.REASM_GATHER, "atomic": fe.REASM_ATOMIC}[best["strategy"]]
     flags = (fe.PATTERN_CHUNK(best["chunk"]) if best["chunk"] else 0) | best.get("layout", 0)
-    p = fe.fe_pattern(q, me, flags=flags)
+    p = fe.fe_pattern(q, me, flags=flags) if pattern is None else pattern(flags)
     p.set_strategy(strategy)
     p.set_threads(best["threads"])
+    p.set_persistent(best.get("persistent", True))
     return p

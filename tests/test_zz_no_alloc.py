@@ -54,6 +54,9 @@ def test_noalloc_rejects_meshes_beyond_its_scratch():
     with pytest.raises(fe.FEError) as e:
         fe.fe_assemble_stiff_noalloc(p, q, vals, prec=fe.F64)
     assert e.value.code == 8
+    with pytest.raises(fe.FEError) as e:  # FE_F64X is not one of its forms
+        fe.fe_assemble_stiff_noalloc(p, q, vals, prec=fe.F64X)
+    assert e.value.code == 1
     vals32 = torch.empty(p.nnz, dtype=torch.float32, device="cuda")  # 8.04 MiB in FP32: fits
     fe.fe_assemble_stiff_noalloc(p, q, vals32, prec=fe.F32)
     expected = fe.fe_assemble_stiff(p, q, prec=fe.F32)
