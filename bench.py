@@ -59,6 +59,8 @@ def parse():
                     help="use the default pattern (chunk 512, count-ordered records, 256 threads) for every "
                          "form instead of the autotuned one")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="headline only: skip the other configurations' block")
     ap.add_argument("--workload", default="stiffness",
                     choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general", "pk",
                              "boundary"],
@@ -165,17 +167,48 @@ def host_cpu():
     return {"model": model or platform.machine(), "logical_cpus": os.cpu_count()}
 
 
-def cpu_baseline(m, sample):
+def cpu_baseline(m, sample, reps=5):
+    """The FP64 oracle on the host cores, on the headline mesh:
+    - value: fixed-pattern reassembly (every element's local matrix, then each nonzero's
+      sum over the oracle's own slot map), like for like with the GPU headline, on all
+      cores, the whole mesh, median of `reps` runs;
+    - beside it: the same on one thread (one run), and the full assembly (element loop,
+      triplet sort, sums: the `sparse` construction) on all cores over the whole mesh
+      and on one thread over the first `sample` tets (one run each).
+    The slot map is built once, untimed (like the GPU pattern)."""
     import oracle
     oracle.build()
-    S = min(sample, m.nme)
-    me = np.ascontiguousarray(m.me[:, :S])
+    cores = oracle.set_threads(os.cpu_count() or 1)
     t0 = time.perf_counter()
-    oracle.assemble(oracle.STIFF, m.q, me)
-    dt = time.perf_counter() - t0
-    return {"value": S / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-            "sample": f"first {S:,} of the {m.nme:,} randomly ordered tets of the same mesh "
-                      f"(element loop + triplet sort-and-sum into CSR, FP64, one thread); {dt:.1f} s"}
+    ptr, n2s = oracle.slot_map(m.me, m.nq)
+    setup = time.perf_counter() - t0
+
+    def timed(fn):
+        t = time.perf_counter()
+        fn()
+        return time.perf_counter() - t
+    reasm = lambda: oracle.reassemble(oracle.STIFF, m.q, m.me, ptr, n2s)
+    timed(reasm)  # warm-up (page faults of the value arrays)
+    runs = sorted(timed(reasm) for _ in range(reps))
+    med = statistics.median(runs)
+    full_all = timed(lambda: oracle.assemble(oracle.STIFF, m.q, m.me))
+    oracle.set_threads(1)
+    reasm_1 = timed(reasm)
+    S = min(sample, m.nme)
+    me_s = np.ascontiguousarray(m.me[:, :S])
+    full_1 = timed(lambda: oracle.assemble(oracle.STIFF, m.q, me_s))
+    del ptr, n2s
+    rate = lambda n, t: n / t / 1e6
+    return {"value": rate(m.nme, med), "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_cpu(),
+            "sample": f"the whole {m.nme:,}-tet mesh: fixed-pattern reassembly (element loop + sums over the "
+                      f"oracle's slot map, FP64), {cores} threads, median of {reps} runs "
+                      f"({', '.join(f'{x:.3f}' for x in runs)} s; slot map built once in {setup:.1f} s, untimed)",
+            "fixed_pattern_1_thread": {"value": rate(m.nme, reasm_1), "cores": 1, "seconds": reasm_1,
+                                       "sample": "whole mesh, one run"},
+            "full_assembly": {"value": rate(m.nme, full_all), "cores": cores, "seconds": full_all,
+                              "sample": "whole mesh (element loop + triplet sort-and-sum into CSR), one run"},
+            "full_assembly_1_thread": {"value": rate(S, full_1), "cores": 1, "seconds": full_1,
+                                       "sample": f"first {S:,} of the {m.nme:,} randomly ordered tets, one run"}}
 
 
 def run_reference(args):
@@ -185,6 +218,7 @@ def run_reference(args):
     import oracle
     from paper_1401_3301_gb300 import meshgen
     oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
     m = meshgen.kuhn_cube_mesh(args.N, seed=0)
     # calibrate: choose a per-step sample so the whole run takes about two minutes
     probe = min(50_000, m.nme)
@@ -211,8 +245,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {**workload_config(args.N), "strategy": "oracle",
-                                            "parallelism": "host, one thread"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+                                            "parallelism": f"host, {cores} threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_cpu(),
                              "sample": f"each step: the first {S:,} of the {m.nme:,} randomly ordered "
                                        "tets (element loop + triplet sort-and-sum, FP64)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -261,18 +295,19 @@ def committed_traffic(form):
         return None
 
 
-def chunk_algorithmic_bytes(p, prec, info, points=None):
+def chunk_algorithmic_bytes(p, prec, info, points=None, block=1, matrices=1, extra_reads=0):
     """Bytes the chunk kernel must move per launch: its plan records (read once), the
     FP64 coordinates (each point once: every vertex, or for P_k only the element
-    vertices), the owned CSR values and the partial sums it writes; counts are exact,
-    from the plan."""
+    vertices), the owned CSR values and the partial sums it writes (block values per
+    vertex or edge entry: m * m for vector problems; `matrices` matrices at once), plus
+    extra_reads (coefficients); counts are exact, from the plan."""
     d = p.d
     npts = p.nq if points is None else points
     sT = 8 if prec == 0 else 4
     lv, le = info["local_vertices"], info["local_edges"]
     pv, pe = info["partial_vertices"], info["partial_edges"]
-    reads = info["plan_bytes"] + 8 * d * npts
-    writes = (lv - pv) * sT + (le - pe) * 2 * sT + (pv + pe) * 8
+    reads = info["plan_bytes"] + 8 * d * npts + extra_reads
+    writes = ((lv - pv) * sT + (le - pe) * 2 * sT + (pv + pe) * 8) * block * matrices
     return reads + writes
 
 
@@ -450,10 +485,15 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return
     sel = forms[args.prec]
+    workloads = None
+    if world == 1 and not args.no_secondary:
+        del pats
+        torch.cuda.empty_cache()
+        workloads = secondary_workloads(fe, torch, flush, hbm_peak)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, args.cpu_sample)
-    roof = sel["roofline_alu"] if args.prec == "f64" else sel["roofline_hbm"]
+    roof = sel["roofline_hbm"]
     line = {"metric": METRIC, "value": sel["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sel["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
@@ -462,8 +502,9 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "nnz": p.nnz, "pattern_build_ms": pattern_ms, "plan": info},
-            "roofline": roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": sel["gpu_launches"], "clocks": clocks}
+            "roofline": roof, "roofline_alu": sel.get("roofline_alu"), "forms": forms, "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": sel["gpu_launches"], "clocks": clocks, "workloads": workloads}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -489,252 +530,388 @@ def _timed(fn, steps, warmup, flush=None):
     return statistics.median(t), sum(t) / len(t)
 
 
+def _forms(fe, torch):
+    return (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32), ("f64x", fe.F64X, torch.float64))
+
+
+def _kernels(p, fn, steps=5, flush=None):
+    """{kernel: ms per launch} of the library's kernels over `steps` calls of fn on
+    pattern p (fe_profile: CUDA events around each launch; L2 flushed between calls)."""
+    p.profile(True)
+    p.profile_read()
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(1)
+        fn()
+    prof = p.profile_read()
+    p.profile(False)
+    return {k: v[0] / v[1] for k, v in prof.items() if v[1]}
+
+
+def _entry(units, ms_mean, ms_median, kern=None, abytes=None, hbm_peak=None, dominant="chunk", **extra):
+    """One form's result: throughput, step time, per-kernel times and, for a chunk kernel
+    with a known byte count, its HBM roofline fraction (algorithmic bytes / kernel time)."""
+    e = {"value": units / (ms_mean * 1e-3) / 1e6, "ms_per_step": ms_mean, "ms_median": ms_median}
+    if kern:
+        e["kernels_ms"] = kern
+        if abytes is not None and dominant in kern:
+            gbs = abytes / (kern[dominant] * 1e-3) / 1e9
+            e["roofline"] = {"bound": "hbm", "kernel": dominant, "algorithmic_bytes_per_launch": abytes,
+                             "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
+    e.update(extra)
+    return e
+
+
+def wl_mass(fe, torch, K, W, flush, hbm_peak, N=100, which=("mass", "wmass")):
+    """3D P1 mass and P1-weighted mass, fixed pattern (the headline mesh)."""
+    from paper_1401_3301_gb300 import meshgen
+    m = meshgen.kuhn_cube_mesh(N, seed=0)
+    q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+    p = fe.fe_pattern(q, me)
+    info = p.plan_info()
+    wv = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
+    out = {}
+    for op in which:
+        res = {}
+        for name, prec, T in _forms(fe, torch):
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            w = wv.to(T)
+            fn = (lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)) if op == "mass" else \
+                 (lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec, vals=vals))
+            med, mean = _timed(fn, K, W, flush)
+            kern = _kernels(p, fn, flush=flush)
+            p.check()
+            ab = chunk_algorithmic_bytes(p, 0 if prec == fe.F64X else prec, info,
+                                         extra_reads=0 if op == "mass" else 8 * m.nq)
+            res[name] = _entry(m.nme, mean, med, kern, ab, hbm_peak)
+        out[op] = {"metric": f"3D P1 {'mass' if op == 'mass' else 'weighted mass (P1 vertex weight)'} Mtets/s, "
+                             "fixed pattern", "unit": "Mtets/s",
+                   "config": workload_config(N, "mass" if op == "mass" else "weighted mass (P1 vertex weight)"),
+                   "forms": res}
+    return out
+
+
+def wl_elas(fe, torch, K, W, flush, hbm_peak, N=80):
+    """3D P1 linear elasticity, 3 dofs per vertex, E = 1, nu = 0.3, with the rigid-mode check."""
+    from paper_1401_3301_gb300 import meshgen
+    m = meshgen.kuhn_cube_mesh(N, seed=0)
+    q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+    t0 = time.perf_counter()
+    p = fe.fe_pattern(q, me, m=3)
+    pms = (time.perf_counter() - t0) * 1e3
+    info = p.plan_info()
+    lam0, mu0 = meshgen.lame_from_young(1.0, 0.3)
+    rp, ci = p.csr()
+    rows = torch.repeat_interleave(torch.arange(p.n, device="cuda"), (rp[1:] - rp[:-1]).long())
+    X = q.T.double()
+    res = {}
+    for name, prec, T in _forms(fe, torch):
+        vals = torch.empty(p.nnz, dtype=T, device="cuda")
+        lam = torch.tensor([lam0], dtype=T, device="cuda")
+        mu = torch.tensor([mu0], dtype=T, device="cuda")
+        fn = lambda: fe.fe_assemble_elas(p, q, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR, prec=prec, vals=vals)
+        med, mean = _timed(fn, K, W, flush)
+        kern = _kernels(p, fn, flush=flush)
+        p.check()
+        # rigid-mode residual: K r for the 6 rigid modes, relative to |K| |r|
+        resid = 0.0
+        for mode in range(6):
+            r = torch.zeros((m.nq, 3), dtype=torch.float64, device="cuda")
+            if mode < 3:
+                r[:, mode] = 1.0
+            else:
+                axis = torch.zeros(3, dtype=torch.float64, device="cuda")
+                axis[mode - 3] = 1.0
+                r = torch.linalg.cross(axis.expand_as(X), X)
+            r = r.reshape(-1)
+            y = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+            y.index_add_(0, rows, vals.double() * r[ci.long()])
+            resid = max(resid, float(y.abs().max() / (vals.double().abs().max() * r.abs().max())))
+        ab = chunk_algorithmic_bytes(p, 0 if prec == fe.F64X else prec, info, block=9)
+        res[name] = _entry(m.nme, mean, med, kern, ab, hbm_peak, dominant="elas_chunk", rigid_mode_residual=resid)
+    return {"metric": "3D P1 linear elasticity (12x12 element blocks) Mtets/s, fixed pattern", "unit": "Mtets/s",
+            "config": {**workload_config(N, "linear elasticity"), "E": 1.0, "nu": 0.3, "nnz": p.nnz,
+                       "pattern_build_ms": pms}, "forms": res}
+
+
+def wl_2d(fe, torch, K, W, flush, hbm_peak, N=100):
+    """2D P1 mass + stiffness (both matrices per step) in one CUDA graph."""
+    from paper_1401_3301_gb300 import meshgen
+    m = meshgen.square_mesh(N, seed=0)
+    q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+    p = fe.fe_pattern(q, me)
+    res = {}
+    for name, prec, T in _forms(fe, torch):
+        v1 = torch.empty(p.nnz, dtype=T, device="cuda")
+        v2 = torch.empty(p.nnz, dtype=T, device="cuda")
+
+        def step():
+            fe.fe_assemble_mass(p, q, prec=prec, vals=v1)
+            fe.fe_assemble_stiff(p, q, prec=prec, vals=v2)
+        step()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        med, mean = _timed(g.replay, K, W)
+        kern = _kernels(p, step)
+        p.check()
+        res[name] = _entry(m.nme, mean, med, kern)
+    return {"metric": "2D P1 mass + stiffness Mtris/s (both matrices per step, CUDA graph)", "unit": "Mtris/s",
+            "config": {"workload": f"unit square N={N}, {m.nme:,} triangles, {m.nq:,} vertices, jitter 0.2h, "
+                                   "vertices and elements permuted", "nnz": p.nnz}, "forms": res}
+
+
+def wl_batched(fe, torch, K, W, flush, hbm_peak, replays=1000, count=256):
+    """The 256-mesh 2D batch: weighted mass + stiffness with fresh lognormal(0, 1)
+    per-element weights every step, one fused persistent kernel (+ one fixup) on the
+    pattern the autotuner picks for the batch, captured with the weight draw in a CUDA
+    graph and replayed `replays` times (the time per replay is reported). The F64X form
+    has no fused kernel and runs the two operators' kernels."""
+    from paper_1401_3301_gb300 import meshgen, tune
+    sizes = meshgen.batch_sizes(0, count, 16, 512)
+    meshes = [meshgen.square_mesh(int(n), seed=b + 1) for b, n in enumerate(sizes)]
+    qs = [torch.from_numpy(mm.q).cuda() for mm in meshes]
+    mes = [torch.from_numpy(mm.me).cuda() for mm in meshes]
+    del meshes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p0 = fe.fe_batch_pattern(qs, mes)
+    pms = (time.perf_counter() - t0) * 1e3
+    vo, eo, _ = fe.fe_batch_offsets(p0)
+    qu = torch.empty((2, int(vo[-1])), dtype=torch.float64, device="cuda")
+    fe.fe_batch_gather_q(p0, qs, mes, qu)
+    ntri = int(eo[-1])
+    res, tuning = {}, {}
+    for name, prec, T in _forms(fe, torch):
+        w = torch.ones(ntri, dtype=T, device="cuda")
+        if prec == fe.F64X:
+            p = p0
+            s_ = torch.empty(p.nnz, dtype=T, device="cuda")
+            m_ = torch.empty(p.nnz, dtype=T, device="cuda")
+
+            def assemble():
+                fe.fe_assemble_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=s_)
+                fe.fe_assemble_wmass(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=m_)
+        else:
+            def make(flags, _qs=qs, _mes=mes):
+                return fe.fe_batch_pattern(_qs, _mes, flags=flags)
+            best = tune.autotune(qu, torch.empty((3, ntri), device="meta"), "wmass_stiff", prec, w=w,
+                                 w_kind=fe.COEF_P0_INTERNAL, pattern=make, tag=f"batch{count}", reps=5)
+            p = tune.tuned_pattern(qu, torch.empty((3, ntri), device="meta"), "wmass_stiff", prec, w=w,
+                                   w_kind=fe.COEF_P0_INTERNAL, pattern=make, tag=f"batch{count}", reps=5)
+            tuning[name] = {k: best.get(k) for k in ("chunk", "layout", "threads", "persistent")}
+            s_ = torch.empty(p.nnz, dtype=T, device="cuda")
+            m_ = torch.empty(p.nnz, dtype=T, device="cuda")
+
+            def assemble():
+                fe.fe_assemble_wmass_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals_mass=m_, vals_stiff=s_)
+        torch.cuda.manual_seed(0)
+
+        def step():
+            # fresh lognormal(0, 1) weights, drawn in FP32 (input data: an FP64 normal
+            # generator would cost more FP64 work than the assembly) and widened to the form
+            w.copy_(torch.randn(w.shape, device="cuda", dtype=torch.float32).exp_())
+            assemble()
+        step()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(W):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(replays):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        mean = e0.elapsed_time(e1) / replays
+        kern = _kernels(p, assemble)
+        p.check()
+        info = p.plan_info()
+        ab = None
+        if prec != fe.F64X:
+            sT = 8 if prec == fe.F64 else 4
+            ab = chunk_algorithmic_bytes(p, prec, info, matrices=2, extra_reads=sT * ntri)
+        res[name] = _entry(ntri, mean, mean, kern, ab, hbm_peak, replays=replays,
+                           launches_per_step=2 if prec != fe.F64X else 4)
+    return {"metric": "Batched 2D weighted mass + stiffness reassembly with fresh lognormal weights, Mtris/s "
+                      f"(CUDA graph, {replays} replays)", "unit": "Mtris/s",
+            "config": {"workload": f"{count} jittered unit-square meshes, N uniform in [16, 512] ({ntri:,} "
+                                   f"triangles, {int(vo[-1]):,} vertices)", "nnz": p0.nnz,
+                       "pattern_build_ms": pms, "tuning": tuning, "replays": replays}, "forms": res}
+
+
+def wl_diff(fe, torch, K, W, flush, hbm_peak, N=64):
+    """3D stiffness K(w) forward + backward: L = u^T K(w) v, dL/dw, dL/dq."""
+    from paper_1401_3301_gb300 import meshgen
+    m = meshgen.kuhn_cube_mesh(N, seed=0)
+    q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+    p = fe.fe_pattern(q, me)
+    w64 = torch.from_numpy(meshgen.element_weights(0, m.nme)).cuda()
+    u64, v64 = (torch.from_numpy(x).cuda() for x in meshgen.random_vectors(0, m.nq))
+    res = {}
+    for name, prec, T in _forms(fe, torch):
+        w, u, v = w64.to(T), u64.to(T), v64.to(T)
+        vals = torch.empty(p.nnz, dtype=T, device="cuda")
+        L = torch.empty(1, dtype=T, device="cuda")
+        dw = torch.empty(m.nme, dtype=T, device="cuda")
+        dq = torch.empty((3, m.nq), dtype=T, device="cuda")
+
+        def step():
+            fe.fe_assemble_stiff(p, q, w, fe.COEF_P0, prec=prec, vals=vals)
+            fe.fe_assemble_stiff_backward(p, q, w, fe.COEF_P0, u, v, L, dw, dq, prec=prec)
+        med, mean = _timed(step, K, W, flush)
+        kern = _kernels(p, step, flush=flush)
+        p.check()
+        res[name] = _entry(m.nme, mean, med, kern)
+    return {"metric": "3D stiffness K(w) forward + backward (L = u^T K v, dL/dw, dL/dq) Mtets/s", "unit": "Mtets/s",
+            "config": workload_config(N, "stiffness forward + backward"), "forms": res}
+
+
+def wl_general(fe, torch, K, W, flush, hbm_peak, N=100):
+    """3D P1 general operator (Eq. EDP), P0 records in internal and input order, P1 records."""
+    from paper_1401_3301_gb300 import meshgen
+    forms = {}
+    # convection-diffusion-reaction operator (non-symmetric), per-element and per-vertex
+    # coefficient sets of 16 values each
+    m = meshgen.kuhn_cube_mesh(N, seed=0)
+    q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+    p = fe.fe_pattern(q, me)
+    c0 = meshgen.general_coefficients(0, 3, m.nme)
+    c1 = meshgen.general_coefficients(1, 3, m.nq)
+    order = p.element_order().long().cpu().numpy()
+    c0i = np.ascontiguousarray(c0[order])
+    for name, prec, T in _forms(fe, torch):
+        vals = torch.empty(p.nnz, dtype=T, device="cuda")
+        res = {}
+        for label, arr, kind in (("p0_internal", c0i, fe.COEF_P0_INTERNAL), ("p0", c0, fe.COEF_P0),
+                                 ("p1", c1, fe.COEF_P1)):
+            cf = torch.from_numpy(arr).cuda().to(T)
+            med, mean = _timed(lambda: fe.fe_assemble_general(p, q, cf, kind, prec=prec, vals=vals), K, W,
+                               flush)
+            p.check()
+            res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+        forms[name] = {"value": res["p0_internal"]["value"], "coefficients": res}
+    return dict(forms=forms, metric="3D P1 general operator -div(A grad u) + div(b u) + c.grad u + a0 u "
+                                    "(non-symmetric) Mtets/s, fixed pattern", unit="Mtets/s",
+                config=workload_config(N, "general operator (Eq. EDP)"))
+
+
+def wl_pk(fe, torch, K, W, flush, hbm_peak):
+    """3D P_k mass (App. D), k = 1..6 at about 10^6 nodes."""
+    from paper_1401_3301_gb300 import meshgen
+    forms = {}
+    # 3D P_k mass (App. D) at the largest size of the paper's P_k table, about 10^6 nodes:
+    # k N = 100 cells per side on the fine lattice, (kN+1)^3 nodes, for k = 1..6
+    for k in range(1, 7):
+        N = {1: 100, 2: 50, 3: 33, 4: 25, 5: 20, 6: 17}[k]
+        m = meshgen.pk_mesh(3, N, k, seed=0)
+        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = fe.fe_pk_pattern(q, me, k)
+        pms = (time.perf_counter() - t0) * 1e3
+        info = p.plan_info()
+        res = {"N": N, "nodes": m.nq, "tets": m.nme, "nnz": p.nnz, "chunk": info["chunk"],
+               "pattern_build_ms": pms}
+        for name, prec, T in _forms(fe, torch):
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            med, mean = _timed(lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals), K, W, flush)
+            p.check()
+            sT = 4 if prec == fe.F32 else 8
+            abytes = chunk_algorithmic_bytes(p, fe.F64 if prec == fe.F64X else prec, info, points=(N + 1) ** 3)
+            res[name] = {"ms_per_step": mean, "ms_median": med, "Mnodes_per_s": m.nq / (mean * 1e-3) / 1e6,
+                         "Mnnz_per_s": p.nnz / (mean * 1e-3) / 1e6,
+                         "algorithmic_bytes": abytes, "GBps": abytes / (mean * 1e-3) / 1e9,
+                         "hbm_frac": abytes / (mean * 1e-3) / 1e9 / hbm_peak, "value_bytes": p.nnz * sT}
+        forms[f"k{k}"] = res
+        del p, vals, q, me
+    forms["f64"] = {"value": forms["k2"]["f64"]["Mnodes_per_s"]}
+    return dict(forms=forms, metric="3D P_k mass (App. D), k = 1..6 at about 10^6 nodes: M nodes/s, fixed "
+                                    "pattern (value: k = 2, FP64)", unit="M nodes/s",
+                config={"workload": "Kuhn cube, P_k lattice nodes, kN ~ 100 (about 1.03e6 nodes), jitter 0.15h, "
+                                    "elements permuted", "hbm_peak_GBps": hbm_peak})
+
+
+def wl_boundary(fe, torch, K, W, flush, hbm_peak, N=2000):
+    """Facet mass and P1-weighted mass of an 8M-triangle surface in 3D, as generated and Morton-renumbered."""
+    from paper_1401_3301_gb300 import meshgen
+    forms = {}
+    # facet (boundary) mass and P1-weighted mass on a large triangulated surface in 3D,
+    # as generated (random vertex numbering) and after fe_morton_vertex_order
+    m = meshgen.surface_mesh(N, seed=0)
+    q0, f0 = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
+    wv0 = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
+    order = fe.fe_morton_vertex_order(q0)
+    q1, f1 = fe.fe_apply_vertex_order(q0, f0, order)
+    numberings = {"as_generated": (q0, f0, wv0), "morton": (q1, f1, wv0[order.long()])}
+    pms = {}
+    for label_n, (q, f, wv) in numberings.items():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = fe.fe_boundary_pattern(q, f)
+        pms[label_n] = (time.perf_counter() - t0) * 1e3
+        for name, prec, T in _forms(fe, torch):
+            vals = torch.empty(p.nnz, dtype=T, device="cuda")
+            w = wv.to(T)
+            res = {}
+            for label, fn in (("mass", lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)),
+                              ("wmass_p1", lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec,
+                                                                        vals=vals))):
+                med, mean = _timed(fn, K, W, flush)
+                p.check()
+                res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
+            forms.setdefault(name, {"value": None, "numbering": {}})["numbering"][label_n] = res
+        nnz = p.nnz
+        del p
+    for name in ("f64", "f32", "f64x"):
+        forms[name]["value"] = forms[name]["numbering"]["morton"]["mass"]["value"]
+    return dict(forms=forms, metric="3D surface (facet) mass and P1-weighted mass, Mtris/s, fixed pattern "
+                                    "(value: Morton vertex numbering, mass)", unit="Mtris/s",
+                config={"workload": f"height-field surface over the unit square, N={N} ({m.nme:,} triangles, "
+                                    f"{m.nq:,} vertices), jitter 0.2h, vertices and elements permuted",
+                        "nnz": nnz, "pattern_build_ms": pms})
+
+
+# the default run prints these beside the headline (shorter runs); --workload X prints one
+SECONDARY = {"mass": wl_mass, "elas": wl_elas, "2d": wl_2d, "batched": wl_batched, "diff": wl_diff}
+ALL_WORKLOADS = {**SECONDARY, "general": wl_general, "pk": wl_pk, "boundary": wl_boundary}
+
+
 def run_other(args):
     import torch
-    from paper_1401_3301_gb300 import build_ext, fe, meshgen
+    from paper_1401_3301_gb300 import build_ext, fe
     build_ext.build()
     fe.lib()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    K, W = args.steps, args.warmup
-    out = {"workload": args.workload, "data": "synthetic", "steps": K, "warmup": W, "n_gpus": 1,
-           "higher_is_better": True, "forms": {}}
-    if args.workload in ("mass", "wmass"):
-        m = meshgen.kuhn_cube_mesh(args.N, seed=0)
-        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-        p = fe.fe_pattern(q, me)
-        wv = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                              ("f64x", fe.F64X, torch.float64)):
-            vals = torch.empty(p.nnz, dtype=T, device="cuda")
-            w = wv.to(T)
-            fn = (lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)) if args.workload == "mass" else \
-                 (lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec, vals=vals))
-            med, mean = _timed(fn, K, W, flush)
-            p.check()
-            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
-        out.update(metric=f"3D P1 {'mass' if args.workload == 'mass' else 'weighted mass (P1 vertex weight)'} "
-                          "Mtets/s, fixed pattern", unit="Mtets/s",
-                   config=workload_config(args.N, "mass" if args.workload == "mass"
-                                          else "weighted mass (P1 vertex weight)"))
-    elif args.workload == "general":
-        # convection-diffusion-reaction operator (non-symmetric), per-element and per-vertex
-        # coefficient sets of 16 values each
-        m = meshgen.kuhn_cube_mesh(args.N, seed=0)
-        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-        p = fe.fe_pattern(q, me)
-        c0 = meshgen.general_coefficients(0, 3, m.nme)
-        c1 = meshgen.general_coefficients(1, 3, m.nq)
-        order = p.element_order().long().cpu().numpy()
-        c0i = np.ascontiguousarray(c0[order])
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                              ("f64x", fe.F64X, torch.float64)):
-            vals = torch.empty(p.nnz, dtype=T, device="cuda")
-            res = {}
-            for label, arr, kind in (("p0_internal", c0i, fe.COEF_P0_INTERNAL), ("p0", c0, fe.COEF_P0),
-                                     ("p1", c1, fe.COEF_P1)):
-                cf = torch.from_numpy(arr).cuda().to(T)
-                med, mean = _timed(lambda: fe.fe_assemble_general(p, q, cf, kind, prec=prec, vals=vals), K, W,
-                                   flush)
-                p.check()
-                res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
-            out["forms"][name] = {"value": res["p0_internal"]["value"], "coefficients": res}
-        out.update(metric="3D P1 general operator -div(A grad u) + div(b u) + c.grad u + a0 u (non-symmetric) "
-                          "Mtets/s, fixed pattern", unit="Mtets/s",
-                   config=workload_config(args.N, "general operator (Eq. EDP)"))
-    elif args.workload == "pk":
-        # 3D P_k mass (App. D) at the largest size of the paper's P_k table, about 10^6 nodes:
-        # k N = 100 cells per side on the fine lattice, (kN+1)^3 nodes, for k = 1..6
-        hbm_peak, _, _ = measured_peaks()
-        for k in range(1, 7):
-            N = {1: 100, 2: 50, 3: 33, 4: 25, 5: 20, 6: 17}[k]
-            m = meshgen.pk_mesh(3, N, k, seed=0)
-            q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            p = fe.fe_pk_pattern(q, me, k)
-            pms = (time.perf_counter() - t0) * 1e3
-            info = p.plan_info()
-            res = {"N": N, "nodes": m.nq, "tets": m.nme, "nnz": p.nnz, "chunk": info["chunk"],
-                   "pattern_build_ms": pms}
-            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                                  ("f64x", fe.F64X, torch.float64)):
-                vals = torch.empty(p.nnz, dtype=T, device="cuda")
-                med, mean = _timed(lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals), K, W, flush)
-                p.check()
-                sT = 4 if prec == fe.F32 else 8
-                abytes = chunk_algorithmic_bytes(p, fe.F64 if prec == fe.F64X else prec, info, points=(N + 1) ** 3)
-                res[name] = {"ms_per_step": mean, "ms_median": med, "Mnodes_per_s": m.nq / (mean * 1e-3) / 1e6,
-                             "Mnnz_per_s": p.nnz / (mean * 1e-3) / 1e6,
-                             "algorithmic_bytes": abytes, "GBps": abytes / (mean * 1e-3) / 1e9,
-                             "hbm_frac": abytes / (mean * 1e-3) / 1e9 / hbm_peak, "value_bytes": p.nnz * sT}
-            out["forms"][f"k{k}"] = res
-            del p, vals, q, me
-        out["forms"]["f64"] = {"value": out["forms"]["k2"]["f64"]["Mnodes_per_s"]}
-        out.update(metric="3D P_k mass (App. D), k = 1..6 at about 10^6 nodes: M nodes/s, fixed pattern "
-                          "(value: k = 2, FP64)", unit="M nodes/s",
-                   config={"workload": "Kuhn cube, P_k lattice nodes, kN ~ 100 (about 1.03e6 nodes), jitter 0.15h, "
-                                       "elements permuted", "hbm_peak_GBps": hbm_peak})
-    elif args.workload == "boundary":
-        # facet (boundary) mass and P1-weighted mass on a large triangulated surface in 3D,
-        # as generated (random vertex numbering) and after fe_morton_vertex_order
-        N = 2000 if args.N == 100 else args.N
-        m = meshgen.surface_mesh(N, seed=0)
-        q0, f0 = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-        wv0 = torch.from_numpy(meshgen.vertex_weights(0, m.nq)).cuda()
-        order = fe.fe_morton_vertex_order(q0)
-        q1, f1 = fe.fe_apply_vertex_order(q0, f0, order)
-        numberings = {"as_generated": (q0, f0, wv0), "morton": (q1, f1, wv0[order.long()])}
-        pms = {}
-        for label_n, (q, f, wv) in numberings.items():
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            p = fe.fe_boundary_pattern(q, f)
-            pms[label_n] = (time.perf_counter() - t0) * 1e3
-            for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                                  ("f64x", fe.F64X, torch.float64)):
-                vals = torch.empty(p.nnz, dtype=T, device="cuda")
-                w = wv.to(T)
-                res = {}
-                for label, fn in (("mass", lambda: fe.fe_assemble_mass(p, q, prec=prec, vals=vals)),
-                                  ("wmass_p1", lambda: fe.fe_assemble_wmass(p, q, w, fe.COEF_P1, prec=prec,
-                                                                            vals=vals))):
-                    med, mean = _timed(fn, K, W, flush)
-                    p.check()
-                    res[label] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
-                out["forms"].setdefault(name, {"value": None, "numbering": {}})["numbering"][label_n] = res
-            nnz = p.nnz
-            del p
-        for name in ("f64", "f32", "f64x"):
-            out["forms"][name]["value"] = out["forms"][name]["numbering"]["morton"]["mass"]["value"]
-        out.update(metric="3D surface (facet) mass and P1-weighted mass, Mtris/s, fixed pattern (value: Morton "
-                          "vertex numbering, mass)", unit="Mtris/s",
-                   config={"workload": f"height-field surface over the unit square, N={N} ({m.nme:,} triangles, "
-                                       f"{m.nq:,} vertices), jitter 0.2h, vertices and elements permuted",
-                           "nnz": nnz, "pattern_build_ms": pms})
-    elif args.workload == "elas":
-        N = 80 if args.N == 100 else args.N
-        m = meshgen.kuhn_cube_mesh(N, seed=0)
-        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-        t0 = time.perf_counter()
-        p = fe.fe_pattern(q, me, m=3)
-        pms = (time.perf_counter() - t0) * 1e3
-        lam0, mu0 = meshgen.lame_from_young(1.0, 0.3)
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                              ("f64x", fe.F64X, torch.float64)):
-            vals = torch.empty(p.nnz, dtype=T, device="cuda")
-            lam = torch.tensor([lam0], dtype=T, device="cuda")
-            mu = torch.tensor([mu0], dtype=T, device="cuda")
-            med, mean = _timed(lambda: fe.fe_assemble_elas(p, q, lam, fe.COEF_SCALAR, mu, fe.COEF_SCALAR,
-                                                          prec=prec, vals=vals), K, W, flush)
-            p.check()
-            # rigid-mode residual: K r for the 6 rigid modes, relative to |K| |r|
-            rp, ci = p.csr()
-            rows = torch.repeat_interleave(torch.arange(p.n, device="cuda"), (rp[1:] - rp[:-1]).long())
-            X = q.T.double()
-            res = 0.0
-            for mode in range(6):
-                r = torch.zeros((m.nq, 3), dtype=torch.float64, device="cuda")
-                if mode < 3:
-                    r[:, mode] = 1.0
-                else:
-                    axis = torch.zeros(3, dtype=torch.float64, device="cuda")
-                    axis[mode - 3] = 1.0
-                    r = torch.linalg.cross(axis.expand_as(X), X)
-                r = r.reshape(-1)
-                y = torch.zeros(p.n, dtype=torch.float64, device="cuda")
-                y.index_add_(0, rows, vals.double() * r[ci.long()])
-                res = max(res, float(y.abs().max() / (vals.double().abs().max() * r.abs().max())))
-            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6,
-                                  "rigid_mode_residual": res}
-        out.update(metric="3D P1 linear elasticity (12x12 element blocks) Mtets/s, fixed pattern", unit="Mtets/s",
-                   config={**workload_config(N, "linear elasticity"), "E": 1.0, "nu": 0.3, "nnz": p.nnz,
-                           "pattern_build_ms": pms})
-    elif args.workload == "2d":
-        m = meshgen.square_mesh(100, seed=0)
-        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-        p = fe.fe_pattern(q, me)
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                              ("f64x", fe.F64X, torch.float64)):
-            v1 = torch.empty(p.nnz, dtype=T, device="cuda")
-            v2 = torch.empty(p.nnz, dtype=T, device="cuda")
+    hbm_peak, _, _ = measured_peaks()
+    name = "mass" if args.workload in ("mass", "wmass") else args.workload
+    res = ALL_WORKLOADS[name](fe, torch, args.steps, args.warmup, flush, hbm_peak)
+    outs = res.values() if name == "mass" else [res]
+    for out in outs:
+        line = {"workload": name, "data": "synthetic", "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
+                "higher_is_better": True, **out}
+        line["value"] = out["forms"]["f64"]["value"]
+        line["dtype"] = "f64"
+        print(json.dumps(line), flush=True)
 
-            def step():
-                fe.fe_assemble_mass(p, q, prec=prec, vals=v1)
-                fe.fe_assemble_stiff(p, q, prec=prec, vals=v2)
-            step()
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                step()
-            med, mean = _timed(g.replay, K, W)
-            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
-        out.update(metric="2D P1 mass + stiffness Mtris/s (both matrices per step, CUDA graph)", unit="Mtris/s",
-                   config={"workload": "unit square N=100, 20,000 triangles, 10,201 vertices, jitter 0.2h, "
-                                       "vertices and elements permuted", "nnz": p.nnz})
-    elif args.workload == "batched":
-        sizes = meshgen.batch_sizes(0, 256, 16, 512)
-        meshes = [meshgen.square_mesh(int(n), seed=b + 1) for b, n in enumerate(sizes)]
-        qs = [torch.from_numpy(mm.q).cuda() for mm in meshes]
-        mes = [torch.from_numpy(mm.me).cuda() for mm in meshes]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        p = fe.fe_batch_pattern(qs, mes)
-        pms = (time.perf_counter() - t0) * 1e3
-        vo, eo, _ = fe.fe_batch_offsets(p)
-        qu = torch.empty((2, int(vo[-1])), dtype=torch.float64, device="cuda")
-        fe.fe_batch_gather_q(p, qs, mes, qu)
-        del qs, mes
-        ntri = int(eo[-1])
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                              ("f64x", fe.F64X, torch.float64)):
-            w = torch.ones(ntri, dtype=T, device="cuda")
-            s = torch.empty(p.nnz, dtype=T, device="cuda")
-            mm_ = torch.empty(p.nnz, dtype=T, device="cuda")
-            torch.cuda.manual_seed(0)
 
-            def step():
-                # fresh lognormal(0, 1) weights, drawn in FP32 (input data: an FP64 normal
-                # generator would cost more FP64 work than the assembly) and widened to the form
-                w.copy_(torch.randn(w.shape, device="cuda", dtype=torch.float32).exp_())
-                fe.fe_assemble_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=s)
-                fe.fe_assemble_wmass(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=mm_)
-            step()
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                step()
-            med, mean = _timed(g.replay, K, W)
-            p.check()
-            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": ntri / (mean * 1e-3) / 1e6}
-        out.update(metric="Batched 2D weighted mass + stiffness reassembly with fresh lognormal weights, "
-                          "Mtris/s (CUDA graph replay)", unit="Mtris/s",
-                   config={"workload": f"256 jittered unit-square meshes, N uniform in [16, 512] "
-                                       f"({ntri:,} triangles, {int(vo[-1]):,} vertices)", "nnz": p.nnz,
-                           "pattern_build_ms": pms})
-    elif args.workload == "diff":
-        N = 64 if args.N == 100 else args.N
-        m = meshgen.kuhn_cube_mesh(N, seed=0)
-        q, me = torch.from_numpy(m.q).cuda(), torch.from_numpy(m.me).cuda()
-        p = fe.fe_pattern(q, me)
-        w64 = torch.from_numpy(meshgen.element_weights(0, m.nme)).cuda()
-        u64, v64 = (torch.from_numpy(x).cuda() for x in meshgen.random_vectors(0, m.nq))
-        for name, prec, T in (("f64", fe.F64, torch.float64), ("f32", fe.F32, torch.float32),
-                              ("f64x", fe.F64X, torch.float64)):
-            w, u, v = w64.to(T), u64.to(T), v64.to(T)
-            vals = torch.empty(p.nnz, dtype=T, device="cuda")
-            L = torch.empty(1, dtype=T, device="cuda")
-            dw = torch.empty(m.nme, dtype=T, device="cuda")
-            dq = torch.empty((3, m.nq), dtype=T, device="cuda")
-
-            def step():
-                fe.fe_assemble_stiff(p, q, w, fe.COEF_P0, prec=prec, vals=vals)
-                fe.fe_assemble_stiff_backward(p, q, w, fe.COEF_P0, u, v, L, dw, dq, prec=prec)
-            med, mean = _timed(step, K, W, flush)
-            p.check()
-            out["forms"][name] = {"ms_per_step": mean, "ms_median": med, "value": m.nme / (mean * 1e-3) / 1e6}
-        out.update(metric="3D stiffness K(w) forward + backward (L = u^T K v, dL/dw, dL/dq) Mtets/s",
-                   unit="Mtets/s", config={**workload_config(N, "stiffness forward + backward")})
-    out["value"] = out["forms"]["f64"]["value"]
-    out["dtype"] = "f64"
-    print(json.dumps(out), flush=True)
+def secondary_workloads(fe, torch, flush, hbm_peak, steps=20, warmup=3):
+    """The other configurations of the hot path, measured compactly for the headline line:
+    per workload and form the throughput, step time, per-kernel times and the dominant
+    kernel's HBM fraction."""
+    out = {}
+    for name, fn in SECONDARY.items():
+        try:
+            r = fn(fe, torch, steps, warmup, flush, hbm_peak)
+        except Exception as e:  # noqa: BLE001 - a failed secondary workload must not lose the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        for key, val in (r.items() if name == "mass" else [(name, r)]):
+            out[key] = val
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():

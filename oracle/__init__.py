@@ -32,11 +32,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, -O2, no vectorisation flags) if it is missing or stale."""
+    """Compile the oracle (plain C, -O2, no vectorisation flags; with OpenMP where the
+    compiler has it, for the threaded timing runs) if it is missing or stale."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:3] + ["-fopenmp"] + base[3:], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,6 +63,10 @@ def _load():
         lib.orc_assemble_table.argtypes = [I32, I64, I64, I32, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_pattern.argtypes = [I32, I32, I64, I64, P, P, P, P, P]
         lib.orc_free.argtypes = [P]
+        lib.orc_set_threads.argtypes = [I32]
+        lib.orc_openmp.restype = I32
+        lib.orc_slot_map.argtypes = [I32, I32, I64, I64, P, P, P, P, P]
+        lib.orc_reassemble.argtypes = [I32, I32, I64, I64, P, P, I32, P, I32, P, I64, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -177,6 +185,55 @@ def pattern(me: np.ndarray, nq: int, m: int = 1) -> tuple:
     lib.orc_free(rp)
     lib.orc_free(ci)
     return row_ptr, col_idx
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's element loops and sorts (1 by default; without OpenMP in
+    the build always 1). Results do not depend on it. Returns the count in effect."""
+    lib = _load()
+    n = max(1, int(n)) if lib.orc_openmp() else 1
+    lib.orc_set_threads(n)
+    return n
+
+
+def slot_map(me: np.ndarray, nq: int, m: int = 1) -> tuple:
+    """(nnz_ptr, nnz2slot) int64: the element slots k ns + slot of each nonzero, in the
+    order orc_assemble sums them (see fe_oracle.c, orc_slot_map)."""
+    me = np.ascontiguousarray(me, dtype=np.int32)
+    d = me.shape[0] - 1
+    nnz, bad = C.c_int64(), C.c_int64()
+    pp, ps = C.c_void_p(), C.c_void_p()
+    lib = _load()
+    rc = lib.orc_slot_map(d, m, nq, me.shape[1], _ptr(me), C.byref(nnz), C.byref(pp), C.byref(ps), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+    nt = me.shape[1] * (m * (d + 1)) ** 2
+    ptr = np.array(np.ctypeslib.as_array(C.cast(pp, C.POINTER(C.c_int64)), shape=(nnz.value + 1,)), dtype=np.int64)
+    n2s = np.array(np.ctypeslib.as_array(C.cast(ps, C.POINTER(C.c_int64)), shape=(max(nt, 1),))[:nt], dtype=np.int64)
+    lib.orc_free(pp)
+    lib.orc_free(ps)
+    return ptr, n2s
+
+
+def reassemble(kind: int, q: np.ndarray, me: np.ndarray, nnz_ptr: np.ndarray, nnz2slot: np.ndarray,
+               c1=None, c2=None) -> np.ndarray:
+    """Fixed-pattern reassembly: the values of assemble(kind, q, me, c1, c2) from the slot
+    map of slot_map(me, nq), bit for bit."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    me = np.ascontiguousarray(me, dtype=np.int32)
+    d, nq = q.shape
+    k1, a1 = _coef(c1)
+    k2, a2 = _coef(c2)
+    nnz = len(nnz_ptr) - 1
+    val = np.empty(nnz)
+    bad = C.c_int64()
+    ptr = np.ascontiguousarray(nnz_ptr, dtype=np.int64)
+    n2s = np.ascontiguousarray(nnz2slot, dtype=np.int64)
+    rc = _load().orc_reassemble(kind, d, nq, me.shape[1], _ptr(q), _ptr(me), k1, _ptr(a1), k2, _ptr(a2), nnz,
+                                _ptr(ptr), _ptr(n2s), _ptr(val), C.byref(bad))
+    if rc:
+        raise OracleError(rc, bad.value)
+    return val
 
 
 def facet_measure(X: np.ndarray) -> float:

@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG 1
@@ -50,6 +53,64 @@
 #define ORC_COEF_SCALAR 1 /* one value */
 #define ORC_COEF_P0 2     /* one value per element */
 #define ORC_COEF_P1 3     /* one value per vertex, P1-interpolated */
+
+/* Threads of the element loops and sorts (1 unless orc_set_threads is called on a build
+ * with OpenMP). Every result is independent of it: each element writes its own
+ * triplets, and the sort order is a total order. */
+static int g_threads = 1;
+
+int orc_openmp(void) {
+#ifdef _OPENMP
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+/* Sort n records of `size` bytes by cmp: qsort, or with several threads, qsort of one
+ * slice per thread and then rounds of pairwise merges of neighbouring sorted runs. */
+static int sort_records(void* base, int64_t n, size_t size, int (*cmp)(const void*, const void*)) {
+  int T = g_threads;
+  if (T <= 1 || n < 2 * (int64_t)T) {
+    qsort(base, (size_t)n, size, cmp);
+    return ORC_OK;
+  }
+  char* a = (char*)base;
+  char* b = (char*)malloc((size_t)n * size);
+  if (!b) return ORC_ERR_NOMEM;
+  int64_t* bound = (int64_t*)malloc(sizeof(int64_t) * (size_t)(T + 1));
+  if (!bound) { free(b); return ORC_ERR_NOMEM; }
+  for (int i = 0; i <= T; ++i) bound[i] = n * i / T;
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+  for (int i = 0; i < T; ++i) qsort(a + bound[i] * size, (size_t)(bound[i + 1] - bound[i]), size, cmp);
+  for (int width = 1; width < T; width *= 2) {
+    const int pairs = (T + 2 * width - 1) / (2 * width);
+#pragma omp parallel for num_threads(T) schedule(dynamic, 1)
+    for (int pi = 0; pi < pairs; ++pi) {
+      const int lo = pi * 2 * width, mid = lo + width < T ? lo + width : T;
+      const int hi = lo + 2 * width < T ? lo + 2 * width : T;
+      int64_t i = bound[lo], j = bound[mid], o = bound[lo];
+      const int64_t ie = bound[mid], je = bound[hi];
+      while (i < ie && j < je) {
+        if (cmp(a + j * size, a + i * size) < 0) { memcpy(b + o * size, a + j * size, size); ++j; }
+        else { memcpy(b + o * size, a + i * size, size); ++i; }
+        ++o;
+      }
+      if (i < ie) memcpy(b + o * size, a + i * size, (size_t)(ie - i) * size), o += ie - i;
+      if (j < je) memcpy(b + o * size, a + j * size, (size_t)(je - j) * size);
+    }
+    char* t = a; a = b; b = t;
+  }
+  if (a != (char*)base) {
+    memcpy(base, a, (size_t)n * size);
+    b = a;
+  }
+  free(b);
+  free(bound);
+  return ORC_OK;
+}
 
 static double factorial(int n) {
   double f = 1.0;
@@ -275,7 +336,7 @@ static int cmp_triplet(const void* pa, const void* pb) {
  * absolute values (abssum), the scale of a cancelling sum's rounding error. */
 static int triplets_to_csr(triplet* t, int64_t nt, int64_t n, int64_t** row_ptr, int32_t** col_idx,
                            double** val, double** scale, double** abssum, int64_t* nnz_out) {
-  qsort(t, (size_t)nt, sizeof(triplet), cmp_triplet);
+  if (sort_records(t, nt, sizeof(triplet), cmp_triplet)) return ORC_ERR_NOMEM;
   int64_t nnz = 0;
   for (int64_t i = 0; i < nt; ++i)
     if (i == 0 || t[i].row != t[i - 1].row || t[i].col != t[i - 1].col) ++nnz;
@@ -325,19 +386,28 @@ int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, cons
   int64_t nt = nme * ns;
   triplet* t = (triplet*)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(triplet));
   if (!t) return ORC_ERR_NOMEM;
-  double X[12], cv1[4], cv2[4], E[144], S[144];
   int rc = ORC_OK;
-  for (int64_t k = 0; k < nme && rc == ORC_OK; ++k) {
-    for (int a = 0; a < nv; ++a) {
+  /* elements are independent; an error reports the smallest failing element */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+  for (int64_t k = 0; k < nme; ++k) {
+    double X[12], cv1[4], cv2[4], E[144], S[144];
+    int erc = ORC_OK;
+    for (int a = 0; a < nv && !erc; ++a) {
       int32_t v = me[(int64_t)a * nme + k];
-      if (v < 0 || v >= nq) { *bad_id = k; rc = ORC_ERR_INDEX; break; }
-      for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
+      if (v < 0 || v >= nq) erc = ORC_ERR_INDEX;
+      else
+        for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
     }
-    if (rc) break;
-    coef_values(c1_kind, c1, d, nme, me, k, cv1);
-    coef_values(c2_kind, c2, d, nme, me, k, cv2);
-    rc = orc_element(kind, d, X, cv1, cv2, E, S);
-    if (rc) { *bad_id = k; break; }
+    if (!erc) {
+      coef_values(c1_kind, c1, d, nme, me, k, cv1);
+      coef_values(c2_kind, c2, d, nme, me, k, cv2);
+      erc = orc_element(kind, d, X, cv1, cv2, E, S);
+    }
+    if (erc) {
+#pragma omp critical
+      if (*bad_id < 0 || k < *bad_id) { *bad_id = k; rc = erc; }
+      continue;
+    }
     for (int j = 0; j < nl; ++j)
       for (int i = 0; i < nl; ++i) {
         triplet* p = &t[k * ns + j * nl + i];
@@ -359,6 +429,109 @@ int orc_assemble(int kind, int d, int64_t nq, int64_t nme, const double* q, cons
 }
 
 void orc_free(void* p) { free(p); }
+
+typedef struct {
+  uint64_t key;  /* row * n + column */
+  int64_t slot;  /* k * ns + local slot (column-wise local order) */
+} slot_key;
+
+static int cmp_slot_key(const void* pa, const void* pb) {
+  const slot_key* a = (const slot_key*)pa;
+  const slot_key* b = (const slot_key*)pb;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->slot < b->slot ? -1 : (a->slot > b->slot ? 1 : 0);
+}
+
+/*
+ * The slot map of the `sparse` step for a fixed pattern: the element slots (k, local
+ * slot), numbered k ns + slot with ns = (m (d+1))^2 in the column-wise local order of
+ * orc_assemble, sorted by (row, column, element, slot) as orc_assemble sorts its
+ * triplets. nnz_ptr[j] .. nnz_ptr[j+1] are the slots of the j-th nonzero (CSR order), in
+ * the order their contributions are summed; nnz2slot lists them. malloc'ed arrays; the
+ * caller frees them with orc_free.
+ */
+int orc_slot_map(int d, int m, int64_t nq, int64_t nme, const int32_t* me, int64_t* nnz_out,
+                 int64_t** nnz_ptr, int64_t** nnz2slot, int64_t* bad_id) {
+  *bad_id = -1;
+  if (d < 1 || d > 3 || m < 1 || nq < 0 || nme < 0) return ORC_ERR_ARG;
+  const int nv = d + 1, nl = m * nv, ns = nl * nl;
+  const int64_t n = (int64_t)m * nq, nt = nme * ns;
+  slot_key* t = (slot_key*)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(slot_key));
+  if (!t) return ORC_ERR_NOMEM;
+  for (int64_t k = 0; k < nme; ++k)
+    for (int j = 0; j < nl; ++j)
+      for (int i = 0; i < nl; ++i) {
+        const int32_t va = me[(int64_t)(i / m) * nme + k], vb = me[(int64_t)(j / m) * nme + k];
+        if (va < 0 || va >= nq || vb < 0 || vb >= nq) { *bad_id = k; free(t); return ORC_ERR_INDEX; }
+        const int64_t row = (int64_t)m * va + i % m, col = (int64_t)m * vb + j % m;
+        t[k * ns + j * nl + i].key = (uint64_t)row * (uint64_t)n + (uint64_t)col;
+        t[k * ns + j * nl + i].slot = k * ns + j * nl + i;
+      }
+  if (sort_records(t, nt, sizeof(slot_key), cmp_slot_key)) { free(t); return ORC_ERR_NOMEM; }
+  int64_t nnz = 0;
+  for (int64_t i = 0; i < nt; ++i)
+    if (i == 0 || t[i].key != t[i - 1].key) ++nnz;
+  *nnz_ptr = (int64_t*)malloc((size_t)(nnz + 1) * sizeof(int64_t));
+  *nnz2slot = (int64_t*)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(int64_t));
+  if (!*nnz_ptr || !*nnz2slot) { free(t); return ORC_ERR_NOMEM; }
+  int64_t j = 0;
+  for (int64_t i = 0; i < nt; ++i) {
+    if (i == 0 || t[i].key != t[i - 1].key) (*nnz_ptr)[j++] = i;
+    (*nnz2slot)[i] = t[i].slot;
+  }
+  (*nnz_ptr)[nnz] = nt;
+  free(t);
+  *nnz_out = nnz;
+  return ORC_OK;
+}
+
+/*
+ * Fixed-pattern reassembly: every element's local matrix (orc_element, into an
+ * element-major array of nme ns values), then each nonzero's sum over its slots in the
+ * order of the slot map (orc_slot_map), into val (nnz doubles). The sums run in the order
+ * of orc_assemble's, so the values equal its values bit for bit, whatever the thread count.
+ * On error *bad_id is the smallest failing element.
+ */
+int orc_reassemble(int kind, int d, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                   int c1_kind, const double* c1, int c2_kind, const double* c2, int64_t nnz,
+                   const int64_t* nnz_ptr, const int64_t* nnz2slot, double* val, int64_t* bad_id) {
+  *bad_id = -1;
+  if (d < 1 || d > 3 || nq < 0 || nme < 0) return ORC_ERR_ARG;
+  const int m = (kind == ORC_ELAS) ? d : 1;
+  const int nv = d + 1, nl = m * nv, ns = nl * nl;
+  double* kg = (double*)malloc((size_t)(nme * ns > 0 ? nme * ns : 1) * sizeof(double));
+  if (!kg) return ORC_ERR_NOMEM;
+  int rc = ORC_OK;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+  for (int64_t k = 0; k < nme; ++k) {
+    double X[12], cv1[4], cv2[4], S[144];
+    int erc = ORC_OK;
+    for (int a = 0; a < nv && !erc; ++a) {
+      const int32_t v = me[(int64_t)a * nme + k];
+      if (v < 0 || v >= nq) erc = ORC_ERR_INDEX;
+      else
+        for (int c = 0; c < d; ++c) X[a * d + c] = q[(int64_t)c * nq + v];
+    }
+    if (!erc) {
+      coef_values(c1_kind, c1, d, nme, me, k, cv1);
+      coef_values(c2_kind, c2, d, nme, me, k, cv2);
+      erc = orc_element(kind, d, X, cv1, cv2, kg + k * ns, S);
+    }
+    if (erc) {
+#pragma omp critical
+      if (*bad_id < 0 || k < *bad_id) { *bad_id = k; rc = erc; }
+    }
+  }
+  if (rc) { free(kg); return rc; }
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+  for (int64_t j = 0; j < nnz; ++j) {
+    double s = 0.0;
+    for (int64_t i = nnz_ptr[j]; i < nnz_ptr[j + 1]; ++i) s += kg[nnz2slot[i]];
+    val[j] = s;
+  }
+  free(kg);
+  return ORC_OK;
+}
 
 static int cmp_u64(const void* pa, const void* pb) {
   const uint64_t a = *(const uint64_t*)pa, b = *(const uint64_t*)pb;

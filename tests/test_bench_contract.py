@@ -39,14 +39,15 @@ def test_gpu_arm_line():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    d = run_bench("--N", "24", "--steps", "4", "--warmup", "3", "--no-tune")
+    d = run_bench("--N", "24", "--steps", "4", "--warmup", "3", "--no-tune", "--no-secondary")
     assert BASE_KEYS <= set(d)
     assert d["value"] > 0 and d["n_gpus"] == 1 and d["dtype"] == "f64" and d["data"] == "synthetic"
     assert d["scaling"] == "weak" and d["vs_baseline"] is None
     assert "l2" in d["config"] and d["config"]["workload"].startswith("3D P1 stiffness")
     r = d["roofline"]
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(r)
-    assert r["bound"] in ("hbm", "alu", "tensor") and r["achieved"] > 0 and r["peak"] > 0
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["achieved"] > 0 and r["peak"] > 0
+    assert d["roofline_alu"]["bound"] == "alu"  # the FP64 form's FP64-pipe fraction beside it
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
@@ -54,3 +55,16 @@ def test_gpu_arm_line():
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     assert {"f64", "f32", "f64x"} <= set(d["forms"])
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] > 0
+
+
+@pytest.mark.gpu
+def test_gpu_workload_line():
+    pytest.importorskip("torch")
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = run_bench("--workload", "2d", "--steps", "3", "--warmup", "2")
+    assert d["workload"] == "2d" and d["value"] > 0 and d["unit"] == "Mtris/s"
+    for form in ("f64", "f32", "f64x"):
+        f = d["forms"][form]
+        assert f["value"] > 0 and f["ms_per_step"] > 0 and "chunk" in f["kernels_ms"]

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_1401_3301_gb300 import meshgen
+from helpers import exact_p1_matrices
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -312,40 +313,6 @@ def test_pattern_alone_against_dense_adjacency(d, m_dofs):
     np.testing.assert_array_equal(ci, res["col_idx"])
 
 
-def exact_p1_matrices(q, me):
-    """Stiffness and mass entries of a P1 mesh in exact rational arithmetic: the coordinates
-    are taken as the exact rationals the doubles are, c_a the rows of adj(B) (c_0 = -sum),
-    stiffness |K| g_a.g_b = c_a.c_b / (d! |det B|), mass |det B| (1 + delta) / (d+2)!.
-    Returns {(i, j): [stiffness, mass, sum |stiffness contributions|]}."""
-    d = q.shape[0]
-    out = {}
-    for k in range(me.shape[1]):
-        v = [int(x) for x in me[:, k]]
-        X = [[Fraction(float(q[c, x])) for c in range(d)] for x in v]
-        B = [[X[i + 1][c] - X[0][c] for i in range(d)] for c in range(d)]  # column i = edge i
-        if d == 2:
-            det = B[0][0] * B[1][1] - B[0][1] * B[1][0]
-            adj = [[B[1][1], -B[0][1]], [-B[1][0], B[0][0]]]           # adj(B)
-        else:
-            det = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1])
-                   - B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0])
-                   + B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0]))
-            adj = [[(B[(j + 1) % 3][(i + 1) % 3] * B[(j + 2) % 3][(i + 2) % 3]
-                     - B[(j + 1) % 3][(i + 2) % 3] * B[(j + 2) % 3][(i + 1) % 3]) for j in range(3)]
-                   for i in range(3)]
-        c = [[-sum(adj[i][j] for i in range(d)) for j in range(d)]] + [adj[i] for i in range(d)]
-        fd, f2 = math.factorial(d), math.factorial(d + 2)
-        for a in range(d + 1):
-            for b in range(d + 1):
-                s = sum(c[a][j] * c[b][j] for j in range(d)) / (fd * abs(det))
-                mval = abs(det) * (2 if a == b else 1) / f2
-                e = out.setdefault((v[a], v[b]), [Fraction(0), Fraction(0), Fraction(0)])
-                e[0] += s
-                e[1] += mval
-                e[2] += abs(s)
-    return out
-
-
 @pytest.mark.parametrize("d,N", [(2, 6), (3, 3)])
 def test_values_against_exact_rational_arithmetic(d, N):
     # the oracle's FP64 sums against the exactly computed matrices of the same (double)
@@ -370,6 +337,43 @@ def test_values_against_exact_rational_arithmetic(d, N):
     zero = a_ex == 0
     assert np.all(rs["val"][zero] == 0) and np.all(rs["abssum"][zero] == 0)
     assert np.max(np.abs(rs["val"] - s_ex)[~zero] / a_ex[~zero]) <= 1e-13
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_fixed_pattern_reassembly_and_threads(d):
+    # the slot map's sums reproduce orc_assemble bit for bit, and neither the threaded
+    # element loops nor the threaded sort change a bit (where the build has OpenMP)
+    m = meshgen.square_mesh(9, seed=34) if d == 2 else meshgen.kuhn_cube_mesh(4, seed=34)
+    w = meshgen.element_weights(34, m.nme)
+    ref = oracle.assemble(oracle.STIFF, m.q, m.me, c1=(oracle.COEF_P0, w))
+    ptr, n2s = oracle.slot_map(m.me, m.nq)
+    assert len(ptr) == ref["nnz"] + 1 and sorted(n2s.tolist()) == list(range(m.nme * (d + 1) ** 2))
+    # the slots of each nonzero name that (row, column): slot k ns + b (d+1) + a is (me[a,k], me[b,k])
+    nv = d + 1
+    k, loc = n2s // nv ** 2, n2s % nv ** 2
+    rows_of_slot = m.me[loc % nv, k]
+    cols_of_slot = m.me[loc // nv, k]
+    rows = np.repeat(np.arange(ref["n"]), np.diff(ref["row_ptr"]))
+    np.testing.assert_array_equal(rows_of_slot, np.repeat(rows, np.diff(ptr)))
+    np.testing.assert_array_equal(cols_of_slot, np.repeat(ref["col_idx"], np.diff(ptr)))
+    try:
+        for threads in (1, 4):
+            oracle.set_threads(threads)
+            v = oracle.reassemble(oracle.STIFF, m.q, m.me, ptr, n2s, c1=(oracle.COEF_P0, w))
+            np.testing.assert_array_equal(v, ref["val"])
+            r2 = oracle.assemble(oracle.STIFF, m.q, m.me, c1=(oracle.COEF_P0, w))
+            for key in ("row_ptr", "col_idx", "val", "scale", "abssum"):
+                np.testing.assert_array_equal(r2[key], ref[key])
+            p2, s2 = oracle.slot_map(m.me, m.nq)
+            np.testing.assert_array_equal(p2, ptr)
+            np.testing.assert_array_equal(s2, n2s)
+        bad = m.me.copy()
+        bad[1, 5] = m.nq + 3
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.assemble(oracle.STIFF, m.q, bad)
+        assert e.value.code == 2 and e.value.bad_id == 5
+    finally:
+        oracle.set_threads(1)
 
 
 # ---------------------------------------------------------------- derivatives
