@@ -95,6 +95,15 @@ extern "C" {
                                      lists of similar length; the nonzero order writes
                                      neighbouring values together). Values are the
                                      same bit for bit either way. */
+#define FE_PATTERN_INTERLEAVED 4 /* interleaved chunk records (scalar volume patterns,
+                                    m = 1): each element's values go straight to
+                                    slots laid out so that the 32 threads of a warp
+                                    sum 32 distinct vertices' or edges' lists from
+                                    consecutive slots. Only the mass, weighted mass
+                                    and stiffness calls (FE_F64, FE_F32) and the
+                                    gather and atomic strategies accept such a
+                                    pattern; the others return FE_ERR_ARG. Values are
+                                    bit-identical to the plain layout's in FE_F32. */
 /* elements per chunk of the chunked reassembly, 32..4096 (0: the default, 512 in
    3D and 1024 in 2D) */
 #define FE_PATTERN_CHUNK(c) ((int32_t)(c) << 8)

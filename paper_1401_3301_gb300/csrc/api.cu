@@ -284,6 +284,7 @@ static int scalar_call(fe_pattern_h h, int kind, const double* q, const void* w,
   }
   if (prec == FE_F64X) {  // volume patterns, scalar operators
     if (!h || !q || !vals || h->m != 1) return FE_ERR_ARG;
+    if ((h->flags & FE_PATTERN_INTERLEAVED) && h->strategy == FE_REASM_CHUNKED) return FE_ERR_ARG;
     if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
     return fe_launch_f64x(h, kind, q, w, w_kind, vals, (cudaStream_t)stream);
   }
@@ -320,6 +321,7 @@ int fe_assemble_wmass_stiff(fe_pattern_h h, const double* q, const void* w, int3
   FE_TRY(check_common(h, q, prec, vals_mass));
   if (!vals_stiff || vals_stiff == vals_mass) return FE_ERR_ARG;
   if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
+  if (h->flags & FE_PATTERN_INTERLEAVED) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && w_kind != FE_COEF_P0 && w_kind != FE_COEF_P0_INTERNAL) return FE_ERR_ARG;
   if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -343,6 +345,7 @@ int fe_assemble_general(fe_pattern_h h, const double* q, const void* coef, int32
                         int32_t prec, void* vals, void* stream) {
   FE_TRY(check_common(h, q, prec == FE_F64X ? FE_F64 : prec, vals));  // F64X: double data
   if (h->m != 1 || h->kdim != h->d || h->pk != 1 || !coef) return FE_ERR_ARG;
+  if ((h->flags & FE_PATTERN_INTERLEAVED) && h->strategy == FE_REASM_CHUNKED) return FE_ERR_ARG;
   if (coef_kind != FE_COEF_SCALAR && coef_kind != FE_COEF_P0 && coef_kind != FE_COEF_P0_INTERNAL &&
       coef_kind != FE_COEF_P1)
     return FE_ERR_ARG;

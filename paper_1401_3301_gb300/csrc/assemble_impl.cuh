@@ -461,6 +461,108 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   }
 }
 
+// Interleaved records (FE_PATTERN_INTERLEAVED, plan.cuh IlvLayout). One block per chunk:
+//  0. the record by one bulk (TMA) copy; the coordinates of the chunk's distinct
+//     vertices (split into hi/lo floats relative to the chunk's reference vertex in the
+//     FP32 form) and their P1 weights;
+//  1. each element reads its corners' local vertices from the record, forms its local
+//     matrix and stores each value in the slot the record names for it;
+//  2. warp w sums the lists of the 32 vertices (then edges) of group w: step j reads
+//     slot grp[w] + 32 j + lane, 32 consecutive slots, and the sums run in ascending
+//     element order as in k_chunk_staged. Values are scaled before they are stored
+//     (no per-element scale at summation), so the FP32 results equal the plain layout's
+//     bit for bit.
+template <int D, class T, int KIND, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_chunk_ilv(StagedArgs A, T* __restrict__ vals,
+                                                       void* __restrict__ partials, uint32_t max_slots) {
+  constexpr int NV = D + 1, NP = Pairs<D>::n;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t c = blockIdx.x;
+  const int64_t e0 = c * A.chunk;
+  const int ne = (int)min((int64_t)A.chunk, A.nme - e0);
+  const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
+  const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
+  const IlvLayout R = ilv_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
+  const IlvSmem S = ilv_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, max_slots);
+  if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
+  const uint16_t* corner = (const uint16_t*)(smem + R.corner);
+  const uint16_t* vpos = (const uint16_t*)(smem + R.vpos);
+  const uint16_t* epos = (const uint16_t*)(smem + R.epos);
+  const uint16_t* grp = (const uint16_t*)(smem + R.grp);
+  const uint16_t* lv_cnt = (const uint16_t*)(smem + R.lv_cnt);
+  const uint16_t* le_cnt = (const uint16_t*)(smem + R.le_cnt);
+  const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
+  T* V = (T*)(smem + S.vals);
+  T* wl = (T*)(smem + S.w);
+  if (!FE_RECORD_VALID_ILV(smem, R, ne, NV, NP, nlv, nle, A.nq, A.nnz, A.npart, max_slots, A.st, c)) return;
+
+  // 0. vertex coordinates (and P1 weights) of the chunk
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const int64_t vid = lv_vid[u];
+    stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
+    if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
+  }
+  __syncthreads();
+
+  // 1. element values, each to its slot
+  const bool has_coef = A.w_kind != FE_COEF_NONE && KIND != K_WMASS_P1;
+  for (int el = threadIdx.x; el < ne; el += THREADS) {
+    int lv[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) lv[a] = corner[a * ne + el];
+    Geo<D, T> g;
+    staged_geo<D, T, KIND == K_STIFF>(smem + S.q, lv, g, A.q, A.nq, lv_vid);
+    if (!det_ok(g.det)) {
+      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+      g.det = T(1);
+    }
+    T wv[NV];
+    if constexpr (KIND == K_WMASS_P1) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) wv[a] = wl[lv[a]];
+    }
+    const T coef = has_coef ? elem_coef<T>(A.w, A.w_kind, A.order, e0 + el) : T(1);
+    ScalarVals<D, T> v;
+    values_from_geo<D, T, KIND, false>(g, has_coef, coef, wv, v);
+#pragma unroll
+    for (int a = 0; a < NV; ++a) V[vpos[a * ne + el]] = v.diag[a];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) V[epos[p * ne + el]] = v.off[p];
+  }
+  __syncthreads();
+
+  // 2. sums: one group of 32 vertices (edges) per warp, 32 consecutive slots per step
+  for (int u = threadIdx.x; u < nlv; u += THREADS) {
+    const T* x = V + grp[u >> 5] + (u & 31);
+    const int n = lv_cnt[u];
+    Acc<T> acc(x[0]);
+    for (int j = 1; j < n; ++j) acc.add(x[32 * j]);
+    const int32_t dst = lv_dst[u];
+    if (dst >= 0) vals[dst] = acc.value();
+    else acc.store_partial(partials, -1 - (int64_t)dst);
+  }
+  const int ngv = (int)ilv_groups((uint32_t)nlv);
+  for (int u = threadIdx.x; u < nle; u += THREADS) {
+    const T* x = V + grp[ngv + (u >> 5)] + (u & 31);
+    const int n = le_cnt[u];
+    Acc<T> acc(x[0]);
+    for (int j = 1; j < n; ++j) acc.add(x[32 * j]);
+    const int32_t dst = le_dst[2 * u];
+    if (dst >= 0) {
+      const T val = acc.value();
+      vals[dst] = val;
+      vals[le_dst[2 * u + 1]] = val;
+    } else {
+      acc.store_partial(partials, -1 - (int64_t)dst);
+    }
+  }
+}
+
 // Sum of the chunk partials of each shared vertex / edge, in chunk order.
 template <class T, class AccT = Acc<T>>
 __global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,

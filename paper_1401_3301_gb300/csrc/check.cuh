@@ -67,6 +67,48 @@ static __device__ __noinline__ bool fe_record_valid(const unsigned char* rec, co
   return !bad;
 }
 
+// The same for an interleaved record (plan.cuh IlvLayout): counts at least 1 and
+// descending within each group of 32 (so a group's slots fit below the next group's
+// first slot), group bases ascending and within max_slots, every corner's local vertex
+// below nlv, every slot below the slot count, vertex ids below nq, destinations valid.
+static __device__ __noinline__ bool fe_record_valid_ilv(const unsigned char* rec, const IlvLayout& R, int ne,
+                                                        int nv, int np, int nlv, int nle, int64_t nq,
+                                                        int64_t nnz, int64_t npart, uint32_t max_slots,
+                                                        fe_status_word* st, int64_t c) {
+  const uint16_t* corner = (const uint16_t*)(rec + R.corner);
+  const uint16_t* vpos = (const uint16_t*)(rec + R.vpos);
+  const uint16_t* epos = (const uint16_t*)(rec + R.epos);
+  const uint16_t* grp = (const uint16_t*)(rec + R.grp);
+  const uint16_t* lv_cnt = (const uint16_t*)(rec + R.lv_cnt);
+  const uint16_t* le_cnt = (const uint16_t*)(rec + R.le_cnt);
+  const int32_t* lv_vid = (const int32_t*)(rec + R.lv_vid);
+  const int32_t* lv_dst = (const int32_t*)(rec + R.lv_dst);
+  const int32_t* le_dst = (const int32_t*)(rec + R.le_dst);
+  const int ngv = (int)ilv_groups(nlv), nge = (int)ilv_groups(nle);
+  const uint32_t total = grp[ngv + nge];
+  auto dst_ok = [&](int32_t dst) { return dst < 0 ? -1 - (int64_t)dst < npart : (int64_t)dst < nnz; };
+  bool bad = total > max_slots;
+  for (int g = threadIdx.x; g < ngv + nge; g += blockDim.x) bad |= grp[g] > grp[g + 1];
+  // the lists of a group end before the next group starts
+  for (int u = threadIdx.x; u < nlv + nle; u += blockDim.x) {
+    const bool ed = u >= nlv;
+    const int e = ed ? u - nlv : u;
+    const int cnt = ed ? le_cnt[e] : lv_cnt[e];
+    const int g = (ed ? ngv : 0) + (e >> 5);
+    bad |= cnt < 1 || (uint32_t)grp[g] + 32u * (uint32_t)(cnt - 1) + (uint32_t)(e & 31) >= grp[g + 1];
+    if (!ed) bad |= lv_vid[e] < 0 || lv_vid[e] >= nq || !dst_ok(lv_dst[e]);
+    else {
+      const int32_t d0 = le_dst[2 * e], d1 = le_dst[2 * e + 1];
+      bad |= !dst_ok(d0) || (d0 >= 0 && !dst_ok(d1)) || (d0 >= 0 && d1 < 0);
+    }
+  }
+  for (int j = threadIdx.x; j < nv * ne; j += blockDim.x) bad |= corner[j] >= nlv || vpos[j] >= total;
+  for (int j = threadIdx.x; j < np * ne; j += blockDim.x) bad |= epos[j] >= total;
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) fe_report(st, FE_ERR_BOUNDS, c);
+  return !bad;
+}
+
 // a shared entity's partial range [s, t) and its destination(s) in the fixup kernels
 __device__ __forceinline__ bool fe_fixup_valid(int32_t s, int32_t t, int64_t npart, int64_t span0, int64_t span1,
                                                bool two, int64_t nnz, fe_status_word* st, int64_t g) {
@@ -82,10 +124,12 @@ __device__ __forceinline__ bool fe_chunk_fits(bool ok, fe_status_word* st, int64
 }
 #define FE_CHUNK_FITS(...) fe_chunk_fits(__VA_ARGS__)
 #define FE_RECORD_VALID(...) fe_record_valid(__VA_ARGS__)
+#define FE_RECORD_VALID_ILV(...) fe_record_valid_ilv(__VA_ARGS__)
 #define FE_FIXUP_VALID(...) fe_fixup_valid(__VA_ARGS__)
 #else
 #define FE_CHUNK_FITS(...) true
 #define FE_RECORD_VALID(...) true
+#define FE_RECORD_VALID_ILV(...) true
 #define FE_FIXUP_VALID(...) true
 #endif
 

@@ -83,6 +83,7 @@ struct fe_pattern_s {
   uint32_t* rec_off16 = nullptr;    // nchunks: record offset in 16-byte units
   int64_t rec_bytes = 0, rec_max_bytes = 0;
   int32_t max_lv = 0;               // most local vertices of any chunk
+  int32_t max_slots = 0;            // FE_PATTERN_INTERLEAVED: most value slots of any chunk
   // scratch owned by the handle
   void* partials = nullptr; size_t partials_bytes = 0;
   void* kg = nullptr; size_t kg_bytes = 0;

@@ -356,13 +356,14 @@ __global__ void k_shared_finish(const uint64_t* keys, const uint32_t* vals, cons
 }
 
 __global__ void k_rec_sizes(int64_t nme, int chunk, int nv, int np, int m, int64_t nchunks,
-                            const int32_t* ch_v_ptr, const int32_t* ch_e_ptr, uint32_t* size16) {
+                            const int32_t* ch_v_ptr, const int32_t* ch_e_ptr, bool interleaved,
+                            uint32_t* size16) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nchunks) return;
   const int64_t ne = min((int64_t)chunk, nme - c * chunk);
-  const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, ch_v_ptr[c + 1] - ch_v_ptr[c],
-                                         ch_e_ptr[c + 1] - ch_e_ptr[c], m > 1);
-  size16[c] = L.total / 16u;
+  const uint32_t nlv = ch_v_ptr[c + 1] - ch_v_ptr[c], nle = ch_e_ptr[c + 1] - ch_e_ptr[c];
+  size16[c] = (interleaved ? fe::ilv_layout((uint32_t)ne, nv, np, nlv, nle).total
+                           : fe::rec_layout((uint32_t)ne, nv, np, nlv, nle, m > 1).total) / 16u;
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim.x a multiple of 32);
@@ -494,6 +495,99 @@ __global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, int m, bool o
       }
     }
     if (threadIdx.x == 0) r_off[n] = (uint16_t)end;
+    __syncthreads();
+  }
+}
+
+// One block per chunk: the interleaved record of a scalar plan (plan.cuh, IlvLayout).
+// The chunk's vertices (then edges) are ordered by descending incidence count and cut
+// into groups of 32; group g's slots start at the sum of 32 x (largest count) over the
+// groups before it, and the j-th incidence of the entity in lane l of group g gets slot
+// base_g + 32 j + l. Each element then learns, per corner and per local pair, the slot of
+// its value (vpos, epos) and, per corner, its local vertex (corner). Incidence lists keep
+// ascending element order, so each sum keeps the order of the plain layout. slots[c]
+// receives the chunk's slot count; a count above 65535 (uint16 slots) sets *overflow.
+// Dynamic shared memory: 6 bytes per entity of the larger list, plus one word per group.
+__global__ void k_rec_fill_ilv(int64_t nme, int chunk, int nv, int np, const int32_t* ch_v_ptr,
+                               const int32_t* ch_e_ptr, const uint16_t* inc_v, const uint16_t* inc_e,
+                               const uint16_t* lv_off, const uint16_t* le_off, const int32_t* lv_vid,
+                               const int32_t* lv_dst, const int32_t* le_dst, const uint32_t* off16,
+                               uint8_t* rec, uint32_t* slots, uint32_t* overflow) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t base_all;
+  const int64_t c = blockIdx.x;
+  const int64_t ne = min((int64_t)chunk, nme - c * chunk);
+  const int32_t vb = ch_v_ptr[c], nlv = ch_v_ptr[c + 1] - vb;
+  const int32_t eb = ch_e_ptr[c], nle = ch_e_ptr[c + 1] - eb;
+  const fe::IlvLayout L = fe::ilv_layout((uint32_t)ne, nv, np, nlv, nle);
+  uint8_t* r = rec + (int64_t)off16[c] * 16;
+  uint16_t* r_corner = (uint16_t*)(r + L.corner);
+  uint16_t* r_vpos = (uint16_t*)(r + L.vpos);
+  uint16_t* r_epos = (uint16_t*)(r + L.epos);
+  uint16_t* r_grp = (uint16_t*)(r + L.grp);
+  int32_t* r_lv_vid = (int32_t*)(r + L.lv_vid);
+  int32_t* r_lv_dst = (int32_t*)(r + L.lv_dst);
+  int32_t* r_le_dst = (int32_t*)(r + L.le_dst);
+  const int64_t ibv = c * (int64_t)chunk * nv, ibe = c * (int64_t)chunk * np;
+  const int ngv = (int)fe::ilv_groups(nlv);
+  if (threadIdx.x == 0) base_all = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool edges = pass == 1;
+    const int32_t n = edges ? nle : nlv, b0 = edges ? eb : vb;
+    const uint16_t* off = edges ? le_off : lv_off;
+    const uint16_t* inc = (edges ? inc_e : inc_v) + (edges ? ibe : ibv);
+    const uint32_t end = (uint32_t)(ne * (edges ? np : nv));
+    uint16_t* cnt = (uint16_t*)sm;
+    uint16_t* perm = cnt + n;
+    uint16_t* noff = perm + n;
+    uint32_t* gbase = (uint32_t*)(sm + 16 * ((6 * (size_t)n + 15) / 16));
+    uint16_t* r_cnt = (uint16_t*)(r + (edges ? L.le_cnt : L.lv_cnt));
+    for (int32_t u = threadIdx.x; u < n; u += blockDim.x)
+      cnt[u] = (uint16_t)((u + 1 < n ? off[b0 + u + 1] : end) - off[b0 + u]);
+    __syncthreads();
+    order_by_count(cnt, n, perm, noff, ws);
+    const int ng = (int)fe::ilv_groups(n);
+    if (threadIdx.x == 0) {  // group bases: the first entity of a group has its largest count
+      uint32_t b = base_all;
+      for (int g = 0; g < ng; ++g) {
+        gbase[g] = b;
+        r_grp[(edges ? ngv : 0) + g] = (uint16_t)b;
+        b += 32u * cnt[perm[32 * g]];
+      }
+      if (b > 65535u) atomicExch(overflow, 1u);
+      base_all = b;
+      if (edges) {
+        r_grp[ngv + ng] = (uint16_t)b;
+        slots[c] = b;
+      }
+    }
+    __syncthreads();
+    for (int32_t nu = threadIdx.x; nu < n; nu += blockDim.x) {
+      const int32_t u = perm[nu];
+      const uint32_t o = off[b0 + u], k = cnt[u];
+      const uint32_t first = gbase[nu >> 5] + (uint32_t)(nu & 31);
+      for (uint32_t j = 0; j < k; ++j) {
+        const uint32_t slot = first + 32u * j;
+        const uint32_t code = inc[o + j];
+        if (!edges) {
+          const uint32_t el = code / nv, a = code - el * nv;
+          r_vpos[a * ne + el] = (uint16_t)slot;
+          r_corner[a * ne + el] = (uint16_t)nu;
+        } else {
+          const uint32_t x = code >> 1, el = x / np, pp = x - el * np;
+          r_epos[pp * ne + el] = (uint16_t)slot;
+        }
+      }
+      r_cnt[nu] = (uint16_t)k;
+      if (!edges) {
+        r_lv_vid[nu] = lv_vid[vb + u];
+        r_lv_dst[nu] = lv_dst[vb + u];
+      } else {
+        r_le_dst[2 * nu] = le_dst[2 * (int64_t)(eb + u)];
+        r_le_dst[2 * nu + 1] = le_dst[2 * (int64_t)(eb + u) + 1];
+      }
+    }
     __syncthreads();
   }
 }
@@ -660,8 +754,9 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
   {
     uint32_t* size16;
     FE_TRY(tmp.get(&size16, h->nchunks + 1));
+    const bool ilv = (h->flags & FE_PATTERN_INTERLEAVED) != 0;
     k_rec_sizes<<<fe_grid(h->nchunks, T), T, 0, s>>>(nme, C, nv, npair, h->m, h->nchunks,
-                                                     h->ch_v_ptr, h->ch_e_ptr, size16);
+                                                     h->ch_v_ptr, h->ch_e_ptr, ilv, size16);
     FE_CUDA_TRY(cudaGetLastError());
     std::vector<uint32_t> sz(h->nchunks);
     FE_CUDA_TRY(cudaMemcpyAsync(sz.data(), size16, sizeof(uint32_t) * h->nchunks,
@@ -694,13 +789,38 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     }
     h->max_lv = mlv;
     const size_t fill_smem = 6u * (size_t)(mlv > mle ? mlv : mle) + 16u;
-    const bool ordered = fill_smem <= 227u * 1024u && !(h->flags & FE_PATTERN_ENTITY_ORDER);
-    if (ordered) FE_TRY(fe_smem_limit(k_rec_fill, fill_smem));
-    k_rec_fill<<<(unsigned)h->nchunks, 256, ordered ? fill_smem : 0, s>>>(
-        nme, C, nv, npair, h->m, ordered, h->ch_v_ptr, h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off,
-        h->le_off, h->lv_vid, h->lv_dst, h->le_dst, h->lv_str, h->le_str, h->rec_off16, h->rec);
-    FE_CUDA_TRY(cudaGetLastError());
-    FE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (ilv) {
+      // interleaved records: entities always count-ordered, plus one word per group
+      const size_t ilv_smem = 16u * ((fill_smem + 15u) / 16u) + 4u * fe::ilv_groups(mlv > mle ? mlv : mle);
+      if (ilv_smem > 227u * 1024u) return FE_ERR_OVERFLOW;
+      uint32_t *slots, *ovf;
+      FE_TRY(tmp.get(&slots, h->nchunks + 1));
+      FE_TRY(tmp.get(&ovf, 1));
+      FE_CUDA_TRY(cudaMemsetAsync(ovf, 0, sizeof(uint32_t), s));
+      FE_TRY(fe_smem_limit(k_rec_fill_ilv, ilv_smem));
+      k_rec_fill_ilv<<<(unsigned)h->nchunks, 256, ilv_smem, s>>>(
+          nme, C, nv, npair, h->ch_v_ptr, h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off, h->le_off, h->lv_vid,
+          h->lv_dst, h->le_dst, h->rec_off16, h->rec, slots, ovf);
+      FE_CUDA_TRY(cudaGetLastError());
+      std::vector<uint32_t> sl(h->nchunks);
+      uint32_t overflow = 0;
+      FE_CUDA_TRY(cudaMemcpyAsync(sl.data(), slots, sizeof(uint32_t) * h->nchunks, cudaMemcpyDeviceToHost, s));
+      FE_CUDA_TRY(cudaMemcpyAsync(&overflow, ovf, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      FE_CUDA_TRY(cudaStreamSynchronize(s));
+      uint32_t ms = 0;
+      for (uint32_t v : sl) ms = v > ms ? v : ms;
+      // more than 65535 slots in a chunk (uint16 slot numbers): the records are unusable,
+      // and the shared-memory check of the caller shrinks the chunk and rebuilds
+      h->max_slots = overflow ? (1 << 20) : (int32_t)ms;
+    } else {
+      const bool ordered = fill_smem <= 227u * 1024u && !(h->flags & FE_PATTERN_ENTITY_ORDER);
+      if (ordered) FE_TRY(fe_smem_limit(k_rec_fill, fill_smem));
+      k_rec_fill<<<(unsigned)h->nchunks, 256, ordered ? fill_smem : 0, s>>>(
+          nme, C, nv, npair, h->m, ordered, h->ch_v_ptr, h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off,
+          h->le_off, h->lv_vid, h->lv_dst, h->le_dst, h->lv_str, h->le_str, h->rec_off16, h->rec);
+      FE_CUDA_TRY(cudaGetLastError());
+      FE_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     // the records hold everything the kernels read: release the plan's flat arrays
     h->bytes -= (int64_t)sizeof(uint16_t) * nme * (nv + npair) + (int64_t)(2 + 4 + 4) * h->nlv +
                 (int64_t)(2 + 8) * h->nle + (h->m > 1 ? (int64_t)2 * h->nlv + (int64_t)4 * h->nle : 0);
@@ -1018,6 +1138,8 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
   if (mesh->nq < 1 || mesh->nme < 1 || !mesh->q || !mesh->me) return FE_ERR_ARG;
   if (kdim != d && !(kdim == d - 1 && m == 1)) return FE_ERR_ARG;
   if (pk > 1 && (kdim != d || m != 1)) return FE_ERR_ARG;
+  // interleaved records: scalar volume patterns only
+  if ((flags & FE_PATTERN_INTERLEAVED) && (m != 1 || kdim != d || pk > 1)) return FE_ERR_ARG;
   const int nv = pk > 1 ? fe_pk_nodes(d, pk) : kdim + 1, S = nv * nv;
   const int64_t nq = mesh->nq, nme = mesh->nme;
   if (nq > INT32_MAX / m || nme > INT32_MAX / S) return FE_ERR_OVERFLOW;
@@ -1133,6 +1255,8 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
       if ((rc = build_chunk_plan(h, &sb, tmp, s))) break;
       const uint32_t need =
           pk > 1 ? fe::pk_smem((uint32_t)nv, (uint32_t)h->npair, 8, (uint32_t)h->rec_max_bytes, (uint32_t)h->chunk).total
+          : (flags & FE_PATTERN_INTERLEAVED)
+              ? fe::ilv_smem(d, 8, true, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->max_slots).total
           : kdim == d
               ? fe::plan_smem_worst(d, m, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->chunk)
               : fe::boundary_smem(d, 8, true, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,

@@ -42,6 +42,58 @@ __host__ __device__ __forceinline__ RecLayout rec_layout(uint32_t ne, uint32_t n
   return L;
 }
 
+// Interleaved layout of a scalar chunk record (FE_PATTERN_INTERLEAVED). The chunk's
+// distinct vertices and edges are ordered by descending incidence count and taken in
+// groups of 32 (one warp); the j-th incidence of entity u (group g = u / 32, lane
+// u % 32) has its value at slot grp[g] + 32 j + lane of the chunk's value array, so a
+// warp summing its group's lists reads 32 consecutive slots per step. Vertex groups come
+// first, then edge groups. Byte offsets within the record:
+//   corner uint16[nv * ne]       local vertex of corner a of element el, at [a * ne + el]
+//   vpos   uint16[nv * ne]       slot of that corner's diagonal entry, at [a * ne + el]
+//   epos   uint16[np * ne]       slot of local pair p's entry, at [p * ne + el]
+//   grp    uint16[ngv + nge + 1] first slot of each group; grp[ngv + nge] = slots used
+//   lv_cnt uint16[nlv], le_cnt uint16[nle]   incidences of each vertex / edge
+//   lv_vid int32[nlv], lv_dst int32[nlv], le_dst int32[2 * nle]   as in the plain layout
+// Each array starts on a 16-byte boundary.
+struct IlvLayout {
+  uint32_t corner, vpos, epos, grp, lv_cnt, le_cnt, lv_vid, lv_dst, le_dst, total;
+};
+
+__host__ __device__ __forceinline__ uint32_t ilv_groups(uint32_t n) { return (n + 31u) / 32u; }
+
+__host__ __device__ __forceinline__ IlvLayout ilv_layout(uint32_t ne, uint32_t nv, uint32_t np, uint32_t nlv,
+                                                         uint32_t nle) {
+  IlvLayout L;
+  uint32_t o = 0;
+  L.corner = o; o += pad16(2u * nv * ne);
+  L.vpos = o;   o += pad16(2u * nv * ne);
+  L.epos = o;   o += pad16(2u * np * ne);
+  L.grp = o;    o += pad16(2u * (ilv_groups(nlv) + ilv_groups(nle) + 1u));
+  L.lv_cnt = o; o += pad16(2u * nlv);
+  L.le_cnt = o; o += pad16(2u * nle);
+  L.lv_vid = o; o += pad16(4u * nlv);
+  L.lv_dst = o; o += pad16(4u * nlv);
+  L.le_dst = o; o += pad16(8u * nle);
+  L.total = o;
+  return L;
+}
+
+// Shared memory of the interleaved chunk kernel: record, staged coordinates, P1
+// weights and the value slots (max_slots of them).
+struct IlvSmem {
+  uint32_t q, w, vals, total;
+};
+__host__ __device__ __forceinline__ IlvSmem ilv_smem(int D, int sizeT, bool p1_weight, uint32_t rec_max,
+                                                     uint32_t max_lv, uint32_t max_slots) {
+  IlvSmem L;
+  uint32_t o = pad16(rec_max);
+  L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
+  L.w = o;    o += p1_weight ? pad16(sizeT * max_lv) : 0u;
+  L.vals = o; o += pad16(sizeT * max_slots);
+  L.total = o;
+  return L;
+}
+
 // Shared-memory layout of the staged chunk kernel (byte offsets).
 struct StagedSmem {
   uint32_t q, w, lvid, kd, ko, sc, total;

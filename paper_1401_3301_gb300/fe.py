@@ -18,6 +18,7 @@ COEF_NONE, COEF_SCALAR, COEF_P0, COEF_P1, COEF_P0_INTERNAL = 0, 1, 2, 3, 4
 REASM_CHUNKED, REASM_GATHER, REASM_ATOMIC = 0, 1, 2
 PATTERN_KEEP_ORDER = 1
 PATTERN_ENTITY_ORDER = 2
+PATTERN_INTERLEAVED = 4
 
 
 def PATTERN_CHUNK(c: int) -> int:

@@ -1,9 +1,10 @@
 """Autotuner of the fixed-pattern reassembly.
 
 For one mesh (or one batch of meshes) and operator it times the chunked kernel over a
-grid of chunk sizes (elements per block, i.e. work per thread), the two layouts of the
-chunk records (distinct vertices and edges by incidence count, or in nonzero order) and
-threads per block, for the fused weighted mass + stiffness kernel also its launch shape
+grid of chunk sizes (elements per block, i.e. work per thread), the three layouts of the
+chunk records (distinct vertices and edges by incidence count, in nonzero order, or
+interleaved slots; a layout an operator or form does not take is skipped) and threads
+per block, for the fused weighted mass + stiffness kernel also its launch shape
 (persistent grid or one block per chunk), and optionally the two-pass gather and atomic
 strategies, with CUDA events (median of `reps` calls after one warm-up). The winner is cached in a JSON file keyed by GPU name,
 dimension, dofs per vertex, operator, precision and the element count's power of
@@ -24,7 +25,7 @@ from . import build_ext, fe
 CHUNKS = (256, 384, 512, 768, 1024)
 THREADS = (128, 256, 512)
 PERSISTENT = (True, False)
-LAYOUTS = (0, fe.PATTERN_ENTITY_ORDER)
+LAYOUTS = (0, fe.PATTERN_ENTITY_ORDER, fe.PATTERN_INTERLEAVED)
 _FORM = {fe.F64: "f64", fe.F32: "f32", fe.F64X: "f64x"}
 
 
@@ -104,6 +105,8 @@ def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int =
     shapes = PERSISTENT if kind == "wmass_stiff" else (True,)
     results = []
     vals = vals2 = None
+    if kind not in ("stiff", "mass", "wmass") or prec == fe.F64X:
+        layouts = tuple(x for x in layouts if x != fe.PATTERN_INTERLEAVED)
     for c in chunks:
         for lay in layouts:
             p = pattern(fe.PATTERN_CHUNK(c) | lay)

@@ -20,7 +20,7 @@ def test_autotune_caches_and_tuned_pattern_is_correct(tmp_path, monkeypatch):
     m = meshgen.kuhn_cube_mesh(10, seed=31)
     q, me = to_cuda(m.q), to_cuda(m.me)
     best = tune.autotune(q, me, chunks=(256, 512), threads=(128, 256), reps=3, deterministic_only=False)
-    assert best["tried"] == 2 * 2 * 2 + 2 and best["ms"] > 0  # chunks x layouts x threads + 2 strategies
+    assert best["tried"] == 2 * 3 * 2 + 2 and best["ms"] > 0  # chunks x layouts x threads + 2 strategies
     stored = json.loads(cache.read_text())
     assert len(stored) == 1 and list(stored.values())[0]["ms"] == best["ms"]
     again = tune.autotune(q, me, chunks=(256, 512), threads=(128, 256), reps=3)
