@@ -37,6 +37,86 @@ struct X64Args {
   int64_t nnz, npart;  // sizes of vals and of the partial sums (bounds-checked builds)
 };
 
+// Entries of element el of chunk c (corners lv, cofactor vectors cf, det B) into its
+// diagonal (Kd) and off-diagonal (Ko) double-float slots.
+template <int D, int KIND>
+__device__ __forceinline__ void x64_element_values(const X64Args& A, int64_t e0, int el, const int lv[D + 1],
+                                                   const df cf[D][D], df det, const float2* wl, float2* Kd,
+                                                   float2* Ko) {
+  constexpr int NV = D + 1, NP = Pairs<D>::n;
+  if (df_degenerate(det)) {
+    fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
+    det = df{1.f, 0.f};
+  }
+  if (det.hi < 0.f) det = df_neg(det);
+  if constexpr (KIND != K_STIFF) {
+    df dv[NV], ov[NP];
+    if constexpr (KIND == K_WMASS_P1) {
+      constexpr DfConst kC = df_const(1.0 / factorial(D + 3));
+      const df base = df_mul_full(det, df_of(kC));
+      df w[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const float2 x = wl[lv[a]];
+        w[a] = df{x.x, x.y};
+      }
+      df ws = w[0];
+#pragma unroll
+      for (int a = 1; a < NV; ++a) ws = df_add_fast(ws, w[a]);
+#pragma unroll
+      for (int a = 0; a < NV; ++a) dv[a] = df_twice(df_mul_full(base, df_add_fast(ws, df_twice(w[a]))));
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        ov[p] = df_mul_full(base, df_add_fast(ws, df_add_fast(w[Pairs<D>::a(p)], w[Pairs<D>::b(p)])));
+    } else {
+      constexpr DfConst kC = df_const(1.0 / factorial(D + 2));
+      df m = df_mul_full(det, df_of(kC));
+      if (A.w_kind != FE_COEF_NONE)
+        m = df_mul_full(m, df_split(elem_coef<double>(A.w, A.w_kind, A.order, e0 + el)));
+#pragma unroll
+      for (int a = 0; a < NV; ++a) dv[a] = df_twice(m);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) ov[p] = m;
+    }
+#pragma unroll
+    for (int a = 0; a < NV; ++a) Kd[el * NV + a] = make_float2(dv[a].hi, dv[a].lo);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Ko[el * NP + p] = make_float2(ov[p].hi, ov[p].lo);
+    return;
+  }
+  df inv = df_recip(df_mul_full(det, df{(float)factorial(D), 0.f}));
+  if (A.w_kind != FE_COEF_NONE)
+    inv = df_mul_full(inv, df_split(elem_coef<double>(A.w, A.w_kind, A.order, e0 + el)));
+  df G[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      G[i][j] = df_mul_full(df_dot<D>(cf[i], cf[j]), inv);
+      G[j][i] = G[i][j];
+    }
+  df nr[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    df s = df_neg(G[i][0]);
+#pragma unroll
+    for (int j = 1; j < D; ++j) s = df_sub(s, G[i][j]);
+    nr[i] = s;
+  }
+  df d0 = df_neg(nr[0]);
+#pragma unroll
+  for (int i = 1; i < D; ++i) d0 = df_sub(d0, nr[i]);
+  Kd[el * NV] = make_float2(d0.hi, d0.lo);
+#pragma unroll
+  for (int i = 0; i < D; ++i) Kd[el * NV + i + 1] = make_float2(G[i][i].hi, G[i][i].lo);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
+    const df v = (a == 0) ? nr[b - 1] : G[a - 1][b - 1];
+    Ko[el * NP + p] = make_float2(v.hi, v.lo);
+  }
+}
+
 template <int D, int KIND, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args A, double* __restrict__ vals,
                                                         float2* __restrict__ partials) {
@@ -50,7 +130,11 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   // same footprint as the FP32 form: split coordinates, uint16 corner map, float2 values
-  const StagedSmem S = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
+  // (the region after the values holds the list of elements to recompute)
+  const StagedSmem S = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, true);
+  __shared__ int nslow;
+  uint16_t* slow = (uint16_t*)(smem + S.sc);
+  if (threadIdx.x == 0) nslow = 0;
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
@@ -85,86 +169,37 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
   }
   __syncthreads();
 
-  // 1. element entries in double-float
+  // 1. element entries in double-float. An element whose double-float det B fails its
+  //    guard (dfloat.cuh) is listed and, after the loop, recomputed with the FP64 det B,
+  //    so that the common path carries no out-of-line call
   for (int el = threadIdx.x; el < ne; el += THREADS) {
     int lv[NV];
 #pragma unroll
     for (int a = 0; a < NV; ++a) lv[a] = lvid[el * NV + a];
     df cf[D][D];  // cofactor vectors c_1..c_D
-    df det = x64_geometry_guarded<D>(smem + S.q, lv, cf, A.q, A.nq, lv_vid);
-    if (df_degenerate(det)) {
-      fe_report(A.st, FE_ERR_DEGENERATE, A.order[e0 + el]);
-      det = df{1.f, 0.f};
-    }
-    if (det.hi < 0.f) det = df_neg(det);
-    if constexpr (KIND != K_STIFF) {
-      df dv[NV], ov[NP];
-      if constexpr (KIND == K_WMASS_P1) {
-        constexpr DfConst kC = df_const(1.0 / factorial(D + 3));
-        const df base = df_mul_full(det, df_of(kC));
-        df w[NV];
-#pragma unroll
-        for (int a = 0; a < NV; ++a) {
-          const float2 x = wl[lv[a]];
-          w[a] = df{x.x, x.y};
-        }
-        df ws = w[0];
-#pragma unroll
-        for (int a = 1; a < NV; ++a) ws = df_add_fast(ws, w[a]);
-#pragma unroll
-        for (int a = 0; a < NV; ++a) dv[a] = df_twice(df_mul_full(base, df_add_fast(ws, df_twice(w[a]))));
-#pragma unroll
-        for (int p = 0; p < NP; ++p)
-          ov[p] = df_mul_full(base, df_add_fast(ws, df_add_fast(w[Pairs<D>::a(p)], w[Pairs<D>::b(p)])));
-      } else {
-        constexpr DfConst kC = df_const(1.0 / factorial(D + 2));
-        df m = df_mul_full(det, df_of(kC));
-        if (A.w_kind != FE_COEF_NONE)
-          m = df_mul_full(m, df_split(elem_coef<double>(A.w, A.w_kind, A.order, e0 + el)));
-#pragma unroll
-        for (int a = 0; a < NV; ++a) dv[a] = df_twice(m);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) ov[p] = m;
-      }
-#pragma unroll
-      for (int a = 0; a < NV; ++a) Kd[el * NV + a] = make_float2(dv[a].hi, dv[a].lo);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) Ko[el * NP + p] = make_float2(ov[p].hi, ov[p].lo);
-      continue;
-    }
-    df inv = df_recip(df_mul_full(det, df{(float)factorial(D), 0.f}));
-    if (A.w_kind != FE_COEF_NONE)
-      inv = df_mul_full(inv, df_split(elem_coef<double>(A.w, A.w_kind, A.order, e0 + el)));
-    df G[D][D];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = i; j < D; ++j) {
-        G[i][j] = df_mul_full(df_dot<D>(cf[i], cf[j]), inv);
-        G[j][i] = G[i][j];
-      }
-    df nr[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      df s = df_neg(G[i][0]);
-#pragma unroll
-      for (int j = 1; j < D; ++j) s = df_sub(s, G[i][j]);
-      nr[i] = s;
-    }
-    df d0 = df_neg(nr[0]);
-#pragma unroll
-    for (int i = 1; i < D; ++i) d0 = df_sub(d0, nr[i]);
-    Kd[el * NV] = make_float2(d0.hi, d0.lo);
-#pragma unroll
-    for (int i = 0; i < D; ++i) Kd[el * NV + i + 1] = make_float2(G[i][i].hi, G[i][i].lo);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const int a = Pairs<D>::a(p), b = Pairs<D>::b(p);
-      const df v = (a == 0) ? nr[b - 1] : G[a - 1][b - 1];
-      Ko[el * NP + p] = make_float2(v.hi, v.lo);
-    }
+    bool exact;
+    const df det = x64_geometry_check<D>(smem + S.q, lv, cf, exact);
+    if (exact) slow[atomicAdd(&nslow, 1)] = (uint16_t)el;
+    x64_element_values<D, KIND>(A, e0, el, lv, cf, det, wl, Kd, Ko);
   }
   __syncthreads();
+  if (nslow > 0) {
+    for (int i = threadIdx.x; i < nslow; i += THREADS) {
+      const int el = slow[i];
+      int lv[NV];
+      int32_t v[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        lv[a] = lvid[el * NV + a];
+        v[a] = lv_vid[lv[a]];
+      }
+      df cf[D][D];
+      bool exact;
+      x64_geometry_check<D>(smem + S.q, lv, cf, exact);
+      x64_element_values<D, KIND>(A, e0, el, lv, cf, df_split(det_from_q<D>(A.q, A.nq, v)), wl, Kd, Ko);
+    }
+    __syncthreads();
+  }
 
   // 2. sums in element order; owned sums become doubles, shared ones stay float pairs
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
@@ -201,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
 template <int D, int KIND>
 int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
-  const StagedSmem L = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
+  const StagedSmem L = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, true);
   if (L.total > 227u * 1024u) return FE_ERR_ARG;
   auto kern = k_chunk_f64x<D, KIND, THREADS>;
   FE_TRY(fe_smem_limit(kern, L.total));

@@ -207,6 +207,24 @@ __device__ __forceinline__ df x64_geometry_guarded(const unsigned char* sq, cons
   return det;
 }
 
+// x64_geometry and the verdict of the same guard: exact = true where det B must be
+// recomputed in FP64 (the caller does it)
+template <int D>
+__device__ __forceinline__ df x64_geometry_check(const unsigned char* sq, const int lv[D + 1], df cf[D][D],
+                                                 bool& exact) {
+  df e[D][D];
+  float xm;
+  x64_edges<D, D>(sq, lv, e, &xm);
+  const df det = x64_cofactors<D>(e, cf);
+  float em = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int k = 0; k < D; ++k) em = fmaxf(em, fabsf(e[i][k].hi));
+  exact = fabsf(det.hi) < kDetGuardF64X * xm * (D == 3 ? em * em : em);
+  return det;
+}
+
 // det B is zero or not finite (tested on its float rounding)
 __device__ __forceinline__ bool df_degenerate(df det) {
   const float dh = __fadd_rn(det.hi, det.lo);
