@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
       df cf[D][D];
       bool exact;
       x64_geometry_check<D>(smem + S.q, lv, cf, exact);
-      x64_element_values<D, KIND>(A, e0, el, lv, cf, df_split(det_from_q<D>(A.q, A.nq, v)), wl, Kd, Ko);
+      x64_element_values<D, KIND>(A, e0, el, lv, cf, df_split(det_from_q<D>(A.q, A.nq, vert_ids<D>(v))), wl, Kd, Ko);
     }
     __syncthreads();
   }

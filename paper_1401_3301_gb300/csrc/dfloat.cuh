@@ -202,7 +202,7 @@ __device__ __forceinline__ df x64_geometry_guarded(const unsigned char* sq, cons
     int32_t v[D + 1];
 #pragma unroll
     for (int a = 0; a <= D; ++a) v[a] = lv_vid[lv[a]];
-    det = df_split(det_from_q<D>(q, nq, v));
+    det = df_split(det_from_q<D>(q, nq, vert_ids<D>(v)));
   }
   return det;
 }

@@ -281,13 +281,33 @@ __device__ __forceinline__ void geo_f32(const float xh[D + 1][D], const float xl
   g.full = COF && min_cofactor<D>(g) < kShapeGuard * (D == 3 ? emax * emax : emax);
 }
 
+// Arguments and results of the out-of-line FP64 recomputations below are passed by
+// value: an object whose address reaches a call that is not inlined has to live in local
+// memory, and the caller's Geo would then be stored and reloaded for every element.
+template <int D>
+struct VertIds {
+  int32_t v[D + 1];
+};
+template <int D>
+struct GeoCof {
+  float c[D + 1][D];
+  float det;
+};
+template <int D>
+__device__ __forceinline__ VertIds<D> vert_ids(const int32_t* v) {
+  VertIds<D> r;
+#pragma unroll
+  for (int a = 0; a <= D; ++a) r.v[a] = v[a];
+  return r;
+}
+
 // FP32 form, badly shaped element (g.full): det B and the cofactors recomputed in FP64
 // from the FP64 coordinates of the element's vertices v (edges by one FP64 subtraction
 // each, c_a = e_{a+1} x e_{a+2}, c_0 = -sum_a c_a, det B = e_1 . c_1), then rounded to
 // float. Rare, so kept out of line.
 template <int D>
-__device__ __noinline__ void geo_exact_f32(const double* __restrict__ q, int64_t nq, const int32_t* v,
-                                           Geo<D, float>& g) {
+__device__ __noinline__ GeoCof<D> geo_exact_f32(const double* __restrict__ q, int64_t nq, const VertIds<D> vi) {
+  const int32_t* v = vi.v;
   double x0[D], e[D][D], c[D + 1][D];
 #pragma unroll
   for (int k = 0; k < D; ++k) x0[k] = __ldg(q + (int64_t)k * nq + v[0]);
@@ -319,11 +339,13 @@ __device__ __noinline__ void geo_exact_f32(const double* __restrict__ q, int64_t
     for (int a = 2; a <= D; ++a) s -= c[a][k];
     c[0][k] = s;
   }
+  GeoCof<D> g;
 #pragma unroll
   for (int a = 0; a <= D; ++a)
 #pragma unroll
     for (int k = 0; k < D; ++k) g.c[a][k] = (float)c[a][k];
   g.det = (float)det;
+  return g;
 }
 
 // coordinates of the d+1 vertices gathered from global memory
@@ -360,7 +382,8 @@ __device__ __forceinline__ void load_x32(const float4* __restrict__ qs, const in
 // edge. Taken only for elements whose double-float det B fails its guard, so it is kept
 // out of line.
 template <int D>
-__device__ __noinline__ double det_from_q(const double* __restrict__ q, int64_t nq, const int32_t* v) {
+__device__ __noinline__ double det_from_q(const double* __restrict__ q, int64_t nq, const VertIds<D> vi) {
+  const int32_t* v = vi.v;
   double x0[D], e[D][D];
 #pragma unroll
   for (int k = 0; k < D; ++k) x0[k] = __ldg(q + (int64_t)k * nq + v[0]);
@@ -380,8 +403,16 @@ __device__ __noinline__ double det_from_q(const double* __restrict__ q, int64_t 
 template <int D>
 __device__ __forceinline__ void guard_geo_f32(Geo<D, float>& g, const double* __restrict__ q, int64_t nq,
                                               const int32_t* v) {
-  if (g.full) geo_exact_f32<D>(q, nq, v, g);
-  else if (fabsf(g.det) < kDetGuardF32 * g.dsc) g.det = (float)det_from_q<D>(q, nq, v);
+  if (g.full) {
+    const GeoCof<D> r = geo_exact_f32<D>(q, nq, vert_ids<D>(v));
+#pragma unroll
+    for (int a = 0; a <= D; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) g.c[a][k] = r.c[a][k];
+    g.det = r.det;
+  } else if (fabsf(g.det) < kDetGuardF32 * g.dsc) {
+    g.det = (float)det_from_q<D>(q, nq, vert_ids<D>(v));
+  }
 }
 
 // det B usable: nonzero, normal and finite (checked on the exponent bits)
