@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
   const int32_t nlv = A.ch_v_ptr[c + 1] - A.ch_v_ptr[c];
   const int32_t nle = A.ch_e_ptr[c + 1] - A.ch_e_ptr[c];
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
-  // same footprint as the FP32 form: split coordinates, uint16 corner map, float2 values
+  // same footprint as the FP32 form: split coordinates, float2 values
   // (the region after the values holds the list of elements to recompute)
   const StagedSmem S = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, true);
   __shared__ int nslow;
@@ -144,11 +144,11 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
   const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
   const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   float2* Kd = (float2*)(smem + S.kd);
   float2* Ko = (float2*)(smem + S.ko);
   float2* wl = (float2*)(smem + S.w);  // P1 weight of each chunk vertex
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   // 0. coordinates relative to corner 0 of the chunk's first element (FP64), split into
   //    float pairs; the reference does not depend on the record's vertex order
@@ -165,7 +165,6 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
       const df wv = df_split(A.w[vid]);
       wl[u] = make_float2(wv.hi, wv.lo);
     }
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -237,7 +236,7 @@ template <int D, int KIND>
 int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
   const StagedSmem L = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, true);
-  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  if (L.total > kSmemDynMax) return FE_ERR_ARG;
   auto kern = k_chunk_f64x<D, KIND, THREADS>;
   FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);

@@ -354,8 +354,8 @@ constexpr uint32_t kBarrierSpin = 1u << 22;
 // One block per chunk of internal elements.
 //  0. one bulk (TMA) copy brings the chunk's plan record into shared memory; the
 //     coordinates of the chunk's distinct vertices are read once from q (split into
-//     hi/lo floats for the FP32 form), and the record's vertex incidence lists give
-//     each element corner its local vertex;
+//     hi/lo floats for the FP32 form); the record also gives each element corner its
+//     local vertex;
 //  1. element values into shared memory (diagonal per corner, off-diagonal per edge);
 //  2. each distinct vertex / edge sums its incidences in ascending element order and
 //     stores the sum in the CSR value (both (i,j) and (j,i) for an edge: the
@@ -384,20 +384,19 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
   const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   T* Kd = (T*)(smem + S.kd);
   T* Ko = (T*)(smem + S.ko);
   T* wl = (T*)(smem + S.w);
   T* Sc = (T*)(smem + S.sc);
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
-  // 0. vertex coordinates of the chunk, and the local vertex of every element corner
+  // 0. vertex coordinates of the chunk (the record carries each corner's local vertex)
   const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
     if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 

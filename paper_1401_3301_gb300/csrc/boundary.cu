@@ -38,17 +38,16 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary(StagedArgs A, T* __r
   const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
   const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   T* Kd = (T*)(smem + S.kd);
   T* Ko = (T*)(smem + S.ko);
   T* wl = (T*)(smem + S.w);
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u);
     if constexpr (KIND == K_WMASS_P1) wl[u] = ((const T*)A.w)[vid];
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -164,7 +163,7 @@ template <int D, class T, int KIND>
 int launch(fe_pattern_s* h, const StagedArgs& A, T* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
   const StagedSmem L = boundary_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
-  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  if (L.total > kSmemDynMax) return FE_ERR_ARG;
   auto kern = k_chunk_boundary<D, T, KIND, THREADS>;
   FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);
@@ -219,11 +218,11 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary_x(StagedArgs A, cons
   const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
   const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   float2* Kd = (float2*)(smem + S.kd);
   float2* Ko = (float2*)(smem + S.ko);
   float2* wl = (float2*)(smem + S.w);
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   double xr[D];
   {
@@ -238,7 +237,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary_x(StagedArgs A, cons
       const df wv = df_split(((const double*)A.w)[vid]);
       wl[u] = make_float2(wv.hi, wv.lo);
     }
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -326,7 +324,7 @@ template <int D, int KIND>
 int launch_x(fe_pattern_s* h, const StagedArgs& A, double* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
   const StagedSmem L = boundary_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
-  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  if (L.total > kSmemDynMax) return FE_ERR_ARG;
   auto kern = k_chunk_boundary_x<D, KIND, THREADS>;
   FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_CHUNK, s);

@@ -2,12 +2,12 @@
 //
 // fe_record_valid validates a chunk's plan record once it is in shared memory, before
 // any index in it is used: offsets ascend from 0 to the incidence counts, every
-// incidence code names a corner / element edge of the chunk, the vertex incidence
-// lists are a permutation of the chunk's corners (so the corner map is fully written),
-// every vertex id is below nq, and every destination is a value inside the matrix or a
-// partial-sum slot below npart. A failure records FE_ERR_BOUNDS with the chunk id and
-// the whole block skips the chunk. `mark` is the kernel's corner-map array (nv * ne
-// uint16), used as scratch and overwritten by the kernel's own phase 0 afterwards.
+// incidence code names a corner / element edge of the chunk, every corner's local
+// vertex is below nlv and the vertex incidence lists agree with the corner map (each
+// corner once in the list of its own local vertex, so the lists are a permutation of
+// the corners), every vertex id is below nq, and every destination is a value inside
+// the matrix or a partial-sum slot below npart. A failure records FE_ERR_BOUNDS with the
+// chunk id and the whole block skips the chunk.
 //
 // In the normal build FE_RECORD_VALID is the constant true and nothing here is compiled.
 #pragma once
@@ -21,8 +21,8 @@ namespace fe {
 // m: dofs per vertex (m x m blocks at dst + l * stride + n when m > 1)
 static __device__ __noinline__ bool fe_record_valid(const unsigned char* rec, const RecLayout& R, int ne, int nv,
                                              int np, int nlv, int nle, int m, int64_t nq, int64_t nnz,
-                                             int64_t npart, uint16_t* mark, fe_status_word* st,
-                                             int64_t c) {
+                                             int64_t npart, fe_status_word* st, int64_t c) {
+  const uint16_t* lvid = (const uint16_t*)(rec + R.lvid);
   const uint16_t* inc_v = (const uint16_t*)(rec + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(rec + R.inc_e);
   const uint16_t* lv_off = (const uint16_t*)(rec + R.lv_off);
@@ -53,15 +53,17 @@ static __device__ __noinline__ bool fe_record_valid(const unsigned char* rec, co
     if (d0 >= 0) bad |= d1 < 0 || !dst_ok(d1, m > 1 ? le_str[2 * u + 1] : 0);
   }
   for (int j = threadIdx.x; j < nee; j += blockDim.x) bad |= (inc_e[j] >> 1) >= nee;
-  for (int j = threadIdx.x; j < nvv; j += blockDim.x) {
-    bad |= inc_v[j] >= nvv;
-    mark[j] = 0;
+  for (int j = threadIdx.x; j < nvv; j += blockDim.x) bad |= inc_v[j] >= nvv || lvid[j] >= nlv;
+  // offsets ascend and end at nvv: the lists are ranges of [0, nvv)
+  bad = __syncthreads_or(bad);
+  if (!bad) {
+    for (int k = threadIdx.x; k < nvv; k += blockDim.x) {  // corner k: once in its vertex's list
+      const int u = lvid[k];
+      int n = 0;
+      for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) n += inc_v[j] == k;
+      bad |= n != 1;
+    }
   }
-  __syncthreads();
-  for (int j = threadIdx.x; j < nvv; j += blockDim.x)
-    if (inc_v[j] < nvv) mark[inc_v[j]] = 1;
-  __syncthreads();
-  for (int j = threadIdx.x; j < nvv; j += blockDim.x) bad |= mark[j] != 1;
   bad = __syncthreads_or(bad);
   if (bad && threadIdx.x == 0) fe_report(st, FE_ERR_BOUNDS, c);
   return !bad;

@@ -110,21 +110,20 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
   const uint16_t* lv_str = (const uint16_t*)(smem + R.lv_str);
   const uint16_t* le_str = (const uint16_t*)(smem + R.le_str);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   T* lam_l = (T*)(smem + S.coef);
   T* mu_l = lam_l + A.max_lv;
   T* Cg = (T*)(smem + S.cg);   // [e][a][i]
   T* LM = (T*)(smem + S.lm);   // [e][2]
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, A.st, c)) return;
 
-  // 0. coordinates (and P1 Lame values) of the chunk's vertices; local vertex of each corner
+  // 0. coordinates (and P1 Lame values) of the chunk's vertices
   const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
     if (A.lam_kind == FE_COEF_P1) lam_l[u] = ((const T*)A.lam)[vid];
     if (A.mu_kind == FE_COEF_P1) mu_l[u] = ((const T*)A.mu)[vid];
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -295,7 +294,7 @@ template <int D, class T>
 int launch(fe_pattern_s* h, const ElasArgs& A, T* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
   const ElasSmem L = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
-  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  if (L.total > kSmemDynMax) return FE_ERR_ARG;
   auto kern = k_chunk_elas<D, T, THREADS>;
   FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_ELAS_CHUNK, s);
@@ -370,12 +369,12 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
   const uint16_t* lv_str = (const uint16_t*)(smem + R.lv_str);
   const uint16_t* le_str = (const uint16_t*)(smem + R.le_str);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   float2* lam_l = (float2*)(smem + S.coef);
   float2* mu_l = lam_l + A.max_lv;
   float2* Cg = (float2*)(smem + S.cg);  // [e][a][i]
   float2* LM = (float2*)(smem + S.lm);  // [e][2]
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   // 0. coordinates relative to corner 0 of the chunk's first element, split into float
   //    pairs; P1 Lame values; local vertex of each corner
@@ -396,7 +395,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __
       const df v = df_split(((const double*)A.mu)[vid]);
       mu_l[u] = make_float2(v.hi, v.lo);
     }
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -528,7 +526,7 @@ template <int D>
 int launch_x(fe_pattern_s* h, const ElasArgs& A, double* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
   const ElasSmem L = elas_smem(D, 8, A.rec_max, A.max_lv, A.chunk);
-  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  if (L.total > kSmemDynMax) return FE_ERR_ARG;
   auto kern = k_chunk_elas_x<D, THREADS>;
   FE_TRY(fe_smem_limit(kern, L.total));
   FE_PROF_BEGIN(h, FE_K_ELAS_CHUNK, s);

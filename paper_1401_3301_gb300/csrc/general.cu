@@ -311,15 +311,14 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
   const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
   const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   T* Kd = (T*)(smem + S.kd);
   T2* Ko = (T2*)(smem + S.ko);
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     stage_vertex<D, T>(A.q, A.nq, lv_vid[u], smem + S.q, u, xr.ptr());
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -464,7 +463,7 @@ int launch_general(fe_pattern_s* h, const ElemArgs& E, T* vals, cudaStream_t s) 
   if (h->strategy == FE_REASM_CHUNKED) {
     const StagedSmem L = general_smem(D, (int)sizeof(T), (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,
                                       (uint32_t)h->chunk);
-    if (L.total > 227u * 1024u) return FE_ERR_ARG;
+    if (L.total > kSmemDynMax) return FE_ERR_ARG;
     GeneralArgs G{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, E.q, E.w,
                   E.w_kind, vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status,
                   h->nnz_s, h->me_int};
@@ -560,10 +559,10 @@ __global__ void __launch_bounds__(THREADS, P1 ? 2 : 3) k_chunk_general_x(General
   const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
   const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   float2* Kd = (float2*)(smem + S.kd);
   float4* Ko = (float4*)(smem + S.ko);  // (E_ab, E_ba) of each element pair as two float pairs
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   double xr[D];
   {
@@ -573,7 +572,6 @@ __global__ void __launch_bounds__(THREADS, P1 ? 2 : 3) k_chunk_general_x(General
   }
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     x64_stage_vertex<D>(A.q, A.nq, lv_vid[u], xr, smem + S.q, u);
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   }
   __syncthreads();
 
@@ -650,7 +648,7 @@ int launch_general_x(fe_pattern_s* h, const double* q, const void* coef, int coe
   constexpr int THREADS = 256;
   if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
   const StagedSmem L = general_smem(D, 8, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->chunk);
-  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  if (L.total > kSmemDynMax) return FE_ERR_ARG;
   const bool vec = ((uintptr_t)coef & 15u) == 0;
   GeneralArgs G{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, coef, coef_kind,
                 vec, h->order, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->npart, h->status, h->nnz_s,

@@ -447,6 +447,7 @@ __global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, int m, bool o
   const int32_t eb = ch_e_ptr[c], nle = ch_e_ptr[c + 1] - eb;
   const fe::RecLayout L = fe::rec_layout((uint32_t)ne, nv, np, nlv, nle, m > 1);
   uint8_t* r = rec + (int64_t)off16[c] * 16;
+  uint16_t* r_lvid = (uint16_t*)(r + L.lvid);
   uint16_t* r_inc_v = (uint16_t*)(r + L.inc_v);
   uint16_t* r_inc_e = (uint16_t*)(r + L.inc_e);
   uint16_t* r_lv_off = (uint16_t*)(r + L.lv_off);
@@ -479,7 +480,10 @@ __global__ void k_rec_fill(int64_t nme, int chunk, int nv, int np, int m, bool o
       const uint32_t o = off[b0 + u];
       const uint32_t no = ordered ? noff[nu] : o;
       const uint32_t k = (u + 1 < n ? off[b0 + u + 1] : end) - o;
-      for (uint32_t j = 0; j < k; ++j) r_inc[no + j] = inc[o + j];
+      for (uint32_t j = 0; j < k; ++j) {
+        r_inc[no + j] = inc[o + j];
+        if (!edges) r_lvid[inc[o + j]] = (uint16_t)nu;  // corner -> its local vertex
+      }
       r_off[nu] = (uint16_t)no;
       if (!edges) {
         r_lv_vid[nu] = lv_vid[vb + u];
@@ -792,7 +796,7 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
     if (ilv) {
       // interleaved records: entities always count-ordered, plus one word per group
       const size_t ilv_smem = 16u * ((fill_smem + 15u) / 16u) + 4u * fe::ilv_groups(mlv > mle ? mlv : mle);
-      if (ilv_smem > 227u * 1024u) return FE_ERR_OVERFLOW;
+      if (ilv_smem > fe::kSmemDynMax) return FE_ERR_OVERFLOW;
       uint32_t *slots, *ovf;
       FE_TRY(tmp.get(&slots, h->nchunks + 1));
       FE_TRY(tmp.get(&ovf, 1));
@@ -813,7 +817,7 @@ int build_chunk_plan(fe_pattern_s* h, fe_sort_buffers* sb, dev_tmp& tmp, cudaStr
       // and the shared-memory check of the caller shrinks the chunk and rebuilds
       h->max_slots = overflow ? (1 << 20) : (int32_t)ms;
     } else {
-      const bool ordered = fill_smem <= 227u * 1024u && !(h->flags & FE_PATTERN_ENTITY_ORDER);
+      const bool ordered = fill_smem <= fe::kSmemDynMax && !(h->flags & FE_PATTERN_ENTITY_ORDER);
       if (ordered) FE_TRY(fe_smem_limit(k_rec_fill, fill_smem));
       k_rec_fill<<<(unsigned)h->nchunks, 256, ordered ? fill_smem : 0, s>>>(
           nme, C, nv, npair, h->m, ordered, h->ch_v_ptr, h->ch_e_ptr, h->inc_v, h->inc_e, h->lv_off,
@@ -1261,7 +1265,7 @@ int fe_pattern_impl(const fe_mesh* mesh, int32_t m, int32_t flags, void* stream,
               ? fe::plan_smem_worst(d, m, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, (uint32_t)h->chunk)
               : fe::boundary_smem(d, 8, true, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv,
                                   (uint32_t)h->chunk).total;
-      if (need <= 227u * 1024u || h->chunk <= (pk > 1 ? 1 : 32)) break;
+      if (need <= fe::kSmemDynMax || h->chunk <= (pk > 1 ? 1 : 32)) break;
       if (cudaStreamSynchronize(s) != cudaSuccess) { rc = FE_ERR_CUDA; break; }
       free_plan(h);
       h->bytes = bytes_before;

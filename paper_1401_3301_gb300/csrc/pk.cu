@@ -200,12 +200,12 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
   const int32_t* lv_vid = (const int32_t*)(smem + R.lv_vid);
   const int32_t* lv_dst = (const int32_t*)(smem + R.lv_dst);
   const int32_t* le_dst = (const int32_t*)(smem + R.le_dst);
-  uint16_t* lvid = (uint16_t*)(smem + S.lvid);
+  const uint16_t* lvid = (const uint16_t*)(smem + R.lvid);
   T* Sc = (T*)(smem + S.sc);
   T* tab = (T*)(smem + S.tab);
   float2* Sx = (float2*)(smem + S.sc);   // X: |det B| pairs
   float2* tabx = (float2*)(smem + S.tab);  // X: table pairs
-  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, lvid, A.st, c)) return;
+  if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   for (int i = threadIdx.x; i < NV + NP; i += THREADS) {
     if constexpr (X) {
@@ -215,8 +215,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_pk(PkArgs A, T* __restrict__ 
       tab[i] = ((const T*)A.tab)[i];
     }
   }
-  for (int u = threadIdx.x; u < nlv; u += THREADS)
-    for (int j = lv_off[u]; j < lv_off[u + 1]; ++j) lvid[inc_v[j]] = (uint16_t)u;
   __syncthreads();
 
   for (int el = threadIdx.x; el < ne; el += THREADS) {
@@ -320,7 +318,7 @@ int launch_pk(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   constexpr int THREADS = 256;
   if (h->nv != NV || h->npair != NP) return FE_ERR_ARG;
   const PkSmem L = pk_smem(NV, NP, (int)sizeof(T), (uint32_t)h->rec_max_bytes, (uint32_t)h->chunk);
-  if (L.total > 227u * 1024u) return FE_ERR_ARG;
+  if (L.total > kSmemDynMax) return FE_ERR_ARG;
   const void* tab = sizeof(T) == 8 ? h->pk_tab : (const void*)((const double*)h->pk_tab + NV + NP);
   PkArgs A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, q, tab, h->order, h->ch_v_ptr, h->ch_e_ptr,
            h->rec, h->rec_off16, h->status, h->nnz_s, h->npart};

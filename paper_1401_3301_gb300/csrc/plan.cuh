@@ -1,6 +1,7 @@
 // Layout of the per-chunk plan record: one contiguous, 16-byte aligned block per
 // element chunk, copied to shared memory with a single bulk copy by the chunked
 // reassembly kernels. Byte offsets within the record:
+//   lvid   uint16[nv * ne]     local vertex of corner a of element e_local, at e_local * nv + a
 //   inc_v  uint16[nv * ne]     (e_local * nv + a), grouped by local vertex
 //   inc_e  uint16[np * ne]     ((e_local * np + p) << 1) | swapped, grouped by local edge
 //   lv_off uint16[nlv + 1]     first incidence of each local vertex; lv_off[nlv] = nv * ne
@@ -19,16 +20,22 @@
 namespace fe {
 
 struct RecLayout {
-  uint32_t inc_v, inc_e, lv_off, le_off, lv_vid, lv_dst, le_dst, lv_str, le_str, total;
+  uint32_t lvid, inc_v, inc_e, lv_off, le_off, lv_vid, lv_dst, le_dst, lv_str, le_str, total;
 };
 
 __host__ __device__ __forceinline__ uint32_t pad16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Dynamic shared memory a chunked kernel may take: the 227 KB a block can opt into, less
+// 1 KB for the kernels' static shared variables (barrier, counters, the 128-byte
+// alignment of the dynamic array), which count against the same limit.
+constexpr uint32_t kSmemDynMax = 227u * 1024u - 1024u;
 
 __host__ __device__ __forceinline__ RecLayout rec_layout(uint32_t ne, uint32_t nv, uint32_t np,
                                                          uint32_t nlv, uint32_t nle,
                                                          bool vector = false) {
   RecLayout L;
   uint32_t o = 0;
+  L.lvid = o;   o += pad16(2u * nv * ne);
   L.inc_v = o;  o += pad16(2u * nv * ne);
   L.inc_e = o;  o += pad16(2u * np * ne);
   L.lv_off = o; o += pad16(2u * (nlv + 1));
@@ -96,7 +103,7 @@ __host__ __device__ __forceinline__ IlvSmem ilv_smem(int D, int sizeT, bool p1_w
 
 // Shared-memory layout of the staged chunk kernel (byte offsets).
 struct StagedSmem {
-  uint32_t q, w, lvid, kd, ko, sc, total;
+  uint32_t q, w, kd, ko, sc, total;
 };
 __host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, bool p1_weight,
                                                            uint32_t rec_max, uint32_t max_lv,
@@ -106,7 +113,6 @@ __host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, boo
   uint32_t o = pad16(rec_max);
   L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
   L.w = o;    o += p1_weight ? pad16(sizeT * max_lv) : 0u;
-  L.lvid = o; o += pad16(2u * nv * chunk);
   L.kd = o;   o += pad16(sizeT * nv * chunk);
   L.ko = o;   o += pad16(sizeT * np * chunk);
   L.sc = o;   o += scale ? pad16(sizeT * chunk) : 0u;
@@ -115,7 +121,7 @@ __host__ __device__ __forceinline__ StagedSmem staged_smem(int D, int sizeT, boo
 }
 
 struct ElasSmem {
-  uint32_t q, coef, lvid, cg, lm, total;
+  uint32_t q, coef, cg, lm, total;
 };
 __host__ __device__ __forceinline__ ElasSmem elas_smem(int D, int sizeT, uint32_t rec_max,
                                                        uint32_t max_lv, uint32_t chunk) {
@@ -124,7 +130,6 @@ __host__ __device__ __forceinline__ ElasSmem elas_smem(int D, int sizeT, uint32_
   uint32_t o = pad16(rec_max);
   L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
   L.coef = o; o += pad16(2u * sizeT * max_lv);
-  L.lvid = o; o += pad16(2u * nv * chunk);
   L.cg = o;   o += pad16(sizeT * nv * D * chunk);
   L.lm = o;   o += pad16(2u * sizeT * chunk);
   L.total = o;
@@ -141,7 +146,6 @@ __host__ __device__ __forceinline__ StagedSmem boundary_smem(int D, int sizeT, b
   uint32_t o = pad16(rec_max);
   L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
   L.w = o;    o += p1_weight ? pad16(sizeT * max_lv) : 0u;
-  L.lvid = o; o += pad16(2u * nv * chunk);
   L.kd = o;   o += pad16(sizeT * nv * chunk);
   L.ko = o;   o += pad16(sizeT * np * chunk);
   L.sc = o;
@@ -158,7 +162,6 @@ __host__ __device__ __forceinline__ StagedSmem general_smem(int D, int sizeT, ui
   uint32_t o = pad16(rec_max);
   L.q = o;    o += pad16((D == 3 ? 32u : 16u) * max_lv);
   L.w = o;
-  L.lvid = o; o += pad16(2u * nv * chunk);
   L.kd = o;   o += pad16(sizeT * nv * chunk);
   L.ko = o;   o += pad16(2u * sizeT * np * chunk);
   L.sc = o;
@@ -166,16 +169,15 @@ __host__ __device__ __forceinline__ StagedSmem general_smem(int D, int sizeT, ui
   return L;
 }
 
-// Shared-memory layout of the P_k mass kernel: local node of each element node (lvid),
-// the |det B| of each element (sc) and the constant table (diagonal, then pairs).
+// Shared-memory layout of the P_k mass kernel: the |det B| of each element (sc) and the
+// constant table (diagonal, then pairs).
 struct PkSmem {
-  uint32_t lvid, sc, tab, total;
+  uint32_t sc, tab, total;
 };
 __host__ __device__ __forceinline__ PkSmem pk_smem(uint32_t nv, uint32_t np, int sizeT, uint32_t rec_max,
                                                    uint32_t chunk) {
   PkSmem L;
   uint32_t o = pad16(rec_max);
-  L.lvid = o; o += pad16(2u * nv * chunk);
   L.sc = o;   o += pad16(sizeT * chunk);
   L.tab = o;  o += pad16(sizeT * (nv + np));
   L.total = o;
