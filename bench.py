@@ -303,11 +303,12 @@ def chunk_algorithmic_bytes(p, prec, info, points=None, block=1, matrices=1, ext
     extra_reads (coefficients); counts are exact, from the plan."""
     d = p.d
     npts = p.nq if points is None else points
-    sT = 8 if prec == 0 else 4
+    sT = 4 if prec == 1 else 8  # CSR values: FP32 form float, FP64 and F64X double
+    sP = 4 if prec == 1 else 8  # partials: FP32 float, FP64 double, F64X float pair
     lv, le = info["local_vertices"], info["local_edges"]
     pv, pe = info["partial_vertices"], info["partial_edges"]
     reads = info["plan_bytes"] + 8 * d * npts + extra_reads
-    writes = ((lv - pv) * sT + (le - pe) * 2 * sT + (pv + pe) * 8) * block * matrices
+    writes = ((lv - pv) * sT + (le - pe) * 2 * sT + (pv + pe) * sP) * block * matrices
     return reads + writes
 
 

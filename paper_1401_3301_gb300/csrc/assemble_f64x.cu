@@ -136,6 +136,13 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
   uint16_t* slow = (uint16_t*)(smem + S.sc);
   if (threadIdx.x == 0) nslow = 0;
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  double xr[D];
+  {
+    const int64_t v0 = A.me0[e0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
+  }
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -152,12 +159,6 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
 
   // 0. coordinates relative to corner 0 of the chunk's first element (FP64), split into
   //    float pairs; the reference does not depend on the record's vertex order
-  double xr[D];
-  {
-    const int64_t v0 = A.me0[e0];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
-  }
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     x64_stage_vertex<D>(A.q, A.nq, vid, xr, smem + S.q, u);

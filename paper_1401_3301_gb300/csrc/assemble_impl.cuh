@@ -198,19 +198,14 @@ struct Acc<float> {
   __device__ __forceinline__ void add(float x) { s.add(x); }
   __device__ __forceinline__ void add_scaled(float x, float f) { s.add(x * f); }
   __device__ __forceinline__ float value() const { return s.value(); }
-  __device__ __forceinline__ void store_partial(void* p, int64_t i) const {
-    ((float2*)p)[i] = make_float2(s.s, s.c);
-  }
+  // a chunk's partial sum is stored rounded to one float (4 bytes of partial traffic
+  // instead of 8; the rounding adds at most 2^-24 of the partial's magnitude, and the
+  // fixup sums the partials with compensation again)
+  __device__ __forceinline__ void store_partial(void* p, int64_t i) const { ((float*)p)[i] = s.value(); }
   __device__ __forceinline__ static Acc from_partial(const void* p, int64_t i) {
-    const float2 v = ((const float2*)p)[i];
-    Acc a(v.x);
-    a.s.c = v.y;
-    return a;
+    return Acc(((const float*)p)[i]);
   }
-  __device__ __forceinline__ void add_partial(const void* p, int64_t i) {
-    const float2 v = ((const float2*)p)[i];
-    s.add2(v.x, v.y);
-  }
+  __device__ __forceinline__ void add_partial(const void* p, int64_t i) { s.add(((const float*)p)[i]); }
   __device__ __forceinline__ void add_acc(const Acc& o) { s.add2(o.s.s, o.s.c); }
   __device__ __forceinline__ void scale2() {  // exact: every rounding of the sum scales by 2
     s.s *= 2.f;
@@ -376,6 +371,8 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = staged_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, DEFER);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -392,7 +389,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __res
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   // 0. vertex coordinates of the chunk (the record carries each corner's local vertex)
-  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
@@ -485,6 +481,8 @@ __global__ void __launch_bounds__(THREADS) k_chunk_ilv(StagedArgs A, T* __restri
   const IlvLayout R = ilv_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const IlvSmem S = ilv_smem(D, (int)sizeof(T), KIND == K_WMASS_P1, A.rec_max, A.max_lv, max_slots);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* corner = (const uint16_t*)(smem + R.corner);
   const uint16_t* vpos = (const uint16_t*)(smem + R.vpos);
@@ -500,7 +498,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_ilv(StagedArgs A, T* __restri
   if (!FE_RECORD_VALID_ILV(smem, R, ne, NV, NP, nlv, nle, A.nq, A.nnz, A.npart, max_slots, A.st, c)) return;
 
   // 0. vertex coordinates (and P1 weights) of the chunk
-  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
@@ -570,7 +567,8 @@ __global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nsh) return;
   const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
-  const int32_t d0 = sh_dst[2 * g], d1 = sh_dst[2 * g + 1];
+  const int2 dd = reinterpret_cast<const int2*>(sh_dst)[g];  // (i,j) and (j,i) in one load
+  const int32_t d0 = dd.x, d1 = dd.y;
   if (!FE_FIXUP_VALID(s, t, npart, d0, d1, g >= nsh_v, nnz, st, g)) return;
   AccT acc = AccT::from_partial(partials, s);
   int32_t i = s + 1;

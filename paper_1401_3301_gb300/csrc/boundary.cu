@@ -210,6 +210,13 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary_x(StagedArgs A, cons
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = boundary_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  double xr[D];
+  {
+    const int64_t v0 = me0[e0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
+  }
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -224,12 +231,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_boundary_x(StagedArgs A, cons
   float2* wl = (float2*)(smem + S.w);
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
-  double xr[D];
-  {
-    const int64_t v0 = me0[e0];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
-  }
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     x64_stage_vertex<D>(A.q, A.nq, vid, xr, smem + S.q, u);

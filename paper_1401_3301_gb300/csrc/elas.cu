@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle, true);
   const ElasSmem S = elas_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -118,7 +120,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas(ElasArgs A, T* __restric
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, D, A.nq, A.nnz, A.npart, A.st, c)) return;
 
   // 0. coordinates (and P1 Lame values) of the chunk's vertices
-  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     stage_vertex<D, T>(A.q, A.nq, vid, smem + S.q, u, xr.ptr());
@@ -359,6 +360,13 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle, true);
   const ElasSmem S = elas_smem(D, 8, A.rec_max, A.max_lv, A.chunk);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  double xr[D];
+  {
+    const int64_t v0 = A.me0[e0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
+  }
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -378,12 +386,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_elas_x(ElasArgs A, double* __
 
   // 0. coordinates relative to corner 0 of the chunk's first element, split into float
   //    pairs; P1 Lame values; local vertex of each corner
-  double xr[D];
-  {
-    const int64_t v0 = A.me0[e0];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
-  }
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int64_t vid = lv_vid[u];
     x64_stage_vertex<D>(A.q, A.nq, vid, xr, smem + S.q, u);

@@ -303,6 +303,8 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = general_smem(D, (int)sizeof(T), A.rec_max, A.max_lv, A.chunk);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -316,7 +318,6 @@ __global__ void __launch_bounds__(THREADS) k_chunk_general(GeneralArgs A, T* __r
   T2* Ko = (T2*)(smem + S.ko);
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
-  const ChunkRef<D> xr(A.q, A.nq, sizeof(T) == 4 ? A.me0 : nullptr, e0);
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     stage_vertex<D, T>(A.q, A.nq, lv_vid[u], smem + S.q, u, xr.ptr());
   }
@@ -551,6 +552,13 @@ __global__ void __launch_bounds__(THREADS, P1 ? 2 : 3) k_chunk_general_x(General
   const RecLayout R = rec_layout((uint32_t)ne, NV, NP, (uint32_t)nlv, (uint32_t)nle);
   const StagedSmem S = general_smem(D, 8, A.rec_max, A.max_lv, A.chunk);
   if (!FE_CHUNK_FITS(R.total <= A.rec_max && nlv <= (int32_t)A.max_lv, A.st, c)) return;
+  // reference vertex of the chunk, loaded while the record copy is in flight
+  double xr[D];
+  {
+    const int64_t v0 = A.me0[e0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
+  }
   if (!load_plan_record(smem, &bar, A.rec, A.rec_off16, c, R.total, A.st, e0, kBarrierSpin)) return;
   const uint16_t* inc_v = (const uint16_t*)(smem + R.inc_v);
   const uint16_t* inc_e = (const uint16_t*)(smem + R.inc_e);
@@ -564,12 +572,6 @@ __global__ void __launch_bounds__(THREADS, P1 ? 2 : 3) k_chunk_general_x(General
   float4* Ko = (float4*)(smem + S.ko);  // (E_ab, E_ba) of each element pair as two float pairs
   if (!FE_RECORD_VALID(smem, R, ne, NV, NP, nlv, nle, 1, A.nq, A.nnz, A.npart, A.st, c)) return;
 
-  double xr[D];
-  {
-    const int64_t v0 = A.me0[e0];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xr[k] = __ldg(A.q + k * A.nq + v0);
-  }
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     x64_stage_vertex<D>(A.q, A.nq, lv_vid[u], xr, smem + S.q, u);
   }
