@@ -233,9 +233,8 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args 
   }
 }
 
-template <int D, int KIND>
+template <int D, int KIND, int THREADS>
 int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
-  constexpr int THREADS = 256;
   const StagedSmem L = staged_smem(D, 8, KIND == K_WMASS_P1, A.rec_max, A.max_lv, A.chunk, true);
   if (L.total > kSmemDynMax) return FE_ERR_ARG;
   auto kern = k_chunk_f64x<D, KIND, THREADS>;
@@ -256,14 +255,22 @@ int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   return FE_OK;
 }
 
-template <int D>
+template <int D, int THREADS>
 int launch_kind(fe_pattern_s* h, int kind, const X64Args& A, double* vals, cudaStream_t s) {
   switch (kind) {
-    case K_MASS: return launch<D, K_MASS>(h, A, vals, s);
-    case K_WMASS_P1: return launch<D, K_WMASS_P1>(h, A, vals, s);
-    case K_WMASS_P0: return launch<D, K_WMASS_P0>(h, A, vals, s);
-    default: return launch<D, K_STIFF>(h, A, vals, s);
+    case K_MASS: return launch<D, K_MASS, THREADS>(h, A, vals, s);
+    case K_WMASS_P1: return launch<D, K_WMASS_P1, THREADS>(h, A, vals, s);
+    case K_WMASS_P0: return launch<D, K_WMASS_P0, THREADS>(h, A, vals, s);
+    default: return launch<D, K_STIFF, THREADS>(h, A, vals, s);
   }
+}
+
+// threads per block of the pattern (fe_pattern_set_threads): 128, 256 (default) or 512
+template <int D>
+int launch_threads(fe_pattern_s* h, int kind, const X64Args& A, double* vals, cudaStream_t s) {
+  if (h->threads == 128) return launch_kind<D, 128>(h, kind, A, vals, s);
+  if (h->threads == 512) return launch_kind<D, 512>(h, kind, A, vals, s);
+  return launch_kind<D, 256>(h, kind, A, vals, s);
 }
 
 }  // namespace
@@ -276,6 +283,6 @@ int fe_launch_f64x(fe_pattern_s* h, int kind, const double* q, const void* w, in
   X64Args A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, (const double*)w,
             w_kind, h->order, h->me_int, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status,
             h->nnz_s, h->npart};
-  if (h->d == 3) return launch_kind<3>(h, kind, A, (double*)vals, s);
-  return launch_kind<2>(h, kind, A, (double*)vals, s);
+  if (h->d == 3) return launch_threads<3>(h, kind, A, (double*)vals, s);
+  return launch_threads<2>(h, kind, A, (double*)vals, s);
 }
