@@ -280,19 +280,29 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(form):
-    """DRAM bytes per launch of the chunk kernel from the committed ncu summary, if the
-    kernel sources are unchanged since it was taken."""
+def committed_profile(form, cfg):
+    """The committed ncu counters (profiles/traffic.json) of the form's chunk kernel in the
+    configuration (chunk, record layout, threads) of this run's pattern, if the kernel
+    sources are unchanged since they were taken; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            t = json.load(f)
-        ent = t[form]
-        if ent.get("source_hash") != kernel_source_hash():
-            return None
-        return ent["bytes_per_launch"] * ent.get("scale_to_workload", 1.0)
-    except Exception:
+            entries = json.load(f)[form]
+    except (OSError, ValueError, KeyError):
         return None
+    for ent in entries:
+        got = ent.get("configuration", {})
+        if ent.get("source_hash") == kernel_source_hash() and all(
+                got.get(k) == cfg.get(k) for k in ("chunk", "layout", "threads")):
+            return ent
+    return None
+
+
+def committed_traffic(form, cfg):
+    """DRAM bytes (read + write) per launch of the chunk kernel at this workload's size,
+    from the committed counters (scaled from the captured mesh by the number of tets)."""
+    ent = committed_profile(form, cfg)
+    return None if ent is None else ent["bytes_per_launch"] * ent.get("scale_to_workload", 1.0)
 
 
 def chunk_algorithmic_bytes(p, prec, info, points=None, block=1, matrices=1, extra_reads=0):
@@ -312,20 +322,25 @@ def chunk_algorithmic_bytes(p, prec, info, points=None, block=1, matrices=1, ext
     return reads + writes
 
 
-def fp64_instr_per_tet():
+def fixup_algorithmic_bytes(prec, info):
+    """Bytes the fixup must move per launch: per shared vertex / edge its list bound (4 B)
+    and destinations (8 B), its partial sums (4 B each in the FP32 form, else 8 B), and the
+    values it writes (one per shared vertex, two per shared edge)."""
+    nsh_v, nsh_e = info["shared_vertices"], info["shared_edges"]
+    npart = info["partial_vertices"] + info["partial_edges"]
+    sT = 4 if prec == 1 else 8
+    sP = 4 if prec == 1 else 8
+    return 4 * (nsh_v + nsh_e + 1) + 8 * (nsh_v + nsh_e) + sP * npart + sT * (nsh_v + 2 * nsh_e)
+
+
+def fp64_instr_per_tet(cfg):
     """FP64-pipe instructions (DADD + DMUL + DFMA) per tet of the FP64 chunk kernel and
-    their mix: ncu-counted when the committed profile matches the current kernel sources,
-    else the count from the source (edges 9, cofactors 18, det 3, 1/(6|det|) 5, Gram 18,
-    scaling 6, row sums 8, about 8 incidence sums) and no mix."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as f:
-            ent = json.load(f)["f64"]
-        if ent.get("source_hash") == kernel_source_hash() and "fp64_instr_per_tet" in ent:
-            return (float(ent["fp64_instr_per_tet"]), "ncu (profiles/traffic.json)",
-                    ent.get("fp64_instr_mix_per_tet"))
-    except Exception:
-        pass
+    their mix: ncu-counted when a committed profile matches the current kernel sources and
+    configuration, else the count from the source (edges 9, cofactors 18, det 3,
+    1/(6|det|) 5, Gram 18, scaling 6, row sums 8, about 8 incidence sums) and no mix."""
+    ent = committed_profile("f64", cfg)
+    if ent is not None and "fp64_instr_per_tet" in ent:
+        return (float(ent["fp64_instr_per_tet"]), "ncu (profiles/traffic.json)", ent.get("fp64_instr_mix_per_tet"))
     return 75.0, "from source", None
 
 
@@ -418,7 +433,7 @@ def run_gpu(args):
         dom_ms = prof[dom][0] / prof[dom][1]
         abytes = chunk_algorithmic_bytes(p, fe.F64 if prec == fe.F64X else prec, info)
         achieved = abytes / (dom_ms * 1e-3) / 1e9
-        traffic = committed_traffic(prec_name)
+        traffic = committed_traffic(prec_name, tuning.get(prec_name, {}))
         roof_hbm = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "traffic": traffic,
                     "algorithmic_bytes_per_launch": abytes, "kernel_ms": dom_ms,
@@ -429,6 +444,14 @@ def run_gpu(args):
                             "step_ms_median": statistics.median(step_ms), "kernels": {
                                 k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()},
                             "roofline_hbm": roof_hbm, "gpu_launches": launches}
+        if "fixup" in prof:
+            fx_ms = prof["fixup"][0] / prof["fixup"][1]
+            fx_bytes = fixup_algorithmic_bytes(prec, info)
+            forms[prec_name]["roofline_fixup"] = {
+                "bound": "hbm", "kernel": "fixup", "achieved": fx_bytes / (fx_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "frac": fx_bytes / (fx_ms * 1e-3) / 1e9 / hbm_peak,
+                "algorithmic_bytes_per_launch": fx_bytes, "kernel_ms": fx_ms,
+                "share_of_step": fx_ms / (total_ms / args.steps)}
         # path-level effective bandwidth with the per-tet bytes of the method (compulsory + slot map)
         per_tet = 94.3 if prec == fe.F32 else 104.4
         forms[prec_name]["path_effective"] = {
@@ -436,7 +459,7 @@ def run_gpu(args):
         forms[prec_name]["path_effective"]["frac"] = forms[prec_name]["path_effective"]["GBps"] / hbm_peak
         if prec == fe.F64:
             clock = sm_max
-            ipt, counted, mix = fp64_instr_per_tet()
+            ipt, counted, mix = fp64_instr_per_tet(tuning.get(prec_name, {}))
             instr = ipt * p.nme
             peak_ops = FP64_PIPE_PER_SM_CLK * SM_COUNT * clock * 1e6 / 1e9
             achieved_ops = instr / (dom_ms * 1e-3) / 1e9

@@ -559,31 +559,57 @@ __global__ void __launch_bounds__(THREADS) k_chunk_ilv(StagedArgs A, T* __restri
   }
 }
 
-// Sum of the chunk partials of each shared vertex / edge, in chunk order.
+// Sum of the chunk partials of each shared vertex / edge, in chunk order. The kernel is
+// bound by load latency rather than bandwidth, so each thread takes kFixupPer shared
+// entities (strided by the block size: every load stays coalesced) and issues the loads
+// of all of them before summing: list bounds and destinations, then the first four
+// partials of each entity; longer lists finish one partial at a time.
+constexpr int kFixupPer = 4;
 template <class T, class AccT = Acc<T>>
-__global__ void k_fixup_scalar(const int32_t* __restrict__ sh_ptr, const int32_t* __restrict__ sh_dst,
-                               int64_t nsh_v, int64_t nsh, const void* __restrict__ partials,
-                               T* __restrict__ vals, int64_t nnz, int64_t npart, fe_status_word* st) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= nsh) return;
-  const int32_t s = sh_ptr[g], t = sh_ptr[g + 1];
-  const int2 dd = reinterpret_cast<const int2*>(sh_dst)[g];  // (i,j) and (j,i) in one load
-  const int32_t d0 = dd.x, d1 = dd.y;
-  if (!FE_FIXUP_VALID(s, t, npart, d0, d1, g >= nsh_v, nnz, st, g)) return;
-  AccT acc = AccT::from_partial(partials, s);
-  int32_t i = s + 1;
-  for (; i + 2 < t; i += 3) {  // three independent loads in flight, summed in order
-    AccT b0 = AccT::from_partial(partials, i), b1 = AccT::from_partial(partials, i + 1),
-         b2 = AccT::from_partial(partials, i + 2);
-    acc.add_acc(b0);
-    acc.add_acc(b1);
-    acc.add_acc(b2);
+__global__ void __launch_bounds__(256) k_fixup_scalar(const int32_t* __restrict__ sh_ptr,
+                                                      const int32_t* __restrict__ sh_dst, int64_t nsh_v,
+                                                      int64_t nsh, const void* __restrict__ partials,
+                                                      T* __restrict__ vals, int64_t nnz, int64_t npart,
+                                                      fe_status_word* st) {
+  constexpr int E = kFixupPer, F = 4;
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x * E + threadIdx.x;
+  int32_t s[E], n[E];
+  int2 dd[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int64_t g = g0 + (int64_t)e * blockDim.x;
+    s[e] = 0;
+    n[e] = 0;
+    dd[e] = make_int2(0, 0);
+    if (g < nsh) {
+      const int32_t t = sh_ptr[g + 1];
+      s[e] = sh_ptr[g];
+      dd[e] = reinterpret_cast<const int2*>(sh_dst)[g];  // (i,j) and (j,i) in one load
+      n[e] = FE_FIXUP_VALID(s[e], t, npart, dd[e].x, dd[e].y, g >= nsh_v, nnz, st, g) ? t - s[e] : 0;
+    }
   }
-  for (; i < t; ++i) acc.add_partial(partials, i);
-  const T val = acc.value();
-  vals[d0] = val;
-  if (g >= nsh_v) vals[d1] = val;
+  AccT p[E][F];
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int k = 0; k < F; ++k)
+      if (k < n[e]) p[e][k] = AccT::from_partial(partials, (int64_t)s[e] + k);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (n[e] == 0) continue;
+    AccT acc = p[e][0];
+#pragma unroll
+    for (int k = 1; k < F; ++k)
+      if (k < n[e]) acc.add_acc(p[e][k]);
+    for (int32_t i = s[e] + F; i < s[e] + n[e]; ++i) acc.add_partial(partials, i);
+    const T val = acc.value();
+    vals[dd[e].x] = val;
+    if (g0 + (int64_t)e * blockDim.x >= nsh_v) vals[dd[e].y] = val;
+  }
 }
+
+// grid of the fixup: kFixupPer shared entities per thread, 256 threads per block
+static inline int fixup_grid(int64_t nsh) { return fe_grid(nsh, 256 * kFixupPer); }
 
 // ---------------------------------------------------------------- FE_REASM_GATHER
 // Pass 1: full local matrix of each element, column-wise, at kg[e*S + b*NV + a].
