@@ -78,9 +78,12 @@ class _DeviceInt16:
 
 
 def corrupted(fe) -> dict:
-    """Bounds-checked build only: corrupt the first vertex incidence code of chunk 1's
-    plan record (a duplicate of the second, or an out-of-range code) and assemble with
-    every chunked kernel. Each must report FE_ERR_BOUNDS for chunk 1 and skip it."""
+    """Bounds-checked build only: corrupt chunk 1's plan record and assemble with every
+    chunked kernel. The first word of the record is the local vertex of the chunk's first
+    element corner: "duplicate" copies the second corner's into it, "range" makes it
+    0xFFFF. For the tetrahedral patterns (chunk 1 full, 512 elements of 4 corners, so the
+    vertex incidence lists start at word 2048) "inc" duplicates the second incidence code
+    of the first list into the first. Each must report FE_ERR_BOUNDS for chunk 1 and skip it."""
     import torch
     from paper_1401_3301_gb300 import meshgen
     assert "bounds-checked" in fe.fe_version()  # the normal build would read out of bounds
@@ -111,17 +114,21 @@ def corrupted(fe) -> dict:
         "pk2/f64x": (lambda: fe.fe_pk_pattern(qk, cuda(mk.me), 2),
                      lambda p: fe.fe_assemble_mass(p, qk, prec=fe.F64X)),
     }
+    tet = {"stiff/f64", "stiff/f32", "stiff/f64x", "general", "general/f64x", "elas", "elas/f64x"}
     out = {}
     for name, (make, assemble) in cases.items():
-        for how in ("duplicate", "range"):
+        for how in ("duplicate", "range", "inc") if name in tet else ("duplicate", "range"):
             p = make()
             assert p.nme > p.plan_info()["chunk"], name  # chunk 1 exists
             ptr, nbytes = p.plan_record(1)
             rec = torch.as_tensor(_DeviceInt16(ptr, nbytes // 2), device="cuda")
             if how == "duplicate":
                 rec[0] = rec[1]
-            else:
+            elif how == "range":
                 rec[0] = -1  # 0xFFFF
+            else:
+                assert p.plan_info()["chunk"] == 512, name
+                rec[2048] = rec[2049]
             torch.cuda.synchronize()
             assemble(p)
             out[f"{name}/{how}"] = p.status()

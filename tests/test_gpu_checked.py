@@ -36,7 +36,7 @@ def test_checked_build_matches_normal_build(tmp_path):
     assert "bounds-checked" not in fe.fe_version()
     # a corrupted plan record is reported (FE_ERR_BOUNDS, chunk 1) by every chunked kernel
     bad = {k: tuple(got.pop(k)) for k in list(got) if k.startswith("corrupted:")}
-    assert len(bad) == 22, sorted(bad)
+    assert len(bad) == 29, sorted(bad)
     for name, st in bad.items():
         assert st == (9, 1), (name, st)
 
