@@ -355,8 +355,12 @@ constexpr uint32_t kBarrierSpin = 1u << 22;
 //  2. each distinct vertex / edge sums its incidences in ascending element order and
 //     stores the sum in the CSR value (both (i,j) and (j,i) for an edge: the
 //     operators are symmetric) or in its partial-sum slot.
+// FP32 form: registers capped so that 6 blocks of 256 threads fit on an SM (40 per
+// thread): the kernel is bound by the latency of each block's dependent steps, and more
+// resident blocks hide more of it (chunk 384: 0.241 -> 0.209 ms at N=100). The FP64 form
+// is bound by the FP64 pipe and keeps the compiler's choice.
 template <int D, class T, int KIND, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_chunk_staged(StagedArgs A, T* __restrict__ vals,
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 1536 / THREADS : 1) k_chunk_staged(StagedArgs A, T* __restrict__ vals,
                                                           void* __restrict__ partials) {
   constexpr int NV = D + 1, NP = Pairs<D>::n;
   // FP64 stiffness: apply each element's scale while summing (FMA) instead of per entry
