@@ -689,8 +689,8 @@ def wl_batched(fe, torch, K, W, flush, hbm_peak, replays=1000, count=256):
     """The 256-mesh 2D batch: weighted mass + stiffness with fresh lognormal(0, 1)
     per-element weights every step, one fused persistent kernel (+ one fixup) on the
     pattern the autotuner picks for the batch, captured with the weight draw in a CUDA
-    graph and replayed `replays` times (the time per replay is reported). The F64X form
-    has no fused kernel and runs the two operators' kernels."""
+    graph and replayed `replays` times (the time per replay is reported). The F64X form's
+    fused kernel takes one block per chunk and runs one fixup per matrix."""
     from paper_1401_3301_gb300 import meshgen, tune
     sizes = meshgen.batch_sizes(0, count, 16, 512)
     meshes = [meshgen.square_mesh(int(n), seed=b + 1) for b, n in enumerate(sizes)]
@@ -708,27 +708,19 @@ def wl_batched(fe, torch, K, W, flush, hbm_peak, replays=1000, count=256):
     res, tuning = {}, {}
     for name, prec, T in _forms(fe, torch):
         w = torch.ones(ntri, dtype=T, device="cuda")
-        if prec == fe.F64X:
-            p = p0
-            s_ = torch.empty(p.nnz, dtype=T, device="cuda")
-            m_ = torch.empty(p.nnz, dtype=T, device="cuda")
 
-            def assemble():
-                fe.fe_assemble_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=s_)
-                fe.fe_assemble_wmass(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals=m_)
-        else:
-            def make(flags, _qs=qs, _mes=mes):
-                return fe.fe_batch_pattern(_qs, _mes, flags=flags)
-            best = tune.autotune(qu, torch.empty((3, ntri), device="meta"), "wmass_stiff", prec, w=w,
-                                 w_kind=fe.COEF_P0_INTERNAL, pattern=make, tag=f"batch{count}", reps=5)
-            p = tune.tuned_pattern(qu, torch.empty((3, ntri), device="meta"), "wmass_stiff", prec, w=w,
-                                   w_kind=fe.COEF_P0_INTERNAL, pattern=make, tag=f"batch{count}", reps=5)
-            tuning[name] = {k: best.get(k) for k in ("chunk", "layout", "threads", "persistent")}
-            s_ = torch.empty(p.nnz, dtype=T, device="cuda")
-            m_ = torch.empty(p.nnz, dtype=T, device="cuda")
+        def make(flags, _qs=qs, _mes=mes):
+            return fe.fe_batch_pattern(_qs, _mes, flags=flags)
+        best = tune.autotune(qu, torch.empty((3, ntri), device="meta"), "wmass_stiff", prec, w=w,
+                             w_kind=fe.COEF_P0_INTERNAL, pattern=make, tag=f"batch{count}", reps=5)
+        p = tune.tuned_pattern(qu, torch.empty((3, ntri), device="meta"), "wmass_stiff", prec, w=w,
+                               w_kind=fe.COEF_P0_INTERNAL, pattern=make, tag=f"batch{count}", reps=5)
+        tuning[name] = {k: best.get(k) for k in ("chunk", "layout", "threads", "persistent")}
+        s_ = torch.empty(p.nnz, dtype=T, device="cuda")
+        m_ = torch.empty(p.nnz, dtype=T, device="cuda")
 
-            def assemble():
-                fe.fe_assemble_wmass_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals_mass=m_, vals_stiff=s_)
+        def assemble():
+            fe.fe_assemble_wmass_stiff(p, qu, w, fe.COEF_P0_INTERNAL, prec=prec, vals_mass=m_, vals_stiff=s_)
         torch.cuda.manual_seed(0)
 
         def step():
@@ -753,12 +745,10 @@ def wl_batched(fe, torch, K, W, flush, hbm_peak, replays=1000, count=256):
         kern = _kernels(p, assemble)
         p.check()
         info = p.plan_info()
-        ab = None
-        if prec != fe.F64X:
-            sT = 8 if prec == fe.F64 else 4
-            ab = chunk_algorithmic_bytes(p, prec, info, matrices=2, extra_reads=sT * ntri)
+        sT = 4 if prec == fe.F32 else 8
+        ab = chunk_algorithmic_bytes(p, 0 if prec == fe.F64X else prec, info, matrices=2, extra_reads=sT * ntri)
         res[name] = _entry(ntri, mean, mean, kern, ab, hbm_peak, replays=replays,
-                           launches_per_step=2 if prec != fe.F64X else 4)
+                           launches_per_step=2 if prec != fe.F64X else 3)
     return {"metric": "Batched 2D weighted mass + stiffness reassembly with fresh lognormal weights, Mtris/s "
                       f"(CUDA graph, {replays} replays)", "unit": "Mtris/s",
             "config": {"workload": f"{count} jittered unit-square meshes, N uniform in [16, 512] ({ntri:,} "

@@ -275,8 +275,8 @@ int fe_pattern_plan_info(fe_pattern_h h, int64_t* chunk, int64_t* local_vertices
                          int64_t* shared_vertices, int64_t* shared_edges, int64_t* plan_bytes);
 
 /* Device address and size in bytes of the plan record of element chunk c (the
- * layout is in csrc/plan.cuh; it starts with the uint16 vertex incidence codes
- * e_local * nv + a). Borrowed: owned by the handle, valid until fe_pattern_destroy,
+ * layout is in csrc/plan.cuh; it starts with the uint16 local vertex of each element
+ * corner, at e_local * nv + a). Borrowed: owned by the handle, valid until fe_pattern_destroy,
  * read by every chunked assembly. Synchronises the device to read the offsets.
  * FE_ERR_ARG for c outside [0, nchunks) or a handle without a chunk plan. */
 int fe_pattern_plan_record(fe_pattern_h h, int64_t c, const void** rec, int64_t* bytes);
@@ -335,7 +335,8 @@ int fe_assemble_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_
  * reads each plan record once, forms each element's geometry once and keeps both
  * matrices' sums in the separate calls' order; one fixup completes the shared
  * entries. w_kind: FE_COEF_NONE, FE_COEF_P0 or FE_COEF_P0_INTERNAL (w NULL only for
- * NONE). prec: FE_F64 or FE_F32 (FE_F64X: FE_ERR_ARG). Pattern: m = 1 volume pattern
+ * NONE). prec: FE_F64, FE_F32 or FE_F64X (w and both value arrays then FP64; one block per
+ * chunk whatever the launch shape, and one fixup per matrix). Pattern: m = 1 volume pattern
  * from fe_pattern or fe_batch_pattern, chunked strategy (else FE_ERR_ARG). The two
  * value arrays must be distinct, nnz entries each. Asynchronous on `stream`; launch
  * shape as set by fe_pattern_set_persistent.

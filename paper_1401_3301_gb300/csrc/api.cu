@@ -20,6 +20,8 @@ int fe_launch_pair_f64(fe_pattern_s* h, const double* q, const void* w, int w_ki
                        void* vals_stiff, cudaStream_t s);
 int fe_launch_pair_f32(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals_mass,
                        void* vals_stiff, cudaStream_t s);
+int fe_launch_pair_f64x(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals_mass,
+                        void* vals_stiff, cudaStream_t s);
 int fe_launch_f64x(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, void* vals,
                    cudaStream_t s);
 int fe_launch_boundary(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, int prec,
@@ -318,7 +320,7 @@ int fe_assemble_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_
 
 int fe_assemble_wmass_stiff(fe_pattern_h h, const double* q, const void* w, int32_t w_kind, int32_t prec,
                             void* vals_mass, void* vals_stiff, void* stream) {
-  FE_TRY(check_common(h, q, prec, vals_mass));
+  FE_TRY(check_common(h, q, prec == FE_F64X ? FE_F64 : prec, vals_mass));  // F64X: double values
   if (!vals_stiff || vals_stiff == vals_mass) return FE_ERR_ARG;
   if (h->m != 1 || h->kdim != h->d || h->pk != 1) return FE_ERR_ARG;
   if (h->flags & FE_PATTERN_INTERLEAVED) return FE_ERR_ARG;
@@ -326,6 +328,7 @@ int fe_assemble_wmass_stiff(fe_pattern_h h, const double* q, const void* w, int3
   if (w_kind != FE_COEF_NONE && !w) return FE_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (prec == FE_F64) return fe_launch_pair_f64(h, q, w, w_kind, vals_mass, vals_stiff, s);
+  if (prec == FE_F64X) return fe_launch_pair_f64x(h, q, w, w_kind, vals_mass, vals_stiff, s);
   return fe_launch_pair_f32(h, q, w, w_kind, vals_mass, vals_stiff, s);
 }
 

@@ -273,8 +273,21 @@ int launch_threads(fe_pattern_s* h, int kind, const X64Args& A, double* vals, cu
   return launch_kind<D, 256>(h, kind, A, vals, s);
 }
 
+#include "assemble_pair_f64x.inc"
+
 }  // namespace
 }  // namespace fe
+
+int fe_launch_pair_f64x(fe_pattern_s* h, const double* q, const void* w, int w_kind, void* vals_mass,
+                        void* vals_stiff, cudaStream_t s) {
+  using namespace fe;
+  if (h->strategy != FE_REASM_CHUNKED) return FE_ERR_ARG;
+  X64Args A{h->nme, h->nq, h->chunk, (uint32_t)h->rec_max_bytes, (uint32_t)h->max_lv, q, (const double*)w,
+            w_kind, h->order, h->me_int, h->ch_v_ptr, h->ch_e_ptr, h->rec, h->rec_off16, h->status,
+            h->nnz_s, h->npart};
+  if (h->d == 3) return launch_pair_x_threads<3>(h, A, (double*)vals_mass, (double*)vals_stiff, s);
+  return launch_pair_x_threads<2>(h, A, (double*)vals_mass, (double*)vals_stiff, s);
+}
 
 int fe_launch_f64x(fe_pattern_s* h, int kind, const double* q, const void* w, int w_kind, void* vals,
                    cudaStream_t s) {

@@ -100,9 +100,8 @@ def autotune(q: torch.Tensor, me: torch.Tensor, kind: str = "stiff", prec: int =
     if use_cache and key in cache:
         return cache[key]
     T = torch.float32 if prec == fe.F32 else torch.float64
-    if prec == fe.F64X:
-        threads = (256,)  # the F64X kernel's block size is fixed; the setting does not reach it
-    shapes = PERSISTENT if kind == "wmass_stiff" else (True,)
+    # the launch shape applies to the FP64 / FP32 fused kernel only (F64X: one block per chunk)
+    shapes = PERSISTENT if kind == "wmass_stiff" and prec != fe.F64X else (True,)
     results = []
     vals = vals2 = None
     if kind not in ("stiff", "mass", "wmass") or prec == fe.F64X:

@@ -2,10 +2,11 @@
 coefficient in one pass (one chunk kernel, persistent or one block per chunk, and one
 fixup), for repeated reassembly with fresh coefficients.
 
-Checked through the C ABI: bit for bit against the separate calls fe_assemble_wmass and
-fe_assemble_stiff (same summation order), against the FP64 oracle for both operators,
-over chunk sizes, threads per block and both launch shapes, on a single 3D mesh and on a
-batch of 2D meshes; a CUDA-graph replay with fresh weights equals direct calls bit for bit.
+Checked through the C ABI, in the FP64, FP32 and F64X forms: bit for bit against the
+separate calls fe_assemble_wmass and fe_assemble_stiff (same summation order), against the
+FP64 oracle for both operators, over chunk sizes, threads per block and both launch shapes,
+on a single 3D mesh and on a batch of 2D meshes; a CUDA-graph replay with fresh weights
+equals direct calls bit for bit.
 """
 import numpy as np
 import pytest
@@ -17,12 +18,12 @@ from helpers import check_values, fe_or_skip, to_cuda
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("chunk,threads,persistent", [(256, 128, True), (512, 256, False), (1024, 512, True)])
 def test_pair_matches_separate_calls_and_oracle_3d(prec, chunk, threads, persistent):
     fe = fe_or_skip()
     import torch
-    T = torch.float64 if prec == 0 else torch.float32
+    T = torch.float32 if prec == 1 else torch.float64
     m = meshgen.kuhn_cube_mesh(9, seed=61)
     q, me = to_cuda(m.q), to_cuda(m.me)
     p = fe.fe_pattern(q, me, flags=fe.PATTERN_CHUNK(chunk))
@@ -44,11 +45,11 @@ def test_pair_matches_separate_calls_and_oracle_3d(prec, chunk, threads, persist
     assert torch.equal(vs0, fe.fe_assemble_stiff(p, q, prec=prec))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_pair_on_a_batch_of_2d_meshes_with_graph_replay(prec):
     fe = fe_or_skip()
     import torch
-    T = torch.float64 if prec == 0 else torch.float32
+    T = torch.float32 if prec == 1 else torch.float64
     sizes = [7, 16, 3, 25, 11]
     meshes = [meshgen.square_mesh(n, seed=70 + b) for b, n in enumerate(sizes)]
     qs = [to_cuda(x.q) for x in meshes]
@@ -98,8 +99,6 @@ def test_pair_rejects_unsupported_calls():
     q, me = to_cuda(m.q), to_cuda(m.me)
     p = fe.fe_pattern(q, me)
     v = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
-    with pytest.raises(fe.FEError):  # F64X form
-        fe.fe_assemble_wmass_stiff(p, q, prec=fe.F64X)
     with pytest.raises(fe.FEError):  # one array for both matrices
         fe.fe_assemble_wmass_stiff(p, q, vals_mass=v, vals_stiff=v)
     with pytest.raises(fe.FEError):  # P1 coefficient
