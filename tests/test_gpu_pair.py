@@ -108,3 +108,21 @@ def test_pair_rejects_unsupported_calls():
         fe.fe_assemble_wmass_stiff(p, q)
     with pytest.raises(fe.FEError):  # launch shape other than 0 / 1
         fe._check(fe.lib().fe_pattern_set_persistent(p.handle, 2))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_pair_on_badly_shaped_elements(prec):
+    # slivers, caps and needles take the recomputation paths of the FP32 and F64X forms
+    # (FP64 det B / whole element from the FP64 coordinates); the fused kernel must take
+    # them for both matrices exactly as the separate calls do
+    fe = fe_or_skip()
+    import torch
+    T = torch.float32 if prec == 1 else torch.float64
+    m = meshgen.badly_shaped_mesh(3, [1e-2, 1e-4, 1e-6, 1e-8, 1e-10], seed=63)
+    q, me = to_cuda(m.q), to_cuda(m.me)
+    p = fe.fe_pattern(q, me)
+    wt = to_cuda(meshgen.element_weights(64, m.nme)).to(T)
+    vm, vs = fe.fe_assemble_wmass_stiff(p, q, wt, fe.COEF_P0, prec=prec)
+    assert p.status() == (0, -1)
+    assert torch.equal(vm, fe.fe_assemble_wmass(p, q, wt, fe.COEF_P0, prec=prec))
+    assert torch.equal(vs, fe.fe_assemble_stiff(p, q, wt, fe.COEF_P0, prec=prec))
