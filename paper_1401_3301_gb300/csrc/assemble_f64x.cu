@@ -117,8 +117,11 @@ __device__ __forceinline__ void x64_element_values(const X64Args& A, int64_t e0,
   }
 }
 
+// registers capped so that 6 blocks of 256 threads fit on an SM (40 per thread, a few
+// spilled): the kernel is latency-bound like the FP32 form's (chunk 224: 0.339 -> 0.312 ms
+// at N=100)
 template <int D, int KIND, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_chunk_f64x(X64Args A, double* __restrict__ vals,
+__global__ void __launch_bounds__(THREADS, 1536 / THREADS) k_chunk_f64x(X64Args A, double* __restrict__ vals,
                                                         float2* __restrict__ partials) {
   constexpr int NV = D + 1, NP = Pairs<D>::n;
   extern __shared__ __align__(128) unsigned char smem[];

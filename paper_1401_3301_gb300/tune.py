@@ -22,7 +22,7 @@ import torch
 
 from . import build_ext, fe
 
-CHUNKS = (256, 384, 512, 768, 1024)
+CHUNKS = (224, 256, 384, 512, 768, 1024)
 THREADS = (128, 256, 512)
 PERSISTENT = (True, False)
 LAYOUTS = (0, fe.PATTERN_ENTITY_ORDER, fe.PATTERN_INTERLEAVED)
