@@ -249,7 +249,7 @@ int launch(fe_pattern_s* h, const X64Args& A, double* vals, cudaStream_t s) {
   const int64_t nsh = h->nsh_v + h->nsh_e;
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_FIXUP, s);
-    k_fixup_scalar<double, AccX><<<fixup_grid(nsh), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
+    k_fixup_scalar<double, AccX><<<fixup_grid<double>(nsh), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
                                                                   h->partials, vals, h->nnz_s, h->npart,
                                                                   h->status);
     FE_CUDA_TRY(cudaGetLastError());

@@ -564,18 +564,21 @@ __global__ void __launch_bounds__(THREADS) k_chunk_ilv(StagedArgs A, T* __restri
 }
 
 // Sum of the chunk partials of each shared vertex / edge, in chunk order. The kernel is
-// bound by load latency rather than bandwidth, so each thread takes kFixupPer shared
+// bound by load latency rather than bandwidth, so each thread takes several shared
 // entities (strided by the block size: every load stays coalesced) and issues the loads
 // of all of them before summing: list bounds and destinations, then the first four
-// partials of each entity; longer lists finish one partial at a time.
-constexpr int kFixupPer = 4;
+// partials of each entity; longer lists finish one partial at a time. Four entities per
+// thread for 8-byte values, two for the FP32 form's (more threads in flight: 0.044 ->
+// 0.042 ms at N=100, where four cost the FP64 form nothing and gained it 3 %).
+template <class T>
+constexpr int fixup_per() { return sizeof(T) == 4 ? 2 : 4; }
 template <class T, class AccT = Acc<T>>
 __global__ void __launch_bounds__(256) k_fixup_scalar(const int32_t* __restrict__ sh_ptr,
                                                       const int32_t* __restrict__ sh_dst, int64_t nsh_v,
                                                       int64_t nsh, const void* __restrict__ partials,
                                                       T* __restrict__ vals, int64_t nnz, int64_t npart,
                                                       fe_status_word* st) {
-  constexpr int E = kFixupPer, F = 4;
+  constexpr int E = fixup_per<T>(), F = 4;
   const int64_t g0 = (int64_t)blockIdx.x * blockDim.x * E + threadIdx.x;
   int32_t s[E], n[E];
   int2 dd[E];
@@ -612,8 +615,9 @@ __global__ void __launch_bounds__(256) k_fixup_scalar(const int32_t* __restrict_
   }
 }
 
-// grid of the fixup: kFixupPer shared entities per thread, 256 threads per block
-static inline int fixup_grid(int64_t nsh) { return fe_grid(nsh, 256 * kFixupPer); }
+// grid of the fixup: fixup_per<T>() shared entities per thread, 256 threads per block
+template <class T>
+static inline int fixup_grid(int64_t nsh) { return fe_grid(nsh, 256 * fixup_per<T>()); }
 
 // ---------------------------------------------------------------- FE_REASM_GATHER
 // Pass 1: full local matrix of each element, column-wise, at kg[e*S + b*NV + a].

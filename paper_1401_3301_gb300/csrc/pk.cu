@@ -332,11 +332,11 @@ int launch_pk(fe_pattern_s* h, const double* q, T* vals, cudaStream_t s) {
   if (nsh > 0) {
     FE_PROF_BEGIN(h, FE_K_FIXUP, s);
     if constexpr (X)
-      k_fixup_scalar<double, AccX><<<fixup_grid(nsh), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
+      k_fixup_scalar<double, AccX><<<fixup_grid<double>(nsh), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh,
                                                                     h->partials, vals, h->nnz_s, h->npart,
                                                                     h->status);
     else
-      k_fixup_scalar<T><<<fixup_grid(nsh), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->partials,
+      k_fixup_scalar<T><<<fixup_grid<T>(nsh), 256, 0, s>>>(h->sh_ptr, h->sh_dst, h->nsh_v, nsh, h->partials,
                                                           vals, h->nnz_s, h->npart, h->status);
     FE_CUDA_TRY(cudaGetLastError());
     FE_PROF_END(h, FE_K_FIXUP, s);
