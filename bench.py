@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1_500_000, help="tets in the CPU-baseline sample")
     ap.add_argument("--no-secondary", action="store_true",
                     help="headline only: skip the other configurations' block")
+    ap.add_argument("--batch-meshes", type=int, default=256,
+                    help="--workload batched: meshes in the batch (default 256; fewer for a profiler capture)")
+    ap.add_argument("--replays", type=int, default=1000,
+                    help="--workload batched: timed graph replays (default 1000)")
     ap.add_argument("--workload", default="stiffness",
                     choices=["stiffness", "mass", "wmass", "elas", "2d", "batched", "diff", "general", "pk",
                              "boundary"],
@@ -894,7 +898,8 @@ def run_other(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     hbm_peak, _, _ = measured_peaks()
     name = "mass" if args.workload in ("mass", "wmass") else args.workload
-    res = ALL_WORKLOADS[name](fe, torch, args.steps, args.warmup, flush, hbm_peak)
+    extra = {"count": args.batch_meshes, "replays": args.replays} if name == "batched" else {}
+    res = ALL_WORKLOADS[name](fe, torch, args.steps, args.warmup, flush, hbm_peak, **extra)
     outs = res.values() if name == "mass" else [res]
     for out in outs:
         line = {"workload": name, "data": "synthetic", "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
