@@ -432,9 +432,13 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 1536 / THREADS : 1) 
   for (int u = threadIdx.x; u < nlv; u += THREADS) {
     const int s = lv_off[u], t = lv_off[u + 1];
     Acc<T> acc = DEFER ? Acc<T>(Kd[inc_v[s]] * Sc[inc_v[s] / NV]) : Acc<T>(Kd[inc_v[s]]);
-    for (int j = s + 1; j < t; ++j) {
-      if constexpr (DEFER) acc.add_scaled(Kd[inc_v[j]], Sc[inc_v[j] / NV]);
-      else acc.add(Kd[inc_v[j]]);
+    if constexpr (DEFER) {
+      // FP64: the scaled sums run faster not unrolled (chunk kernel 0.801 -> 0.791 ms at
+      // N=100); the FP32 sums need the compiler's unrolling (0.209 against 0.227 ms)
+#pragma unroll 1
+      for (int j = s + 1; j < t; ++j) acc.add_scaled(Kd[inc_v[j]], Sc[inc_v[j] / NV]);
+    } else {
+      for (int j = s + 1; j < t; ++j) acc.add(Kd[inc_v[j]]);
     }
     const int32_t dst = lv_dst[u];
     if (dst >= 0) vals[dst] = acc.value();
@@ -444,10 +448,14 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 1536 / THREADS : 1) 
     const int s = le_off[u], t = le_off[u + 1];
     const int i0 = inc_e[s] >> 1;
     Acc<T> acc = DEFER ? Acc<T>(Ko[i0] * Sc[i0 / NP]) : Acc<T>(Ko[i0]);
-    for (int j = s + 1; j < t; ++j) {
-      const int ij = inc_e[j] >> 1;
-      if constexpr (DEFER) acc.add_scaled(Ko[ij], Sc[ij / NP]);
-      else acc.add(Ko[ij]);
+    if constexpr (DEFER) {
+#pragma unroll 1
+      for (int j = s + 1; j < t; ++j) {
+        const int ij = inc_e[j] >> 1;
+        acc.add_scaled(Ko[ij], Sc[ij / NP]);
+      }
+    } else {
+      for (int j = s + 1; j < t; ++j) acc.add(Ko[inc_e[j] >> 1]);
     }
     const int32_t dst = le_dst[2 * u];
     if (dst >= 0) {
